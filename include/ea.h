@@ -1,0 +1,168 @@
+/*
+ * ea.h -- C ABI of the GB300 (sm_103a) parallel-tempering Metropolis simulator
+ * of the three-dimensional +-J Edwards-Anderson spin glass.
+ *
+ * The method is that of Fang et al., "Parallel Tempering Simulation of the
+ * three-dimensional Edwards-Anderson Model with Compact Asynchronous Multispin
+ * Coding on GPU": the Hamiltonian of Sec. 2.2 (Eq. 1, here with h = 0),
+ * single-spin-flip Metropolis (Sec. 2.3) in a two-stage checkerboard sweep
+ * (Sec. 3.1), replica exchange between adjacent temperatures (Sec. 2.4,
+ * Sec. 4.1), integer threshold tables compared with the generator's integer
+ * output (Sec. 4.3.1, 4.3.2), and measurements in their own pass (Sec. 4.1).
+ *
+ * Data conventions (every array is C order, little-endian uint32 words):
+ *   L even >= 4, N = L^3 sites, site i = x + L*(y + L*z), periodic in x, y, z.
+ *   G word-groups; bit b of a group's words is realization 32*g + b.
+ *   NT temperature slots, slot 0 the coldest; C copies per slot (1 or 2).
+ *   spins  [G][NT][C][N]  bit 1 <=> S = +1, indexed by temperature slot.
+ *   bonds  [G][3][N]      bit 1 <=> J = -1 on bond (i, i + e_d), d = x, y, z.
+ *   metro  [NT][3]        flip threshold for dE = 12 - 4u, u = 0, 1, 2;
+ *                         each row non-decreasing in u.
+ *   swapt  [NT-1][swap_len]  swap threshold for E_p - E_{p+1} = -4k at
+ *                         column k-1; each row non-increasing in k.
+ *   energies [G][NT][C][32] int32, E = -sum_bonds J S_i S_j (Eq. 1).
+ * Random numbers: Philox4x32-10 keyed by seed = (lo32, hi32).
+ *   Metropolis: one 32-bit output per (g, t, c, sweep s, site), shared by the
+ *     32 realizations of the word: counter (k >> 2, s, g,
+ *     (colour << 16) | (c << 8) | t), output word k & 3, k = i >> 1,
+ *     colour = (x + y + z) & 1.
+ *   Swap pass P, pair p, realization b: counter ((p << 3) | (b >> 2), P, g,
+ *     (1 << 24) | (c << 8)), output word b & 3.
+ * A sweep updates colour 0 then colour 1.  Site i flips iff dE <= 0 or
+ * r < metro[t][u], u = number of unsatisfied bonds of i.  After sweep s
+ * (global index since creation) a swap pass runs iff swap_every > 0 and
+ * (s + 1) % swap_every == 0: for each realization, pairs p = 0..NT-2 in
+ * order, accept iff E_p - E_{p+1} >= 0 or r < swapt[p][k-1] with
+ * k = (E_{p+1} - E_p) / 4 <= swap_len; an accepted pair exchanges the two
+ * slots' configurations (that realization's bit only) and energies.
+ *
+ * Errors: every call returns EA_OK (0) or a negative EA_E* code; nothing is
+ * thrown across the ABI.  Work is enqueued on the stream given at creation;
+ * device faults surface as EA_ECUDA on the next call that synchronises
+ * (ea_sync, ea_read_spins_host, ea_run, ea_get_*).  A context is not
+ * thread-safe; use one per host thread.
+ */
+#ifndef EA_H
+#define EA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EA_OK 0
+#define EA_PENDING 1          /* ea_poll: request not finished yet */
+#define EA_EINVAL (-1)        /* bad argument, shape, table or null pointer */
+#define EA_ENOMEM (-2)        /* device or host allocation failed */
+#define EA_ECUDA (-3)         /* CUDA runtime error (launch or device fault) */
+#define EA_ETIMEOUT (-4)      /* wait deadline passed */
+#define EA_EUNSUPPORTED (-5)  /* lattice size without a compiled kernel */
+#define EA_ESTATE (-6)        /* call not valid in the object's current state */
+
+typedef struct ea_ctx ea_ctx;
+
+typedef struct {
+    uint32_t L;               /* even, one of the sizes ea_supported_L() accepts */
+    uint32_t n_groups;        /* G >= 1 (32 realizations each) */
+    uint32_t n_temps;         /* 1 <= NT <= 64 */
+    uint32_t n_copies;        /* C in {1, 2} */
+    uint64_t seed;            /* Philox key */
+    const uint32_t *bonds;    /* host [G][3][N], copied at creation */
+    const uint32_t *spins0;   /* host [G][NT][C][N], copied at creation */
+    const uint32_t *metro;    /* host [NT][3], copied */
+    const uint32_t *swapt;    /* host [NT-1][swap_len], copied; may be NULL if swap_len == 0 */
+    uint32_t swap_len;
+} ea_config;
+
+/* Options of one ea_sweep call.  All output pointers are DEVICE pointers and
+ * may be NULL.  Counters continue from the context's global sweep index s and
+ * swap-pass index P. */
+typedef struct {
+    uint32_t n_sweeps;
+    uint32_t swap_every;      /* 0: no swap passes */
+    int32_t *energy_log;      /* [n_sweeps][G][NT][C][32] energies by slot after each sweep
+                                 (after its swap pass, if any) */
+    uint32_t *swap_log;       /* [passes][G][C][NT-1] accepted-pair masks, bit b = realization b */
+    uint64_t *qhist;          /* [NT][N+1] += 1 at bin n_diff for every (g, b) of each measured
+                                 sweep; n_diff = #sites where copy 0 and copy 1 differ; needs C == 2 */
+    int64_t *esum;            /* [NT] += sum over (g, c, b) of E at each measured sweep */
+    uint64_t measure_from;    /* sweep s is measured iff s >= measure_from and */
+    uint32_t measure_every;   /*   (s - measure_from) % measure_every == 0; 0 = never */
+} ea_sweep_args;
+
+/* Threshold tables in FP64 (Sec. 4.3.1, 4.3.2): metro[t][u] =
+ * floor(exp(-beta_t (12 - 4u)) * 2^32) and swapt[p][k-1] =
+ * floor(exp(-4k (beta_p - beta_{p+1})) * 2^32), clamped to 2^32 - 1.
+ * beta: host [n_temps], >= 0 and non-increasing (slot 0 coldest).
+ * swap columns run over k = 1..3N/2 (the largest possible |dE| / 4) with
+ * trailing all-zero columns dropped; *swap_len_out receives that length.
+ * swap_out (host [n_temps-1][swap_cap]) is filled when swap_cap >= the
+ * length, else left untouched (call with swap_cap = 0 to query).
+ * metro_out: host [n_temps][3], may be NULL.  Host-only, no GPU needed. */
+int ea_build_tables(const double *beta, uint32_t n_temps, uint32_t n_sites, uint32_t *metro_out,
+                    uint32_t *swap_out, uint32_t swap_cap, uint32_t *swap_len_out);
+
+/* 1 if lattice size L has compiled kernels, else 0. */
+int ea_supported_L(uint32_t L);
+
+/* Allocates the device state of one ensemble on the current device and copies
+ * the host arrays of cfg (the caller keeps ownership of them).  stream is a
+ * cudaStream_t (NULL = legacy default stream); all later work of this context
+ * is enqueued on it.  On success *out owns the context until ea_destroy. */
+int ea_create(const ea_config *cfg, void *stream, ea_ctx **out);
+
+/* Frees the context's device memory after its stream has drained.  NULL is a no-op. */
+void ea_destroy(ea_ctx *ctx);
+
+/* Runs args->n_sweeps checkerboard sweeps with the swap passes and
+ * measurements the arguments ask for; asynchronous on the context's stream. */
+int ea_sweep(ea_ctx *ctx, const ea_sweep_args *args);
+
+/* One replica-exchange pass now (pass index P, then P += 1), on energies
+ * recomputed from the spins.  masks: DEVICE [G][C][NT-1] or NULL.  Asynchronous. */
+int ea_pt_swap(ea_ctx *ctx, uint32_t *masks);
+
+/* Measurement pass (Sec. 4.1): recomputes the energies from the spins.
+ * energies: DEVICE [G][NT][C][32] int32 or NULL; ndiff: DEVICE [G][NT][32]
+ * uint32 or NULL (needs C == 2); qhist: DEVICE [NT][N+1] uint64, += one
+ * count per (g, b), or NULL (needs C == 2).  Asynchronous. */
+int ea_measure(ea_ctx *ctx, int32_t *energies, uint32_t *ndiff, uint64_t *qhist);
+
+/* Spins by slot into DEVICE dst [G][NT][C][N].  Asynchronous. */
+int ea_read_spins(ea_ctx *ctx, uint32_t *dst);
+
+/* Spins by slot into HOST dst [G][NT][C][N]; synchronises the stream. */
+int ea_read_spins_host(ea_ctx *ctx, uint32_t *dst);
+
+/* Replaces the state (checkpoint restore): spins from DEVICE src
+ * [G][NT][C][N] by slot, and the global sweep and swap-pass indices. */
+int ea_write_spins(ea_ctx *ctx, const uint32_t *src, uint64_t sweep_index, uint64_t pass_index);
+
+/* Global sweep index s of the next sweep and pass index P of the next swap pass. */
+int ea_get_counters(const ea_ctx *ctx, uint64_t *sweep_index, uint64_t *pass_index);
+
+/* Waits for the context's stream; returns EA_ECUDA on a device fault. */
+int ea_sync(ea_ctx *ctx);
+
+/* Number of kernel launches this context has enqueued so far. */
+uint64_t ea_launch_count(const ea_ctx *ctx);
+
+/* Host-buffer entry point: creates a context from cfg, runs the sweeps of
+ * args (its DEVICE output pointers must be NULL), copies the results to the
+ * HOST buffers below (each may be NULL), destroys the context and
+ * synchronises.  Host outputs: energies [G][NT][C][32] (final), spins
+ * [G][NT][C][N] (final), qhist [NT][N+1] (overwritten with this run's counts),
+ * esum [NT] (overwritten).  stream as in ea_create. */
+int ea_run(const ea_config *cfg, const ea_sweep_args *args, void *stream, int32_t *energies_host,
+           uint32_t *spins_host, uint64_t *qhist_host, int64_t *esum_host);
+
+/* Static description of an error code. */
+const char *ea_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EA_H */

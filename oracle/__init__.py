@@ -48,7 +48,7 @@ def _bind(lib):
     lib.or_swap_table.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _u32p]
     lib.or_swap_table.restype = ctypes.c_int
     lib.or_create.argtypes = [ctypes.c_int] * 4 + [ctypes.c_uint64, _u32p, _u32p, _u32p, vp,
-                                                  ctypes.c_int]
+                                                  ctypes.c_int, ctypes.c_int]
     lib.or_create.restype = vp
     lib.or_destroy.argtypes = [vp]
     lib.or_destroy.restype = None
@@ -124,7 +124,10 @@ def swap_table_trimmed(betas, n_sites: int) -> np.ndarray:
 class OracleSim:
     """Scalar simulation state; mirrors the product's create/sweep/swap/measure calls."""
 
-    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt):
+    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, group_base=0):
+        """group_base: global index of the first group passed (the random-number
+        counters use global group indices, so a subset of groups reproduces the
+        same trajectories as the full ensemble)."""
         self.lib = load()
         self.L, self.G, self.NT, self.C = int(L), int(G), int(NT), int(C)
         self.N = self.L ** 3
@@ -139,7 +142,7 @@ class OracleSim:
         self.swap_len = swap_len
         self.h = self.lib.or_create(self.L, self.G, self.NT, self.C, int(seed), self.bonds, spins,
                                     self.metro, self.swapt.ctypes.data if self.swapt.size else None,
-                                    swap_len)
+                                    swap_len, int(group_base))
         if not self.h:
             raise ValueError("oracle rejected the configuration")
 

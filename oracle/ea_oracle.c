@@ -128,6 +128,7 @@ int or_swap_table(const double *beta, int nt, int len, uint32_t *swapt)
 typedef struct {
     int L, N, G, NT, C;
     uint64_t seed;
+    int group_base;  /* global index of local group 0 (for runs on a subset of groups) */
     int swap_len;
     int8_t *sigma;   /* [G][C][32][NT][N]  stored configurations, +-1 */
     int8_t *J;       /* [G][32][3][N]      couplings, +-1 */
@@ -220,13 +221,13 @@ or_sim *or_create(int L, int G, int NT, int C, uint64_t seed,
                   const uint32_t *spins,   /* [G][NT][C][N] */
                   const uint32_t *metro,   /* [NT][3] */
                   const uint32_t *swapt,   /* [NT-1][swap_len] */
-                  int swap_len)
+                  int swap_len, int group_base)
 {
     if (L < 2 || (L & 1) || G < 1 || NT < 1 || C < 1 || C > 2 || swap_len < 0) return NULL;
     or_sim *m = (or_sim *)calloc(1, sizeof(or_sim));
     if (!m) return NULL;
     m->L = L; m->N = L * L * L; m->G = G; m->NT = NT; m->C = C;
-    m->seed = seed; m->swap_len = swap_len;
+    m->seed = seed; m->swap_len = swap_len; m->group_base = group_base;
     size_t N = (size_t)m->N;
     m->sigma = (int8_t *)malloc((size_t)G * C * OR_LANES * NT * N);
     m->J = (int8_t *)malloc((size_t)G * OR_LANES * 3 * N);
@@ -282,7 +283,7 @@ static void sweep_slot(or_sim *m, int g, int c, int t, uint64_t s)
         for (int i = 0; i < m->N; ++i) {
             if (m->colour[i] != colour) continue;
             uint32_t k = (uint32_t)i >> 1;
-            uint32_t r = or_uniform(m->seed, k >> 2, (uint32_t)s, (uint32_t)g,
+            uint32_t r = or_uniform(m->seed, k >> 2, (uint32_t)s, (uint32_t)(m->group_base + g),
                                     ((uint32_t)colour << 16) | ((uint32_t)c << 8) | (uint32_t)t,
                                     (int)(k & 3u));
             for (int b = 0; b < OR_LANES; ++b) {
@@ -312,7 +313,8 @@ static void swap_pass(or_sim *m, int g, int c, uint64_t P, uint32_t *mask)
         for (int p = 0; p + 1 < m->NT; ++p) {
             int64_t delta = e[l[p]] - e[l[p + 1]];
             uint32_t r = or_uniform(m->seed, ((uint32_t)p << 3) | ((uint32_t)b >> 2), (uint32_t)P,
-                                    (uint32_t)g, (1u << 24) | ((uint32_t)c << 8), b & 3);
+                                    (uint32_t)(m->group_base + g), (1u << 24) | ((uint32_t)c << 8),
+                                    b & 3);
             int accept;
             if (delta >= 0) {
                 accept = 1;

@@ -1,0 +1,273 @@
+"""Python binding of the GB300 parallel-tempering Edwards-Anderson simulator.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of ``_build/libea.so`` behind the C ABI of ``include/ea.h``.  PyTorch
+provides device memory (output tensors) and the CUDA stream.  There is no CPU
+fallback: if the library is missing, importing the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+EA_OK, EA_PENDING = 0, 1
+_ERRORS = {-1: "EA_EINVAL", -2: "EA_ENOMEM", -3: "EA_ECUDA", -4: "EA_ETIMEOUT",
+           -5: "EA_EUNSUPPORTED", -6: "EA_ESTATE"}
+
+_lib = None
+
+
+class EAError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_ERRORS.get(code, code)}")
+        self.code = code
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint32), ("n_groups", ctypes.c_uint32),
+                ("n_temps", ctypes.c_uint32), ("n_copies", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("bonds", ctypes.c_void_p),
+                ("spins0", ctypes.c_void_p), ("metro", ctypes.c_void_p),
+                ("swapt", ctypes.c_void_p), ("swap_len", ctypes.c_uint32)]
+
+
+class _SweepArgs(ctypes.Structure):
+    _fields_ = [("n_sweeps", ctypes.c_uint32), ("swap_every", ctypes.c_uint32),
+                ("energy_log", ctypes.c_void_p), ("swap_log", ctypes.c_void_p),
+                ("qhist", ctypes.c_void_p), ("esum", ctypes.c_void_p),
+                ("measure_from", ctypes.c_uint64), ("measure_every", ctypes.c_uint32)]
+
+
+EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_sweep",
+           "ea_pt_swap", "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
+           "ea_get_counters", "ea_sync", "ea_launch_count", "ea_run", "ea_strerror"]
+
+
+def load_library(path: str | None = None):
+    """Loads libea.so (building it with nvcc when the source is newer).
+
+    Raises when the library cannot be built or loaded: the simulator has no
+    other implementation to fall back to."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    if path is None:
+        path = LIB_PATH
+        if not os.path.exists(path) or _build._stale(path, [
+                os.path.join(_build.CSRC, f) for f in os.listdir(_build.CSRC)]):
+            _build.build()
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    lib.ea_build_tables.argtypes = [vp, u32, u32, vp, vp, u32, ctypes.POINTER(u32)]
+    lib.ea_supported_L.argtypes = [u32]
+    lib.ea_create.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(vp)]
+    lib.ea_destroy.argtypes = [vp]
+    lib.ea_destroy.restype = None
+    lib.ea_sweep.argtypes = [vp, ctypes.POINTER(_SweepArgs)]
+    lib.ea_pt_swap.argtypes = [vp, vp]
+    lib.ea_measure.argtypes = [vp, vp, vp, vp]
+    lib.ea_read_spins.argtypes = [vp, vp]
+    lib.ea_read_spins_host.argtypes = [vp, vp]
+    lib.ea_write_spins.argtypes = [vp, vp, u64, u64]
+    lib.ea_get_counters.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.ea_sync.argtypes = [vp]
+    lib.ea_launch_count.argtypes = [vp]
+    lib.ea_launch_count.restype = u64
+    lib.ea_run.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_SweepArgs), vp, vp, vp, vp, vp]
+    lib.ea_strerror.argtypes = [i32]
+    lib.ea_strerror.restype = ctypes.c_char_p
+    for name in ("ea_build_tables", "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
+                 "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
+                 "ea_get_counters", "ea_sync", "ea_run"):
+        getattr(lib, name).restype = i32
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != EA_OK:
+        raise EAError(rc, what)
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array, or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def ea_build_tables(betas, n_sites: int):
+    """FP64 threshold tables (metro [NT][3], swapt [NT-1][swap_len]) as uint32 numpy arrays."""
+    lib = load_library()
+    betas = np.ascontiguousarray(betas, np.float64)
+    nt = len(betas)
+    metro = np.zeros((nt, 3), np.uint32)
+    ln = ctypes.c_uint32(0)
+    _check(lib.ea_build_tables(betas.ctypes.data, nt, n_sites, metro.ctypes.data, None, 0,
+                               ctypes.byref(ln)), "ea_build_tables")
+    swapt = np.zeros((max(nt - 1, 0), ln.value), np.uint32)
+    if swapt.size:
+        _check(lib.ea_build_tables(betas.ctypes.data, nt, n_sites, None, swapt.ctypes.data,
+                                   ln.value, ctypes.byref(ln)), "ea_build_tables")
+    return metro, swapt
+
+
+def ea_supported_L(L: int) -> bool:
+    return bool(load_library().ea_supported_L(L))
+
+
+def _config(L, G, NT, C, seed, bonds, spins, metro, swapt):
+    keep = [np.ascontiguousarray(a, np.uint32) for a in (bonds, spins, metro, swapt)]
+    b, s, m, w = keep
+    N = L ** 3
+    assert b.shape == (G, 3, N) and s.shape == (G, NT, C, N) and m.shape == (NT, 3)
+    cfg = _Config(L, G, NT, C, int(seed), b.ctypes.data, s.ctypes.data, m.ctypes.data,
+                  w.ctypes.data if w.size else None, w.shape[1] if w.ndim == 2 else 0)
+    return cfg, keep
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream, stream
+
+
+class Ensemble:
+    """One simulated ensemble (an ea_ctx): G word-groups x NT slots x C copies of an L^3 lattice."""
+
+    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, stream=None):
+        import torch
+        self.lib = load_library()
+        self.L, self.G, self.NT, self.C = int(L), int(G), int(NT), int(C)
+        self.N = self.L ** 3
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.handle, self.stream = _stream_handle(stream)
+        cfg, _keep = _config(self.L, self.G, self.NT, self.C, seed, bonds, spins, metro, swapt)
+        self.swap_len = cfg.swap_len
+        h = ctypes.c_void_p(None)
+        _check(self.lib.ea_create(ctypes.byref(cfg), self.handle, ctypes.byref(h)), "ea_create")
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.ea_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- counters
+    @property
+    def counters(self):
+        s, p = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(self.lib.ea_get_counters(self.ctx, ctypes.byref(s), ctypes.byref(p)), "ea_get_counters")
+        return s.value, p.value
+
+    @property
+    def sweep_index(self) -> int:
+        return self.counters[0]
+
+    @property
+    def pass_index(self) -> int:
+        return self.counters[1]
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.ea_launch_count(self.ctx))
+
+    def n_passes(self, n_sweeps: int, swap_every: int) -> int:
+        if swap_every <= 0:
+            return 0
+        s0 = self.sweep_index
+        return (s0 + n_sweeps) // swap_every - s0 // swap_every
+
+    def _empty(self, shape, dtype):
+        import torch
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    # -- the C ABI calls
+    def sweep(self, n_sweeps, swap_every, energy_log=False, swap_log=False, qhist=None, esum=None,
+              measure_from=0, measure_every=0):
+        """Runs sweeps; returns dict of requested device logs.  qhist/esum tensors accumulate."""
+        import torch
+        out = {}
+        elog = slog = None
+        if energy_log:
+            elog = self._empty((n_sweeps, self.G, self.NT, self.C, 32), torch.int32)
+            out["energy_log"] = elog
+        if swap_log:
+            slog = self._empty((self.n_passes(n_sweeps, swap_every), self.G, self.C,
+                                max(self.NT - 1, 0)), torch.int32)
+            out["swap_log"] = slog
+        args = _SweepArgs(int(n_sweeps), int(swap_every), _ptr(elog), _ptr(slog), _ptr(qhist),
+                          _ptr(esum), int(measure_from), int(measure_every))
+        _check(self.lib.ea_sweep(self.ctx, ctypes.byref(args)), "ea_sweep")
+        return out
+
+    def pt_swap(self):
+        import torch
+        masks = self._empty((self.G, self.C, max(self.NT - 1, 0)), torch.int32)
+        _check(self.lib.ea_pt_swap(self.ctx, _ptr(masks) if masks.numel() else None), "ea_pt_swap")
+        return masks
+
+    def measure(self, energies=True, ndiff=False, qhist=None):
+        import torch
+        e = self._empty((self.G, self.NT, self.C, 32), torch.int32) if energies else None
+        nd = self._empty((self.G, self.NT, 32), torch.int32) if ndiff else None
+        _check(self.lib.ea_measure(self.ctx, _ptr(e), _ptr(nd), _ptr(qhist)), "ea_measure")
+        return e, nd
+
+    def read_spins(self, out=None):
+        import torch
+        if out is None:
+            out = self._empty((self.G, self.NT, self.C, self.N), torch.int32)
+        _check(self.lib.ea_read_spins(self.ctx, _ptr(out)), "ea_read_spins")
+        return out
+
+    def read_spins_host(self) -> np.ndarray:
+        out = np.zeros((self.G, self.NT, self.C, self.N), np.uint32)
+        _check(self.lib.ea_read_spins_host(self.ctx, out.ctypes.data), "ea_read_spins_host")
+        return out
+
+    def write_spins(self, spins_dev, sweep_index: int, pass_index: int):
+        _check(self.lib.ea_write_spins(self.ctx, _ptr(spins_dev), int(sweep_index), int(pass_index)),
+               "ea_write_spins")
+
+    def sync(self):
+        _check(self.lib.ea_sync(self.ctx), "ea_sync")
+
+
+def ea_run(L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every, measure_from=0,
+           measure_every=0, want_spins=True, want_qhist=False, want_esum=False, host_out=None,
+           stream=None):
+    """Host-buffer entry point: host arrays in, host arrays out (ea_run)."""
+    lib = load_library()
+    handle, _ = _stream_handle(stream)
+    cfg, _keep = _config(L, G, NT, C, seed, bonds, spins, metro, swapt)
+    N = L ** 3
+    ho = host_out or {}
+    energies = ho.get("energies", np.zeros((G, NT, C, 32), np.int32))
+    sp = ho.get("spins", np.zeros((G, NT, C, N), np.uint32)) if want_spins else None
+    qh = ho.get("qhist", np.zeros((NT, N + 1), np.uint64)) if want_qhist else None
+    es = ho.get("esum", np.zeros(NT, np.int64)) if want_esum else None
+    args = _SweepArgs(int(n_sweeps), int(swap_every), None, None, None, None, int(measure_from),
+                      int(measure_every))
+    _check(lib.ea_run(ctypes.byref(cfg), ctypes.byref(args), handle, _ptr(energies), _ptr(sp),
+                      _ptr(qh), _ptr(es)), "ea_run")
+    return {"energies": energies, "spins": sp, "qhist": qh, "esum": es}

@@ -1,0 +1,448 @@
+// C ABI of the simulator (declared in include/ea.h): argument validation,
+// device state, the FP64 threshold tables, and the host-side schedule that
+// splits a sweep range into kernel launches.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ea.h"
+#include "ea_internal.h"
+
+struct ea_ctx {
+    uint32_t L, G, NT, C, N, swap_len;
+    uint64_t seed;
+    cudaStream_t stream;
+    int device;
+    size_t smem_optin;
+    uint32_t *d_spins, *d_bonds, *d_metro, *d_swapt, *d_masks;
+    int32_t *d_energy;
+    int *d_err;
+    uint64_t sweep, pass;
+    uint64_t launches;
+    ea::Plan plan;
+    ea::RoundKeys rk;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) return EA_ENOMEM;
+    return EA_ECUDA;
+}
+
+#define EA_TRY(expr)                                      \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_);      \
+    } while (0)
+
+uint32_t prob_to_u32(double p)
+{
+    const double v = std::floor(std::ldexp(p, 32));
+    if (v >= 4294967295.0) return 4294967295u;
+    if (v <= 0.0) return 0u;
+    return (uint32_t)v;
+}
+
+bool swap_after(uint64_t s, uint32_t every) { return every != 0 && (s + 1) % every == 0; }
+bool measured(uint64_t s, uint64_t from, uint32_t every)
+{
+    return every != 0 && s >= from && (s - from) % every == 0;
+}
+
+int validate_tables(const uint32_t *metro, const uint32_t *swapt, uint32_t NT, uint32_t len)
+{
+    for (uint32_t t = 0; t < NT; ++t)
+        if (metro[t * 3] > metro[t * 3 + 1] || metro[t * 3 + 1] > metro[t * 3 + 2]) return EA_EINVAL;
+    if (NT > 1 && len > 0) {
+        if (!swapt) return EA_EINVAL;
+        for (uint32_t p = 0; p + 1 < NT; ++p)
+            for (uint32_t k = 1; k < len; ++k)
+                if (swapt[(size_t)p * len + k] > swapt[(size_t)p * len + k - 1]) return EA_EINVAL;
+    }
+    return EA_OK;
+}
+
+ea::SweepLaunch base_launch(ea_ctx *c)
+{
+    ea::SweepLaunch a;
+    std::memset(&a, 0, sizeof(a));
+    a.spins = c->d_spins;
+    a.bonds = c->d_bonds;
+    a.metro = c->d_metro;
+    a.swapt = c->d_swapt;
+    a.swap_len = c->swap_len;
+    a.energy = c->d_energy;
+    a.G = c->G;
+    a.NT = c->NT;
+    a.C = c->C;
+    a.rk = c->rk;
+    a.err = c->d_err;
+    return a;
+}
+
+void free_ctx(ea_ctx *c)
+{
+    if (!c) return;
+    cudaFree(c->d_spins);
+    cudaFree(c->d_bonds);
+    cudaFree(c->d_metro);
+    cudaFree(c->d_swapt);
+    cudaFree(c->d_masks);
+    cudaFree(c->d_energy);
+    cudaFree(c->d_err);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ea_strerror(int code)
+{
+    switch (code) {
+    case EA_OK: return "ok";
+    case EA_PENDING: return "pending";
+    case EA_EINVAL: return "invalid argument";
+    case EA_ENOMEM: return "out of memory";
+    case EA_ECUDA: return "CUDA error";
+    case EA_ETIMEOUT: return "timed out";
+    case EA_EUNSUPPORTED: return "unsupported lattice size";
+    case EA_ESTATE: return "invalid state";
+    default: return "unknown error";
+    }
+}
+
+int ea_supported_L(uint32_t L) { return ea::supported_L((int)L) ? 1 : 0; }
+
+int ea_build_tables(const double *beta, uint32_t n_temps, uint32_t n_sites, uint32_t *metro_out,
+                    uint32_t *swap_out, uint32_t swap_cap, uint32_t *swap_len_out)
+{
+    if (!beta || n_temps == 0 || n_sites == 0 || !swap_len_out) return EA_EINVAL;
+    for (uint32_t t = 0; t < n_temps; ++t) {
+        if (!(beta[t] >= 0.0) || !std::isfinite(beta[t])) return EA_EINVAL;
+        if (t > 0 && !(beta[t] <= beta[t - 1])) return EA_EINVAL;
+    }
+    if (metro_out)
+        for (uint32_t t = 0; t < n_temps; ++t)
+            for (int u = 0; u < 3; ++u)
+                metro_out[t * 3 + u] = prob_to_u32(std::exp(-beta[t] * (12.0 - 4.0 * u)));
+    // largest k with a non-zero threshold in any row, k <= 3N/2
+    const uint32_t kmax = 3u * n_sites / 2u;
+    uint32_t len = 0;
+    for (uint32_t p = 0; p + 1 < n_temps; ++p) {
+        const double db = beta[p] - beta[p + 1];
+        // thresholds decrease in k: find the last non-zero one by bisection
+        uint32_t lo = 0, hi = kmax;   // invariant: entry lo is non-zero (lo = 0: none known)
+        while (lo < hi) {
+            const uint32_t mid = lo + (hi - lo + 1) / 2;
+            if (prob_to_u32(std::exp(-db * 4.0 * (double)mid)) != 0) lo = mid; else hi = mid - 1;
+        }
+        if (lo > len) len = lo;
+    }
+    *swap_len_out = len;
+    if (swap_out && swap_cap >= len && len > 0)
+        for (uint32_t p = 0; p + 1 < n_temps; ++p) {
+            const double db = beta[p] - beta[p + 1];
+            for (uint32_t k = 1; k <= len; ++k)
+                swap_out[(size_t)p * swap_cap + (k - 1)] = prob_to_u32(std::exp(-db * 4.0 * (double)k));
+        }
+    return EA_OK;
+}
+
+int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
+{
+    if (!cfg || !out) return EA_EINVAL;
+    *out = nullptr;
+    const uint32_t L = cfg->L;
+    if (L < 4 || (L & 1u)) return EA_EINVAL;
+    if (!ea::supported_L((int)L)) return EA_EUNSUPPORTED;
+    if (cfg->n_groups == 0 || cfg->n_temps == 0 || cfg->n_temps > (uint32_t)ea::kMaxTemps)
+        return EA_EINVAL;
+    if (cfg->n_copies < 1 || cfg->n_copies > 2) return EA_EINVAL;
+    if (!cfg->bonds || !cfg->spins0 || !cfg->metro) return EA_EINVAL;
+    if (cfg->n_temps > 1 && cfg->swap_len > 0 && !cfg->swapt) return EA_EINVAL;
+    int rc = validate_tables(cfg->metro, cfg->swapt, cfg->n_temps, cfg->swap_len);
+    if (rc != EA_OK) return rc;
+
+    ea_ctx *c = new (std::nothrow) ea_ctx;
+    if (!c) return EA_ENOMEM;
+    std::memset(c, 0, sizeof(*c));
+    c->L = L;
+    c->G = cfg->n_groups;
+    c->NT = cfg->n_temps;
+    c->C = cfg->n_copies;
+    c->N = L * L * L;
+    c->swap_len = cfg->swap_len;
+    c->seed = cfg->seed;
+    c->stream = (cudaStream_t)stream;
+    c->rk = ea::make_round_keys(cfg->seed);
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    int optin = 0;
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    if (e != cudaSuccess) { delete c; return cuda_fail(e); }
+    c->smem_optin = (size_t)optin;
+    if (!ea::make_plan((int)L, (int)c->NT, (int)c->C, c->smem_optin, 0, &c->plan)) {
+        delete c;
+        return EA_EUNSUPPORTED;
+    }
+
+    const size_t n_spin = (size_t)c->G * c->NT * c->C * c->N;
+    const size_t n_bond = (size_t)c->G * 3 * c->N;
+    const size_t n_swap = (size_t)(c->NT > 1 ? c->NT - 1 : 0) * c->swap_len;
+    uint32_t *stage_s = nullptr, *stage_b = nullptr;
+    auto fail = [&](cudaError_t err) {
+        cudaFree(stage_s);
+        cudaFree(stage_b);
+        free_ctx(c);
+        return cuda_fail(err);
+    };
+    if ((e = cudaMalloc(&c->d_spins, n_spin * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->d_bonds, n_bond * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->d_metro, (size_t)c->NT * 3 * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->d_swapt, (n_swap ? n_swap : 1) * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&c->d_masks, (size_t)c->G * c->C * ea::kMaxTemps * 4)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMalloc(&c->d_energy, (size_t)c->G * c->C * c->NT * ea::kLanes * 4)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&stage_s, n_spin * 4)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&stage_b, n_bond * 4)) != cudaSuccess) return fail(e);
+    cudaStream_t st = c->stream;
+    if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(stage_s, cfg->spins0, n_spin * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpyAsync(stage_b, cfg->bonds, n_bond * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return fail(e);
+    if ((e = cudaMemcpyAsync(c->d_metro, cfg->metro, (size_t)c->NT * 3 * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return fail(e);
+    if (n_swap &&
+        (e = cudaMemcpyAsync(c->d_swapt, cfg->swapt, n_swap * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return fail(e);
+    if ((e = ea::launch_import(stage_s, stage_b, c->d_spins, c->d_bonds, (int)L, c->G, c->NT, c->C, st,
+                               &c->launches)) != cudaSuccess)
+        return fail(e);
+    if ((e = ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)L, c->G, c->NT, c->C, st,
+                               &c->launches)) != cudaSuccess)
+        return fail(e);
+    // the staging buffers are freed once the copies above have run
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+    cudaFree(stage_s);
+    cudaFree(stage_b);
+    *out = c;
+    return EA_OK;
+}
+
+void ea_destroy(ea_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+}
+
+int ea_sweep(ea_ctx *c, const ea_sweep_args *args)
+{
+    if (!c || !args) return EA_EINVAL;
+    if ((args->qhist) && c->C != 2) return EA_EINVAL;
+    const uint32_t n = args->n_sweeps;
+    if (n == 0) return EA_OK;
+    cudaStream_t st = c->stream;
+    ea::SweepLaunch a = base_launch(c);
+    a.swap_every = args->swap_every;
+    a.energy_log = args->energy_log;
+    a.log_s0 = c->sweep;
+    a.swap_log = args->swap_log;
+    a.qhist = args->qhist;
+    a.esum = args->esum;
+    a.measure_from = args->measure_from;
+    a.measure_every = args->measure_every;
+    const uint64_t s_begin = c->sweep;
+    uint64_t passes = 0;
+    for (uint64_t s = s_begin; s < s_begin + n; ++s) passes += swap_after(s, args->swap_every);
+
+    if (c->plan.unit) {
+        a.s0 = s_begin;
+        a.n_sweeps = n;
+        a.P0 = c->pass;
+        a.pass_local0 = 0;
+        const bool overlaps = c->C == 2 && args->qhist != nullptr && args->measure_every != 0;
+        EA_TRY(ea::launch_sweep_unit(a, (int)c->L, c->plan, overlaps, st, &c->launches));
+    } else {
+        // Chunked form: sweep kernels run up to each swap or measured sweep;
+        // swap passes and measurements run as their own kernels in between.
+        uint64_t s = s_begin;
+        uint32_t pass_local = 0;
+        const uint64_t s_end = s_begin + n;
+        while (s < s_end) {
+            uint64_t e = s;
+            while (e + 1 < s_end && !swap_after(e, args->swap_every) &&
+                   !measured(e, args->measure_from, args->measure_every))
+                ++e;
+            // [s, e] inclusive
+            ea::SweepLaunch b = a;
+            b.s0 = s;
+            b.n_sweeps = (uint32_t)(e - s + 1);
+            b.qhist = nullptr;
+            b.esum = nullptr;
+            b.measure_every = 0;
+            const bool sw = swap_after(e, args->swap_every);
+            const bool me = measured(e, args->measure_from, args->measure_every);
+            b.compute_energy_last = 1;
+            EA_TRY(ea::launch_sweep_chunk(b, (int)c->L, c->plan, st, &c->launches));
+            if (sw) {
+                b.P0 = c->pass + pass_local;
+                b.pass_local0 = pass_local;
+                int32_t *elog_row = args->energy_log
+                    ? args->energy_log + (size_t)(e - s_begin) * c->G * c->NT * c->C * ea::kLanes
+                    : nullptr;
+                EA_TRY(ea::launch_swap_global(b, (int)c->L, c->pass + pass_local, c->d_masks, elog_row,
+                                              st, &c->launches));
+                ++pass_local;
+            }
+            if (me)
+                EA_TRY(ea::launch_measure(c->d_spins, c->d_energy, (int)c->L, c->G, c->NT, c->C,
+                                          nullptr, nullptr, args->qhist, args->esum, st,
+                                          &c->launches));
+            s = e + 1;
+        }
+    }
+    c->sweep += n;
+    c->pass += passes;
+    return EA_OK;
+}
+
+int ea_pt_swap(ea_ctx *c, uint32_t *masks)
+{
+    if (!c) return EA_EINVAL;
+    cudaStream_t st = c->stream;
+    EA_TRY(ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)c->L, c->G, c->NT, c->C, st,
+                             &c->launches));
+    ea::SweepLaunch a = base_launch(c);
+    a.swap_log = masks;   // row 0 of a one-pass log
+    a.pass_local0 = 0;
+    EA_TRY(ea::launch_swap_global(a, (int)c->L, c->pass, c->d_masks, nullptr, st, &c->launches));
+    c->pass += 1;
+    return EA_OK;
+}
+
+int ea_measure(ea_ctx *c, int32_t *energies, uint32_t *ndiff, uint64_t *qhist)
+{
+    if (!c) return EA_EINVAL;
+    if ((ndiff || qhist) && c->C != 2) return EA_EINVAL;
+    cudaStream_t st = c->stream;
+    EA_TRY(ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)c->L, c->G, c->NT, c->C, st,
+                             &c->launches));
+    EA_TRY(ea::launch_measure(c->d_spins, c->d_energy, (int)c->L, c->G, c->NT, c->C, energies, ndiff,
+                              qhist, nullptr, st, &c->launches));
+    return EA_OK;
+}
+
+int ea_read_spins(ea_ctx *c, uint32_t *dst)
+{
+    if (!c || !dst) return EA_EINVAL;
+    EA_TRY(ea::launch_export(c->d_spins, dst, (int)c->L, c->G, c->NT, c->C, c->stream, &c->launches));
+    return EA_OK;
+}
+
+int ea_read_spins_host(ea_ctx *c, uint32_t *dst)
+{
+    if (!c || !dst) return EA_EINVAL;
+    const size_t bytes = (size_t)c->G * c->NT * c->C * c->N * 4;
+    uint32_t *tmp = nullptr;
+    EA_TRY(cudaMalloc(&tmp, bytes));
+    cudaError_t e = ea::launch_export(c->d_spins, tmp, (int)c->L, c->G, c->NT, c->C, c->stream,
+                                      &c->launches);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    return e == cudaSuccess ? EA_OK : cuda_fail(e);
+}
+
+int ea_write_spins(ea_ctx *c, const uint32_t *src, uint64_t sweep_index, uint64_t pass_index)
+{
+    if (!c || !src) return EA_EINVAL;
+    EA_TRY(ea::launch_import_spins(src, c->d_spins, (int)c->L, c->G, c->NT, c->C, c->stream,
+                                   &c->launches));
+    EA_TRY(ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)c->L, c->G, c->NT, c->C,
+                             c->stream, &c->launches));
+    c->sweep = sweep_index;
+    c->pass = pass_index;
+    return EA_OK;
+}
+
+int ea_get_counters(const ea_ctx *c, uint64_t *sweep_index, uint64_t *pass_index)
+{
+    if (!c) return EA_EINVAL;
+    if (sweep_index) *sweep_index = c->sweep;
+    if (pass_index) *pass_index = c->pass;
+    return EA_OK;
+}
+
+int ea_sync(ea_ctx *c)
+{
+    if (!c) return EA_EINVAL;
+    EA_TRY(cudaStreamSynchronize(c->stream));
+    EA_TRY(cudaGetLastError());
+    return EA_OK;
+}
+
+uint64_t ea_launch_count(const ea_ctx *c) { return c ? c->launches : 0; }
+
+int ea_run(const ea_config *cfg, const ea_sweep_args *args, void *stream, int32_t *energies_host,
+           uint32_t *spins_host, uint64_t *qhist_host, int64_t *esum_host)
+{
+    if (!cfg || !args) return EA_EINVAL;
+    if (args->energy_log || args->swap_log || args->qhist || args->esum) return EA_EINVAL;
+    ea_ctx *c = nullptr;
+    int rc = ea_create(cfg, stream, &c);
+    if (rc != EA_OK) return rc;
+    const size_t nq = (size_t)c->NT * (c->N + 1);
+    const size_t ne = (size_t)c->G * c->NT * c->C * ea::kLanes;
+    uint64_t *d_q = nullptr;
+    int64_t *d_es = nullptr;
+    int32_t *d_e = nullptr;
+    cudaError_t e = cudaSuccess;
+    ea_sweep_args a2 = *args;
+    if (qhist_host) {
+        if (c->C != 2) { ea_destroy(c); return EA_EINVAL; }
+        e = cudaMalloc(&d_q, nq * 8);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_q, 0, nq * 8, c->stream);
+        a2.qhist = d_q;
+    }
+    if (e == cudaSuccess && esum_host) {
+        e = cudaMalloc(&d_es, (size_t)c->NT * 8);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_es, 0, (size_t)c->NT * 8, c->stream);
+        a2.esum = d_es;
+    }
+    if (e == cudaSuccess) {
+        rc = ea_sweep(c, &a2);
+        if (rc == EA_OK && energies_host) {
+            e = cudaMalloc(&d_e, ne * 4);
+            if (e == cudaSuccess)
+                e = ea::launch_measure(c->d_spins, c->d_energy, (int)c->L, c->G, c->NT, c->C, d_e,
+                                       nullptr, nullptr, nullptr, c->stream, &c->launches);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(energies_host, d_e, ne * 4, cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (rc == EA_OK && e == cudaSuccess && qhist_host)
+            e = cudaMemcpyAsync(qhist_host, d_q, nq * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (rc == EA_OK && e == cudaSuccess && esum_host)
+            e = cudaMemcpyAsync(esum_host, d_es, (size_t)c->NT * 8, cudaMemcpyDeviceToHost, c->stream);
+        if (rc == EA_OK && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (rc == EA_OK && e == cudaSuccess && spins_host) rc = ea_read_spins_host(c, spins_host);
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(d_q);
+    cudaFree(d_es);
+    cudaFree(d_e);
+    ea_destroy(c);
+    if (rc != EA_OK) return rc;
+    return e == cudaSuccess ? EA_OK : cuda_fail(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Internal interface between the C ABI (ea_api.cu) and the kernels (ea_kernels.cu).
+//
+// Device layout of one ensemble:
+//   spins  [G][C][NT][2][H]   colour-split: word (colour, k) holds site 2k + (x parity),
+//                             k = i >> 1, H = N / 2; unit (g, c) owns NT*N contiguous words
+//   bonds  [G][3][2][H]       bond words in the same colour-split order
+//   energy [G][C][NT][32]     int32 energies by slot
+// The colour-split order makes the four sites of one Philox call (class
+// indices 4q..4q+3 of one colour) one aligned 16-byte vector.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ea {
+
+constexpr int kLanes = 32;
+constexpr int kMaxTemps = 64;
+constexpr int kPlanes = 8;          // bit planes of a thread's energy counter (sum <= 255)
+constexpr int kMaxQuadsPerThread = 10;  // 4 sites x 6 bonds x 10 quads = 240 <= 255
+constexpr int kMaxThreads = 512;        // per CTA of the sweep kernels (128 registers a thread)
+
+struct RoundKeys {
+    uint32_t k[20];                 // Philox key of rounds 0..9: (k0 + r*W0, k1 + r*W1)
+};
+
+RoundKeys make_round_keys(uint64_t seed);
+
+// Everything one sweep launch needs.  Pointers are device pointers.
+struct SweepLaunch {
+    uint32_t *spins;
+    const uint32_t *bonds;
+    const uint32_t *metro;          // [NT][3]
+    const uint32_t *swapt;          // [NT-1][swap_len]
+    uint32_t swap_len;
+    int32_t *energy;                // [G][C][NT][32]
+    uint32_t G, NT, C;
+    RoundKeys rk;
+    uint64_t s0;                    // global index of the first sweep
+    uint32_t n_sweeps;
+    uint32_t swap_every;
+    uint64_t P0;                    // global index of the first swap pass of this launch
+    uint32_t pass_local0;           // index into swap_log of that pass
+    int32_t *energy_log;            // [n_log][G][NT][C][32], row = s - log_s0
+    uint64_t log_s0;
+    uint32_t *swap_log;             // [passes][G][C][NT-1]
+    uint64_t *qhist;                // [NT][N+1]
+    int64_t *esum;                  // [NT]
+    uint64_t measure_from;
+    uint32_t measure_every;
+    int *err;
+    // chunked form: lattices [t0, t0 + nlat) of each unit per CTA
+    uint32_t t_per_cta;
+    int compute_energy_last;        // chunked form: energies after the last sweep
+};
+
+struct Plan {
+    bool unit;          // all NT lattices of a (g, c) unit in one CTA (swaps in-kernel)
+    int threads_per_lattice;
+    int lattices_per_cta;   // == NT for unit
+    int threads;
+    size_t smem;
+    bool j_in_smem;
+};
+
+bool supported_L(int L);
+// Chooses the kernel form for (L, NT) given the device's opt-in shared memory.
+bool make_plan(int L, int NT, int C, size_t smem_optin, int tpl_override, Plan *plan);
+
+// Launchers: return cudaSuccess or the launch error.  Each adds its kernel
+// count to *launches.
+cudaError_t launch_import(const uint32_t *api_spins, const uint32_t *api_bonds, uint32_t *spins,
+                          uint32_t *bonds, int L, uint32_t G, uint32_t NT, uint32_t C,
+                          cudaStream_t st, uint64_t *launches);
+cudaError_t launch_export(const uint32_t *spins, uint32_t *api_spins, int L, uint32_t G,
+                          uint32_t NT, uint32_t C, cudaStream_t st, uint64_t *launches);
+cudaError_t launch_import_spins(const uint32_t *api_spins, uint32_t *spins, int L, uint32_t G,
+                                uint32_t NT, uint32_t C, cudaStream_t st, uint64_t *launches);
+cudaError_t launch_sweep_unit(const SweepLaunch &a, int L, const Plan &plan, bool cluster_measure,
+                              cudaStream_t st, uint64_t *launches);
+cudaError_t launch_sweep_chunk(const SweepLaunch &a, int L, const Plan &plan, cudaStream_t st,
+                               uint64_t *launches);
+cudaError_t launch_swap_global(const SweepLaunch &a, int L, uint64_t P, uint32_t *masks,
+                               int32_t *energy_log_row, cudaStream_t st, uint64_t *launches);
+cudaError_t launch_energy(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, int L,
+                          uint32_t G, uint32_t NT, uint32_t C, cudaStream_t st,
+                          uint64_t *launches);
+cudaError_t launch_measure(const uint32_t *spins, const int32_t *energy, int L, uint32_t G,
+                           uint32_t NT, uint32_t C, int32_t *energies_out, uint32_t *ndiff_out,
+                           uint64_t *qhist, int64_t *esum, cudaStream_t st, uint64_t *launches);
+
+}  // namespace ea

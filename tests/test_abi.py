@@ -1,0 +1,111 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every entry point include/ea.h declares, and its host-only pieces (threshold
+tables, argument validation) behave as documented."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1311_5582_gb300 as ea
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "ea.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ea_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ea.load_library()
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(ea.EXPORTS)
+
+
+def test_library_is_built_for_sm_103a():
+    import subprocess
+    out = subprocess.run(["cuobjdump", "--list-elf", ea.LIB_PATH], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+@pytest.mark.parametrize("nt,tmin,tmax,L", [(16, 0.8, 2.0, 4), (24, 0.9, 2.0, 8), (32, 0.95, 2.0, 16),
+                                            (32, 0.95, 2.0, 32), (1, 1.0, 1.0, 6), (20, 0.8, 2.0, 10)])
+def test_tables_match_oracle_bit_for_bit(nt, tmin, tmax, L):
+    betas = W.geometric_ladder(nt, tmin, tmax)
+    m, s = ea.ea_build_tables(betas, L ** 3)
+    np.testing.assert_array_equal(m, oracle.metro_table(betas))
+    np.testing.assert_array_equal(s, oracle.swap_table_trimmed(betas, L ** 3))
+
+
+def test_table_builder_rejects_bad_ladders():
+    with pytest.raises(ea.EAError):
+        ea.ea_build_tables(np.array([0.5, 1.0]), 64)      # increasing beta
+    with pytest.raises(ea.EAError):
+        ea.ea_build_tables(np.array([-1.0]), 64)
+
+
+def test_supported_sizes_and_strerror():
+    for L in (4, 6, 8, 10, 12, 14, 16, 20, 24, 32):
+        assert ea.ea_supported_L(L)
+    for L in (2, 3, 5, 18, 64):
+        assert not ea.ea_supported_L(L)
+    lib = ea.load_library()
+    assert lib.ea_strerror(-1) == b"invalid argument"
+
+
+def _cfg(**over):
+    inst = W.Instance(L=4, G=1, NT=4, C=2, seed=1, tmin=1.0, tmax=2.0, input_seed=1)
+    inp = W.draw_inputs(inst)
+    m, s = ea.ea_build_tables(inp["betas"], 64)
+    arrays = dict(bonds=inp["bonds"], spins=inp["spins"], metro=m, swapt=s)
+    arrays.update({k: v for k, v in over.items() if k in arrays})
+    dims = dict(L=4, G=1, NT=4, C=2)
+    dims.update({k: v for k, v in over.items() if k in dims})
+    cfg, keep = ea._config(dims["L"], dims["G"], dims["NT"], dims["C"], 1, arrays["bonds"],
+                           arrays["spins"], arrays["metro"], arrays["swapt"])
+    return cfg, keep
+
+
+def _create_rc(cfg):
+    lib = ea.load_library()
+    h = ctypes.c_void_p(None)
+    return lib.ea_create(ctypes.byref(cfg), None, ctypes.byref(h))
+
+
+def test_create_validates_arguments_before_touching_the_device():
+    cfg, keep = _cfg()
+    bad = []
+    c = ea._Config.from_buffer_copy(cfg); c.L = 5; bad.append((c, -1))
+    c = ea._Config.from_buffer_copy(cfg); c.L = 18; bad.append((c, -5))
+    c = ea._Config.from_buffer_copy(cfg); c.n_copies = 3; bad.append((c, -1))
+    c = ea._Config.from_buffer_copy(cfg); c.n_temps = 65; bad.append((c, -1))
+    c = ea._Config.from_buffer_copy(cfg); c.bonds = None; bad.append((c, -1))
+    for c, want in bad:
+        assert _create_rc(c) == want
+    # non-monotone Metropolis row
+    m = keep[2].copy(); m[0] = [5, 4, 3]
+    cfg2, keep2 = _cfg(metro=m)
+    assert _create_rc(cfg2) == -1
+    # increasing swap row
+    s = keep[3].copy(); s[0, 1] = s[0, 0] + 1 if s[0, 0] < 2**32 - 1 else s[0, 0]; s[0, 0] = 0
+    cfg3, keep3 = _cfg(swapt=s)
+    assert _create_rc(cfg3) == -1
+
+
+def test_null_context_calls_fail_cleanly():
+    lib = ea.load_library()
+    assert lib.ea_sweep(None, None) == -1
+    assert lib.ea_pt_swap(None, None) == -1
+    assert lib.ea_measure(None, None, None, None) == -1
+    assert lib.ea_sync(None) == -1
+    lib.ea_destroy(None)
