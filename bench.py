@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the parallel-tempering Edwards-Anderson simulator on GB300.
+
+Workload (one step): the L=8 ensemble -- 512 sites, 2048 realizations (64 words
+per site), 24 temperatures geometric in [0.9, 2.0] x 2 copies -- run for 10^5
+checkerboard sweeps with a replica-exchange pass after every sweep and the
+energy / overlap-q histogram measurement over the second half.  Metric: ps per
+spin-flip attempt (Eq. tsf of the paper, copies counted):
+    t = T / (sweeps * N * NT * C * realizations).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch under torch.distributed.run; each rank runs its own ensemble
+(weak scaling, no data exchange) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "ps per spin-flip attempt at 1 GPU, % of INT/HBM roofline; served p50/p99 latency"
+UNIT = "ps/flip"
+# Algorithmic integer operations of one site-word update (32 flip attempts):
+# 6 LOP3 bond XORs + 8 adder-tree LOP3 + 3 compares + 3 selects + 3 LOP
+# mask terms + 1 flip = 24, plus a quarter of a Philox4x32-10 call
+# (10 rounds x (2 IMAD.WIDE + 2 LOP3) / 4 = 10) minus the two constant-key
+# XORs folded into the LOP3s = 32.
+ALG_OPS_PER_SITE_WORD = 32
+ALU_LANES_PER_CLK_PER_SM = 64     # integer ALU pipe (LOP3/IADD3/ISETP/SEL) of one SM
+
+
+def workload():
+    inst = W.SCALE
+    n = W.SCALE_SWEEPS
+    return {
+        "inst": inst, "sweeps": n, "swap_every": W.SCALE_SWAP_EVERY,
+        "measure_from": n // 2, "measure_every": 1,
+        "flips": n * inst.N * inst.NT * inst.C * 32 * inst.G,
+        "name": (f"EA +-J L={inst.L} ({inst.N} sites), {32 * inst.G} realizations "
+                 f"({inst.G} words/site), {inst.NT} temperatures geometric in "
+                 f"[{inst.tmin},{inst.tmax}] x {inst.C} copies, {n} sweeps, PT swap every sweep, "
+                 f"energy + overlap-q histograms over the second half"),
+    }
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def rank_instance(inst, rank):
+    """Weak scaling: rank r simulates its own ensemble of the same shape
+    (its own disorder draws and Philox key); nothing is exchanged."""
+    return W.Instance(L=inst.L, G=inst.G, NT=inst.NT, C=inst.C, seed=inst.seed + 7919 * rank,
+                      tmin=inst.tmin, tmax=inst.tmax, input_seed=inst.input_seed + 7919 * rank)
+
+
+def aggregate(times_s, flips_per_rank):
+    """Job value: slowest rank's time over all ranks' flips (ps per flip)."""
+    t = max(times_s)
+    return t / (flips_per_rank * len(times_s)) * 1e12, t
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(wl, budget_s=15.0, threads=None):
+    """The oracle as it stands, on this host's cores, on a bounded sample of the
+    workload: the first `threads` word-groups for as many sweeps (from sweep 0,
+    same schedule and measurement) as fit the time budget."""
+    import oracle
+    inst = wl["inst"]
+    threads = threads or max(1, min(os.cpu_count() or 1, inst.G))
+    inp = W.draw_inputs(inst)
+    g = threads
+    metro = oracle.metro_table(inp["betas"])
+    swapt = oracle.swap_table_trimmed(inp["betas"], inst.N)
+
+    def run(n):
+        sim = oracle.OracleSim(inst.L, g, inst.NT, inst.C, inst.seed, inp["bonds"][:g],
+                               inp["spins"][:g], metro, swapt)
+        qh = np.zeros((inst.NT, inst.N + 1), np.uint64)
+        es = np.zeros(inst.NT, np.int64)
+        t0 = time.perf_counter()
+        sim.sweep(n, wl["swap_every"], qhist=qh, esum=es, measure_from=n // 2, measure_every=1,
+                  threads=threads)
+        return time.perf_counter() - t0
+
+    t_probe = run(10)
+    n = max(10, int(10 * budget_s / max(t_probe, 1e-3)))
+    t = run(n)
+    flips = n * inst.N * inst.NT * inst.C * 32 * g
+    return {"value": t / flips * 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{g} of {inst.G} word-groups ({32 * g} realizations), {n} sweeps "
+                      f"with the same swap and measurement schedule, {t:.1f} s"}
+
+
+def run_reference(args, wl):
+    """Reference arm: the CPU oracle, timed as it stands on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    inst = wl["inst"]
+    per_step_budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    import oracle
+    threads = max(1, min(os.cpu_count() or 1, inst.G))
+    inp = W.draw_inputs(inst)
+    metro = oracle.metro_table(inp["betas"])
+    swapt = oracle.swap_table_trimmed(inp["betas"], inst.N)
+    g = threads
+
+    def step(n):
+        sim = oracle.OracleSim(inst.L, g, inst.NT, inst.C, inst.seed, inp["bonds"][:g],
+                               inp["spins"][:g], metro, swapt)
+        qh = np.zeros((inst.NT, inst.N + 1), np.uint64)
+        es = np.zeros(inst.NT, np.int64)
+        t0 = time.perf_counter()
+        sim.sweep(n, wl["swap_every"], qhist=qh, esum=es, measure_from=n // 2, measure_every=1,
+                  threads=threads)
+        return time.perf_counter() - t0
+
+    t_probe = step(10)
+    n = max(10, int(10 * per_step_budget / max(t_probe, 1e-3)))
+    for _ in range(args.warmup):
+        step(n)
+    ts = [step(n) for _ in range(args.steps)]
+    flips = n * inst.N * inst.NT * inst.C * 32 * g
+    val = sum(ts) / len(ts) / flips * 1e12
+    sample = (f"{g} of {inst.G} word-groups, {n} sweeps per step, swap every sweep, "
+              f"measurement over the second half")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--sweeps", type=int, default=None, help="override sweeps per step (debug)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = workload()
+    if args.sweeps:
+        wl["sweeps"] = args.sweeps
+        wl["measure_from"] = args.sweeps // 2
+        inst = wl["inst"]
+        wl["flips"] = args.sweeps * inst.N * inst.NT * inst.C * 32 * inst.G
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    import paper_1311_5582_gb300 as ea
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    inst = rank_instance(wl["inst"], rank)
+    inp = W.draw_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    stream = torch.cuda.Stream()
+    ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
+                      metro, swapt, stream=stream)
+    qh = torch.zeros((inst.NT, inst.N + 1), dtype=torch.int64, device="cuda")
+    es = torch.zeros(inst.NT, dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        s0 = ens.sweep_index
+        ens.sweep(wl["sweeps"], wl["swap_every"], qhist=qh, esum=es,
+                  measure_from=s0 + wl["measure_from"], measure_every=wl["measure_every"])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        l0 = ens.launches
+        with ClockSampler(dev) as clk:
+            for i in range(args.steps):
+                flush.fill_(i)        # evict the ensemble from L2 between steps
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            barrier()
+        launches = ens.launches - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = t_total / (wl["flips"] * args.steps * world) * 1e12
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel (the fused sweep kernel: one launch per step)
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_tops = sms * ALU_LANES_PER_CLK_PER_SM * mhz * 1e6 / 1e12
+    site_words = wl["sweeps"] * inst.N * inst.NT * inst.C * inst.G
+    launch_s = statistics.mean(step_ms) / 1e3
+    achieved = site_words * ALG_OPS_PER_SITE_WORD / launch_s / 1e12
+
+    # end to end through the host-buffer entry point (pinned host memory both ways)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    h_in = {k: pin(v) for k, v in (("bonds", inp["bonds"]), ("spins", inp["spins"]),
+                                   ("metro", metro), ("swapt", swapt))}
+    h_out = {"energies": pin(np.zeros((inst.G, inst.NT, inst.C, 32), np.int32)),
+             "spins": pin(np.zeros((inst.G, inst.NT, inst.C, inst.N), np.uint32)),
+             "qhist": pin(np.zeros((inst.NT, inst.N + 1), np.uint64)),
+             "esum": pin(np.zeros(inst.NT, np.int64))}
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ea.ea_run(inst.L, inst.G, inst.NT, inst.C, inst.seed, h_in["bonds"], h_in["spins"],
+                  h_in["metro"], h_in["swapt"], wl["sweeps"], wl["swap_every"],
+                  measure_from=wl["measure_from"], measure_every=wl["measure_every"],
+                  want_spins=True, want_qhist=True, want_esum=True, host_out=h_out, stream=stream)
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    h2d = sum(v.nbytes for v in h_in.values())
+    d2h = sum(v.nbytes for v in h_out.values())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "l2_flush": True, "L": inst.L,
+                       "realizations": 32 * inst.G, "temps": inst.NT, "copies": inst.C,
+                       "sweeps_per_step": wl["sweeps"], "swap_every": wl["swap_every"],
+                       "kernel_launches_per_step": launches / args.steps},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+                         "frac": achieved / peak_tops, "traffic": None,
+                         "peak_basis": f"{sms} SMs x {ALU_LANES_PER_CLK_PER_SM} int-ALU lanes/clk x "
+                                       f"{mhz:.0f} MHz (max SM clock of measured peaks file)",
+                         "alg_ops_per_site_word": ALG_OPS_PER_SITE_WORD},
+            "e2e": {"value": t_e2e / (wl["flips"] * world) * 1e12, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "flips_per_step": wl["flips"] * world,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -23,11 +23,11 @@
  *   energies [G][NT][C][32] int32, E = -sum_bonds J S_i S_j (Eq. 1).
  * Random numbers: Philox4x32-10 keyed by seed = (lo32, hi32).
  *   Metropolis: one 32-bit output per (g, t, c, sweep s, site), shared by the
- *     32 realizations of the word: counter (k >> 2, s, g,
- *     (colour << 16) | (c << 8) | t), output word k & 3, k = i >> 1,
+ *     32 realizations of the word: counter (k >> 2,
+ *     (colour << 16) | (c << 8) | t, s, g), output word k & 3, k = i >> 1,
  *     colour = (x + y + z) & 1.
- *   Swap pass P, pair p, realization b: counter ((p << 3) | (b >> 2), P, g,
- *     (1 << 24) | (c << 8)), output word b & 3.
+ *   Swap pass P, pair p, realization b: counter ((p << 3) | (b >> 2),
+ *     (1 << 24) | (c << 8), P, g), output word b & 3.
  * A sweep updates colour 0 then colour 1.  Site i flips iff dE <= 0 or
  * r < metro[t][u], u = number of unsatisfied bonds of i.  After sweep s
  * (global index since creation) a swap pass runs iff swap_every > 0 and
@@ -148,6 +148,31 @@ int ea_sync(ea_ctx *ctx);
 
 /* Number of kernel launches this context has enqueued so far. */
 uint64_t ea_launch_count(const ea_ctx *ctx);
+
+/* Kernel plans.  An ensemble can run under several plans (kernel form, CTA
+ * shape, shared-memory staging); all give bit-identical results and differ
+ * only in speed.  ea_create selects a default; ea_autotune times them. */
+typedef struct {
+    int32_t form;              /* 0: unit (all slots of a group and copy in one CTA, generic);
+                                  1: unit, specialised for L % 8 == 0;
+                                  2: chunked (slots split over CTAs, swap pass as own kernels) */
+    int32_t threads;           /* threads per CTA */
+    int32_t group_threads;     /* threads per lattice (form 1: per lattice row-parity class) */
+    int32_t lattices_per_cta;
+    uint64_t smem_bytes;       /* dynamic shared memory per CTA */
+} ea_plan_desc;
+
+int ea_plan_count(const ea_ctx *ctx);
+int ea_plan_current(const ea_ctx *ctx);
+int ea_plan_info(const ea_ctx *ctx, int index, ea_plan_desc *out);
+int ea_plan_select(ea_ctx *ctx, int index);
+
+/* Autotuner: runs every plan twice for probe_sweeps sweeps (swap pass every
+ * swap_every) from the current state, restoring the state after each run,
+ * and selects the fastest.  Spins, energies and counters are unchanged.
+ * ms_out: host [ea_plan_count] receives the second run's milliseconds (may
+ * be NULL).  Synchronises the stream. */
+int ea_autotune(ea_ctx *ctx, uint32_t probe_sweeps, uint32_t swap_every, float *ms_out);
 
 /* Host-buffer entry point: creates a context from cfg, runs the sweeps of
  * args (its DEVICE output pointers must be NULL), copies the results to the

@@ -33,8 +33,9 @@
  * Conventions fixed here (the paper leaves them open):
  *  bit 1 of a spin word  <=> S = +1;  bit 1 of a bond word <=> J = -1.
  *  site i = x + L*(y + L*z); colour(i) = (x+y+z) & 1; class index k = i >> 1.
- *  Metropolis counter  = (k >> 2, s, g, (colour << 16) | (c << 8) | t), output k & 3.
- *  Swap counter        = ((p << 3) | (b >> 2), P, g, (1 << 24) | (c << 8)), output b & 3.
+ *  Metropolis counter  = (k >> 2, (colour << 16) | (c << 8) | t, s, g), output k & 3.
+ *  Swap counter        = ((p << 3) | (b >> 2), (1 << 24) | (c << 8), P, g), output b & 3.
+ *  (word 1 carries a tag in its top byte: 0 Metropolis, 1 swap).
  *  key = (seed & 0xffffffff, seed >> 32);  s = global sweep index;
  *  P = global swap-pass index.
  */
@@ -283,9 +284,9 @@ static void sweep_slot(or_sim *m, int g, int c, int t, uint64_t s)
         for (int i = 0; i < m->N; ++i) {
             if (m->colour[i] != colour) continue;
             uint32_t k = (uint32_t)i >> 1;
-            uint32_t r = or_uniform(m->seed, k >> 2, (uint32_t)s, (uint32_t)(m->group_base + g),
+            uint32_t r = or_uniform(m->seed, k >> 2,
                                     ((uint32_t)colour << 16) | ((uint32_t)c << 8) | (uint32_t)t,
-                                    (int)(k & 3u));
+                                    (uint32_t)s, (uint32_t)(m->group_base + g), (int)(k & 3u));
             for (int b = 0; b < OR_LANES; ++b) {
                 int rr = lab(m, g, c, b)[t];
                 int8_t *sp = sig(m, g, c, b, rr);
@@ -312,9 +313,9 @@ static void swap_pass(or_sim *m, int g, int c, uint64_t P, uint32_t *mask)
         int64_t *e = en(m, g, c, b);
         for (int p = 0; p + 1 < m->NT; ++p) {
             int64_t delta = e[l[p]] - e[l[p + 1]];
-            uint32_t r = or_uniform(m->seed, ((uint32_t)p << 3) | ((uint32_t)b >> 2), (uint32_t)P,
-                                    (uint32_t)(m->group_base + g), (1u << 24) | ((uint32_t)c << 8),
-                                    b & 3);
+            uint32_t r = or_uniform(m->seed, ((uint32_t)p << 3) | ((uint32_t)b >> 2),
+                                    (1u << 24) | ((uint32_t)c << 8), (uint32_t)P,
+                                    (uint32_t)(m->group_base + g), b & 3);
             int accept;
             if (delta >= 0) {
                 accept = 1;

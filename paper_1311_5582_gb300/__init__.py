@@ -45,9 +45,18 @@ class _SweepArgs(ctypes.Structure):
                 ("measure_from", ctypes.c_uint64), ("measure_every", ctypes.c_uint32)]
 
 
+class _PlanDesc(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("group_threads", ctypes.c_int32), ("lattices_per_cta", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_uint64)]
+
+
+PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked"}
+
 EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_sweep",
            "ea_pt_swap", "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
-           "ea_get_counters", "ea_sync", "ea_launch_count", "ea_run", "ea_strerror"]
+           "ea_get_counters", "ea_sync", "ea_launch_count", "ea_plan_count", "ea_plan_current",
+           "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_run", "ea_strerror"]
 
 
 def load_library(path: str | None = None):
@@ -80,12 +89,18 @@ def load_library(path: str | None = None):
     lib.ea_sync.argtypes = [vp]
     lib.ea_launch_count.argtypes = [vp]
     lib.ea_launch_count.restype = u64
+    lib.ea_plan_count.argtypes = [vp]
+    lib.ea_plan_current.argtypes = [vp]
+    lib.ea_plan_info.argtypes = [vp, i32, ctypes.POINTER(_PlanDesc)]
+    lib.ea_plan_select.argtypes = [vp, i32]
+    lib.ea_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_float)]
     lib.ea_run.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_SweepArgs), vp, vp, vp, vp, vp]
     lib.ea_strerror.argtypes = [i32]
     lib.ea_strerror.restype = ctypes.c_char_p
     for name in ("ea_build_tables", "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
                  "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
-                 "ea_get_counters", "ea_sync", "ea_run"):
+                 "ea_get_counters", "ea_sync", "ea_run", "ea_plan_count", "ea_plan_current",
+                 "ea_plan_info", "ea_plan_select", "ea_autotune"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -251,6 +266,31 @@ class Ensemble:
 
     def sync(self):
         _check(self.lib.ea_sync(self.ctx), "ea_sync")
+
+    # -- kernel plans and the autotuner
+    def plans(self) -> list[dict]:
+        out = []
+        for i in range(self.lib.ea_plan_count(self.ctx)):
+            d = _PlanDesc()
+            _check(self.lib.ea_plan_info(self.ctx, i, ctypes.byref(d)), "ea_plan_info")
+            out.append({"form": PLAN_FORMS.get(d.form, d.form), "threads": d.threads,
+                        "group_threads": d.group_threads, "lattices_per_cta": d.lattices_per_cta,
+                        "smem_bytes": d.smem_bytes})
+        return out
+
+    @property
+    def plan(self) -> int:
+        return int(self.lib.ea_plan_current(self.ctx))
+
+    def select_plan(self, index: int):
+        _check(self.lib.ea_plan_select(self.ctx, int(index)), "ea_plan_select")
+
+    def autotune(self, probe_sweeps: int = 200, swap_every: int = 1) -> list[float]:
+        """Times every plan from the current state (restored after each run), selects the fastest."""
+        n = self.lib.ea_plan_count(self.ctx)
+        ms = (ctypes.c_float * n)()
+        _check(self.lib.ea_autotune(self.ctx, int(probe_sweeps), int(swap_every), ms), "ea_autotune")
+        return list(ms)
 
 
 def ea_run(L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every, measure_from=0,

@@ -21,7 +21,9 @@ struct ea_ctx {
     int *d_err;
     uint64_t sweep, pass;
     uint64_t launches;
-    ea::Plan plan;
+    std::vector<ea::Plan> plans;   // every kernel plan that can run this ensemble
+    int plan_idx;
+    ea::Plan plan;                 // plans[plan_idx]
     ea::RoundKeys rk;
 };
 
@@ -168,9 +170,8 @@ int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
     int rc = validate_tables(cfg->metro, cfg->swapt, cfg->n_temps, cfg->swap_len);
     if (rc != EA_OK) return rc;
 
-    ea_ctx *c = new (std::nothrow) ea_ctx;
+    ea_ctx *c = new (std::nothrow) ea_ctx();
     if (!c) return EA_ENOMEM;
-    std::memset(c, 0, sizeof(*c));
     c->L = L;
     c->G = cfg->n_groups;
     c->NT = cfg->n_temps;
@@ -187,10 +188,13 @@ int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (e != cudaSuccess) { delete c; return cuda_fail(e); }
     c->smem_optin = (size_t)optin;
-    if (!ea::make_plan((int)L, (int)c->NT, (int)c->C, c->smem_optin, 0, &c->plan)) {
+    c->plans = ea::make_plans((int)L, (int)c->NT, (int)c->C, c->swap_len, c->smem_optin);
+    if (c->plans.empty()) {
         delete c;
         return EA_EUNSUPPORTED;
     }
+    c->plan_idx = 0;
+    c->plan = c->plans[0];
 
     const size_t n_spin = (size_t)c->G * c->NT * c->C * c->N;
     const size_t n_bond = (size_t)c->G * 3 * c->N;
@@ -245,12 +249,15 @@ void ea_destroy(ea_ctx *ctx)
     free_ctx(ctx);
 }
 
-int ea_sweep(ea_ctx *c, const ea_sweep_args *args)
+}  // extern "C"
+
+namespace {
+
+// Enqueues the kernels of n sweeps starting at the context's counters with
+// the given plan; does not advance the counters.
+int run_sweeps(ea_ctx *c, const ea_sweep_args *args, const ea::Plan &plan)
 {
-    if (!c || !args) return EA_EINVAL;
-    if ((args->qhist) && c->C != 2) return EA_EINVAL;
     const uint32_t n = args->n_sweeps;
-    if (n == 0) return EA_OK;
     cudaStream_t st = c->stream;
     ea::SweepLaunch a = base_launch(c);
     a.swap_every = args->swap_every;
@@ -262,58 +269,149 @@ int ea_sweep(ea_ctx *c, const ea_sweep_args *args)
     a.measure_from = args->measure_from;
     a.measure_every = args->measure_every;
     const uint64_t s_begin = c->sweep;
-    uint64_t passes = 0;
-    for (uint64_t s = s_begin; s < s_begin + n; ++s) passes += swap_after(s, args->swap_every);
-
-    if (c->plan.unit) {
+    if (plan.unit) {
         a.s0 = s_begin;
         a.n_sweeps = n;
         a.P0 = c->pass;
         a.pass_local0 = 0;
         const bool overlaps = c->C == 2 && args->qhist != nullptr && args->measure_every != 0;
-        EA_TRY(ea::launch_sweep_unit(a, (int)c->L, c->plan, overlaps, st, &c->launches));
-    } else {
-        // Chunked form: sweep kernels run up to each swap or measured sweep;
-        // swap passes and measurements run as their own kernels in between.
-        uint64_t s = s_begin;
-        uint32_t pass_local = 0;
-        const uint64_t s_end = s_begin + n;
-        while (s < s_end) {
-            uint64_t e = s;
-            while (e + 1 < s_end && !swap_after(e, args->swap_every) &&
-                   !measured(e, args->measure_from, args->measure_every))
-                ++e;
-            // [s, e] inclusive
-            ea::SweepLaunch b = a;
-            b.s0 = s;
-            b.n_sweeps = (uint32_t)(e - s + 1);
-            b.qhist = nullptr;
-            b.esum = nullptr;
-            b.measure_every = 0;
-            const bool sw = swap_after(e, args->swap_every);
-            const bool me = measured(e, args->measure_from, args->measure_every);
-            b.compute_energy_last = 1;
-            EA_TRY(ea::launch_sweep_chunk(b, (int)c->L, c->plan, st, &c->launches));
-            if (sw) {
-                b.P0 = c->pass + pass_local;
-                b.pass_local0 = pass_local;
-                int32_t *elog_row = args->energy_log
-                    ? args->energy_log + (size_t)(e - s_begin) * c->G * c->NT * c->C * ea::kLanes
-                    : nullptr;
-                EA_TRY(ea::launch_swap_global(b, (int)c->L, c->pass + pass_local, c->d_masks, elog_row,
-                                              st, &c->launches));
-                ++pass_local;
-            }
-            if (me)
-                EA_TRY(ea::launch_measure(c->d_spins, c->d_energy, (int)c->L, c->G, c->NT, c->C,
-                                          nullptr, nullptr, args->qhist, args->esum, st,
-                                          &c->launches));
-            s = e + 1;
-        }
+        if (plan.form == ea::kFormUnitFast)
+            EA_TRY(ea::launch_sweep_unit_fast(a, (int)c->L, plan.threads_per_lattice, plan.smem,
+                                              plan.swap_in_smem, overlaps, st, &c->launches));
+        else
+            EA_TRY(ea::launch_sweep_unit(a, (int)c->L, plan, overlaps, st, &c->launches));
+        return EA_OK;
     }
+    // Chunked form: sweep kernels run up to each swap or measured sweep;
+    // swap passes and measurements run as their own kernels in between.
+    uint64_t s = s_begin;
+    uint32_t pass_local = 0;
+    const uint64_t s_end = s_begin + n;
+    while (s < s_end) {
+        uint64_t e = s;
+        while (e + 1 < s_end && !swap_after(e, args->swap_every) &&
+               !measured(e, args->measure_from, args->measure_every))
+            ++e;
+        // sweeps [s, e]
+        ea::SweepLaunch b = a;
+        b.s0 = s;
+        b.n_sweeps = (uint32_t)(e - s + 1);
+        b.qhist = nullptr;
+        b.esum = nullptr;
+        b.measure_every = 0;
+        const bool sw = swap_after(e, args->swap_every);
+        const bool me = measured(e, args->measure_from, args->measure_every);
+        b.compute_energy_last = 1;
+        EA_TRY(ea::launch_sweep_chunk(b, (int)c->L, plan, st, &c->launches));
+        if (sw) {
+            b.P0 = c->pass + pass_local;
+            b.pass_local0 = pass_local;
+            int32_t *elog_row = args->energy_log
+                ? args->energy_log + (size_t)(e - s_begin) * c->G * c->NT * c->C * ea::kLanes
+                : nullptr;
+            EA_TRY(ea::launch_swap_global(b, (int)c->L, c->pass + pass_local, c->d_masks, elog_row,
+                                          st, &c->launches));
+            ++pass_local;
+        }
+        if (me)
+            EA_TRY(ea::launch_measure(c->d_spins, c->d_energy, (int)c->L, c->G, c->NT, c->C,
+                                      nullptr, nullptr, args->qhist, args->esum, st, &c->launches));
+        s = e + 1;
+    }
+    return EA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ea_sweep(ea_ctx *c, const ea_sweep_args *args)
+{
+    if (!c || !args) return EA_EINVAL;
+    if ((args->qhist) && c->C != 2) return EA_EINVAL;
+    const uint32_t n = args->n_sweeps;
+    if (n == 0) return EA_OK;
+    uint64_t passes = 0;
+    for (uint64_t s = c->sweep; s < c->sweep + n; ++s) passes += swap_after(s, args->swap_every);
+    const int rc = run_sweeps(c, args, c->plan);
+    if (rc != EA_OK) return rc;
     c->sweep += n;
     c->pass += passes;
     return EA_OK;
+}
+
+int ea_plan_count(const ea_ctx *c) { return c ? (int)c->plans.size() : EA_EINVAL; }
+
+int ea_plan_current(const ea_ctx *c) { return c ? c->plan_idx : EA_EINVAL; }
+
+int ea_plan_info(const ea_ctx *c, int index, ea_plan_desc *out)
+{
+    if (!c || !out || index < 0 || index >= (int)c->plans.size()) return EA_EINVAL;
+    const ea::Plan &p = c->plans[(size_t)index];
+    out->form = p.form;
+    out->threads = p.threads;
+    out->group_threads = p.threads_per_lattice;
+    out->lattices_per_cta = p.lattices_per_cta;
+    out->smem_bytes = p.smem;
+    return EA_OK;
+}
+
+int ea_plan_select(ea_ctx *c, int index)
+{
+    if (!c || index < 0 || index >= (int)c->plans.size()) return EA_EINVAL;
+    c->plan_idx = index;
+    c->plan = c->plans[(size_t)index];
+    return EA_OK;
+}
+
+int ea_autotune(ea_ctx *c, uint32_t probe_sweeps, uint32_t swap_every, float *ms_out)
+{
+    if (!c || probe_sweeps == 0) return EA_EINVAL;
+    const size_t n_spin = (size_t)c->G * c->NT * c->C * c->N;
+    const size_t n_e = (size_t)c->G * c->C * c->NT * ea::kLanes;
+    uint32_t *save_s = nullptr;
+    int32_t *save_e = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaError_t e = cudaMalloc(&save_s, n_spin * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&save_e, n_e * 4);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save_s, c->d_spins, n_spin * 4, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(save_e, c->d_energy, n_e * 4, cudaMemcpyDeviceToDevice, c->stream);
+    int best = c->plan_idx, rc = EA_OK;
+    float best_ms = 0.f;
+    ea_sweep_args args;
+    std::memset(&args, 0, sizeof(args));
+    args.n_sweeps = probe_sweeps;
+    args.swap_every = swap_every;
+    for (size_t i = 0; e == cudaSuccess && rc == EA_OK && i < c->plans.size(); ++i) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && rc == EA_OK && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(ev0, c->stream);
+            if (e == cudaSuccess) rc = run_sweeps(c, &args, c->plans[i]);
+            if (e == cudaSuccess && rc == EA_OK) e = cudaEventRecord(ev1, c->stream);
+            if (e == cudaSuccess && rc == EA_OK) e = cudaEventSynchronize(ev1);
+            if (e == cudaSuccess && rc == EA_OK) e = cudaEventElapsedTime(&ms, ev0, ev1);
+            // every plan starts from the same state
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->d_spins, save_s, n_spin * 4, cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->d_energy, save_e, n_e * 4, cudaMemcpyDeviceToDevice, c->stream);
+        }
+        if (ms_out) ms_out[i] = ms;
+        if (e == cudaSuccess && rc == EA_OK && (i == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = (int)i;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(save_s);
+    cudaFree(save_e);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (rc != EA_OK) return rc;
+    if (e != cudaSuccess) return cuda_fail(e);
+    return ea_plan_select(c, best);
 }
 
 int ea_pt_swap(ea_ctx *c, uint32_t *masks)

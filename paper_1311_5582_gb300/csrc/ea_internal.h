@@ -10,6 +10,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace ea {
@@ -54,18 +56,29 @@ struct SweepLaunch {
     int compute_energy_last;        // chunked form: energies after the last sweep
 };
 
+enum PlanForm { kFormUnit = 0, kFormUnitFast = 1, kFormChunked = 2 };
+
 struct Plan {
-    bool unit;          // all NT lattices of a (g, c) unit in one CTA (swaps in-kernel)
-    int threads_per_lattice;
-    int lattices_per_cta;   // == NT for unit
+    int form;               // PlanForm
+    bool unit;              // all NT lattices of a (g, c) unit in one CTA (swaps in-kernel)
+    int threads_per_lattice;    // generic forms: threads per lattice; fast form: threads per
+                                // (lattice, row parity) class
+    int lattices_per_cta;   // == NT for the unit forms
     int threads;
     size_t smem;
     bool j_in_smem;
+    bool swap_in_smem;      // unit forms: swap threshold table staged in shared memory
 };
 
 bool supported_L(int L);
-// Chooses the kernel form for (L, NT) given the device's opt-in shared memory.
-bool make_plan(int L, int NT, int C, size_t smem_optin, int tpl_override, Plan *plan);
+// Every kernel plan that can run (L, NT) within the device's opt-in shared
+// memory, best guess first.  Empty if none.
+std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin);
+
+int fast_unit_threads(int L, int HP, int NT);
+cudaError_t launch_sweep_unit_fast(const SweepLaunch &a, int L, int HP, size_t smem,
+                                   bool swap_in_smem, bool cluster_measure, cudaStream_t st,
+                                   uint64_t *launches);
 
 // Launchers: return cudaSuccess or the launch error.  Each adds its kernel
 // count to *launches.

@@ -1,369 +1,12 @@
-// Kernels of the parallel-tempering Metropolis simulation of the 3D +-J
-// Edwards-Anderson model, written for sm_103a.
-//
-// Sec. 4.3 of the paper turns the Metropolis step into bit operations on
-// multispin-coded words (XOR bond energies, a local energy E in 0..6, a table
-// compare).  Here 32 disorder realizations share a word (one bit each), so one
-// 32-bit operation advances 32 realizations:
-//   e_d = s ^ s_nb ^ J_d                      (Eq. e: 1 = unsatisfied bond)
-//   (u2 u1 u0) = e_0 + ... + e_5              (bit-sliced full-adder tree)
-//   flip lanes with u >= m, m = #thresholds r has passed (Eq. r, Sec. 4.3.2)
-// which is exact because the three thresholds of a slot are monotone.
-// Random numbers come from Philox4x32-10 (Sec. 4.3.2 evaluates this generator
-// family), one 32-bit output per (group, slot, copy, sweep, site) shared by
-// the 32 lanes; one call serves the four sites of a quad.
-#include <cooperative_groups.h>
-
-#include "ea_internal.h"
-
-namespace cg = cooperative_groups;
+// Generic kernels of the parallel-tempering Metropolis simulation of the 3D
+// +-J Edwards-Anderson model for sm_103a (any supported even L): the unit and
+// chunked sweep kernels, the global swap pass, energy recomputation,
+// measurement and layout conversion, plus the launch plan.
+#include "ea_device.cuh"
 
 namespace ea {
 
 namespace {
-
-constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;   // Philox4x32 multipliers
-constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;   // Philox Weyl key increments
-constexpr uint32_t kFull = 0xFFFFFFFFu;
-
-template <int L>
-struct Geo {
-    static constexpr int N = L * L * L;
-    static constexpr int H = N / 2;   // sites per colour
-    static constexpr int R = L / 2;   // sites per row per colour
-    static constexpr int Q = N / 8;   // quads (four consecutive class indices) per colour
-};
-
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                        const RoundKeys &rk)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = kM0 * c0, hi0 = __umulhi(kM0, c0);
-        const uint32_t lo1 = kM1 * c2, hi1 = __umulhi(kM1, c2);
-        const uint32_t n0 = hi1 ^ c1 ^ rk.k[2 * r];
-        const uint32_t n2 = hi0 ^ c3 ^ rk.k[2 * r + 1];
-        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    }
-    return make_uint4(c0, c1, c2, c3);
-}
-
-__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c)
-{
-    return (a & b) | (c & (a | b));
-}
-__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &cy)
-{
-    s = a ^ b ^ c;
-    cy = maj3(a, b, c);
-}
-
-// The words one quad update reads: own spins, the six neighbour spins and the
-// six bond words of each of its four sites.  Index order of the six:
-// +x, -x, +y, -y, +z, -z; the -d bond's J is stored at the neighbour.
-struct Quad {
-    uint32_t s[4];
-    uint32_t nb[6][4];
-    uint32_t jb[6][4];
-};
-
-// Loads quad q of colour col.  S: lattice base [2][H]; J: bond base [3][2][H].
-// Works on shared or global pointers.
-template <int L>
-__device__ __forceinline__ void load_quad(const uint32_t *__restrict__ S,
-                                          const uint32_t *__restrict__ J, int col, int q, Quad &o)
-{
-    using Gm = Geo<L>;
-    constexpr int N = Gm::N, H = Gm::H, R = Gm::R;
-    const uint32_t *Sc = S + col * H;
-    const uint32_t *So = S + (col ^ 1) * H;
-    const int k0 = 4 * q;
-    if constexpr (L % 8 == 0) {
-        // The quad's four sites sit in one x-row: vector loads.
-        const int row = k0 / R, m0 = k0 - row * R;
-        const int y = row % L, z = row / L;
-        const int px = (y + z + col) & 1;      // x parity of this colour in this row
-        const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
-        const int zp = (z + 1 == L) ? 0 : z + 1, zm = (z == 0) ? L - 1 : z - 1;
-        const int rowb = row * R;
-        const uint4 own = *reinterpret_cast<const uint4 *>(Sc + k0);
-        const uint4 xo = *reinterpret_cast<const uint4 *>(So + k0);
-        const uint4 vyp = *reinterpret_cast<const uint4 *>(So + m0 + R * (yp + L * z));
-        const uint4 vym = *reinterpret_cast<const uint4 *>(So + m0 + R * (ym + L * z));
-        const uint4 vzp = *reinterpret_cast<const uint4 *>(So + m0 + R * (y + L * zp));
-        const uint4 vzm = *reinterpret_cast<const uint4 *>(So + m0 + R * (y + L * zm));
-        const uint4 jcx = *reinterpret_cast<const uint4 *>(J + 0 * N + col * H + k0);
-        const uint4 jcy = *reinterpret_cast<const uint4 *>(J + 1 * N + col * H + k0);
-        const uint4 jcz = *reinterpret_cast<const uint4 *>(J + 2 * N + col * H + k0);
-        const uint4 jox = *reinterpret_cast<const uint4 *>(J + 0 * N + (col ^ 1) * H + k0);
-        const uint4 joy = *reinterpret_cast<const uint4 *>(J + 1 * N + (col ^ 1) * H + m0 + R * (ym + L * z));
-        const uint4 joz = *reinterpret_cast<const uint4 *>(J + 2 * N + (col ^ 1) * H + m0 + R * (y + L * zm));
-        // x neighbours: same class index in the other colour, plus one word
-        // across the quad edge (x-1 of the first site when px = 0, x+1 of the
-        // last site when px = 1), wrapping inside the row.
-        uint32_t xs_extra, xj_extra;
-        if constexpr (R == 4) {
-            xs_extra = px ? xo.x : xo.w;
-            xj_extra = jox.w;   // only used when px = 0
-        } else {
-            const int ie = px ? (m0 + 4 == R ? 0 : m0 + 4) : (m0 == 0 ? R - 1 : m0 - 1);
-            xs_extra = So[rowb + ie];
-            xj_extra = J[0 * N + (col ^ 1) * H + rowb + ie];
-        }
-        o.s[0] = own.x; o.s[1] = own.y; o.s[2] = own.z; o.s[3] = own.w;
-        // +x
-        o.nb[0][0] = px ? xo.y : xo.x;
-        o.nb[0][1] = px ? xo.z : xo.y;
-        o.nb[0][2] = px ? xo.w : xo.z;
-        o.nb[0][3] = px ? xs_extra : xo.w;
-        // -x
-        o.nb[1][0] = px ? xo.x : xs_extra;
-        o.nb[1][1] = px ? xo.y : xo.x;
-        o.nb[1][2] = px ? xo.z : xo.y;
-        o.nb[1][3] = px ? xo.w : xo.z;
-        o.nb[2][0] = vyp.x; o.nb[2][1] = vyp.y; o.nb[2][2] = vyp.z; o.nb[2][3] = vyp.w;
-        o.nb[3][0] = vym.x; o.nb[3][1] = vym.y; o.nb[3][2] = vym.z; o.nb[3][3] = vym.w;
-        o.nb[4][0] = vzp.x; o.nb[4][1] = vzp.y; o.nb[4][2] = vzp.z; o.nb[4][3] = vzp.w;
-        o.nb[5][0] = vzm.x; o.nb[5][1] = vzm.y; o.nb[5][2] = vzm.z; o.nb[5][3] = vzm.w;
-        o.jb[0][0] = jcx.x; o.jb[0][1] = jcx.y; o.jb[0][2] = jcx.z; o.jb[0][3] = jcx.w;
-        // -x bond: J of the -x neighbour
-        o.jb[1][0] = px ? jox.x : xj_extra;
-        o.jb[1][1] = px ? jox.y : jox.x;
-        o.jb[1][2] = px ? jox.z : jox.y;
-        o.jb[1][3] = px ? jox.w : jox.z;
-        o.jb[2][0] = jcy.x; o.jb[2][1] = jcy.y; o.jb[2][2] = jcy.z; o.jb[2][3] = jcy.w;
-        o.jb[3][0] = joy.x; o.jb[3][1] = joy.y; o.jb[3][2] = joy.z; o.jb[3][3] = joy.w;
-        o.jb[4][0] = jcz.x; o.jb[4][1] = jcz.y; o.jb[4][2] = jcz.z; o.jb[4][3] = jcz.w;
-        o.jb[5][0] = joz.x; o.jb[5][1] = joz.y; o.jb[5][2] = joz.z; o.jb[5][3] = joz.w;
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int k = k0 + j;
-            const int row = k / R, m = k - row * R;
-            const int y = row % L, z = row / L;
-            const int px = (y + z + col) & 1;
-            const int rowb = row * R;
-            const int kxp = rowb + (px ? (m + 1 == R ? 0 : m + 1) : m);
-            const int kxm = rowb + (px ? m : (m == 0 ? R - 1 : m - 1));
-            const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
-            const int zp = (z + 1 == L) ? 0 : z + 1, zm = (z == 0) ? L - 1 : z - 1;
-            const int kyp = m + R * (yp + L * z), kym = m + R * (ym + L * z);
-            const int kzp = m + R * (y + L * zp), kzm = m + R * (y + L * zm);
-            o.s[j] = Sc[k];
-            o.nb[0][j] = So[kxp];
-            o.nb[1][j] = So[kxm];
-            o.nb[2][j] = So[kyp];
-            o.nb[3][j] = So[kym];
-            o.nb[4][j] = So[kzp];
-            o.nb[5][j] = So[kzm];
-            o.jb[0][j] = J[0 * N + col * H + k];
-            o.jb[1][j] = J[0 * N + (col ^ 1) * H + kxm];
-            o.jb[2][j] = J[1 * N + col * H + k];
-            o.jb[3][j] = J[1 * N + (col ^ 1) * H + kym];
-            o.jb[4][j] = J[2 * N + col * H + k];
-            o.jb[5][j] = J[2 * N + (col ^ 1) * H + kzm];
-        }
-    }
-}
-
-// Number of unsatisfied bonds u = (u2 u1 u0) of the 32 lanes of one site.
-__device__ __forceinline__ void unsat_count(uint32_t s, const uint32_t (&nb)[6][4],
-                                            const uint32_t (&jb)[6][4], int j, uint32_t &u0,
-                                            uint32_t &u1, uint32_t &u2)
-{
-    const uint32_t e0 = s ^ nb[0][j] ^ jb[0][j];
-    const uint32_t e1 = s ^ nb[1][j] ^ jb[1][j];
-    const uint32_t e2 = s ^ nb[2][j] ^ jb[2][j];
-    const uint32_t e3 = s ^ nb[3][j] ^ jb[3][j];
-    const uint32_t e4 = s ^ nb[4][j] ^ jb[4][j];
-    const uint32_t e5 = s ^ nb[5][j] ^ jb[5][j];
-    uint32_t a0, a1, b0, b1;
-    full_add(e0, e1, e2, a0, a1);
-    full_add(e3, e4, e5, b0, b1);
-    u0 = a0 ^ b0;
-    const uint32_t c = a0 & b0;
-    full_add(a1, b1, c, u1, u2);
-}
-
-// Flip mask of a site: all lanes with dE <= 0 (u >= 3), and lanes with
-// u >= m where m counts the thresholds r is not below (t0 <= t1 <= t2).
-__device__ __forceinline__ uint32_t flip_mask(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t r,
-                                              uint32_t t0, uint32_t t1, uint32_t t2)
-{
-    const uint32_t ge2 = u2 | u1;
-    const uint32_t ge1 = ge2 | u0;
-    const uint32_t ge3 = u2 | (u1 & u0);
-    return (r < t0) ? kFull : (r < t1) ? ge1 : (r < t2) ? ge2 : ge3;
-}
-
-// Sum of four 3-bit lane values (x2 x1 x0)[j] into a 5-bit value A.
-__device__ __forceinline__ void quad_sum(const uint32_t (&x0)[4], const uint32_t (&x1)[4],
-                                         const uint32_t (&x2)[4], uint32_t (&A)[5])
-{
-    uint32_t s, ca, cb, c1, c2, c3, s2, k1, k2, k3;
-    full_add(x0[0], x0[1], x0[2], s, ca);
-    A[0] = s ^ x0[3]; cb = s & x0[3];
-    full_add(ca, cb, x1[0], s, c1);
-    full_add(s, x1[1], x1[2], s2, c2);
-    A[1] = s2 ^ x1[3]; c3 = s2 & x1[3];
-    full_add(c1, c2, c3, s, k1);
-    full_add(x2[0], x2[1], x2[2], s2, k2);
-    full_add(s, s2, x2[3], A[2], k3);
-    full_add(k1, k2, k3, A[3], A[4]);
-}
-
-// acc += A (bit-sliced ripple add of a 5-bit value into kPlanes planes).
-__device__ __forceinline__ void acc_add5(uint32_t (&acc)[kPlanes], const uint32_t (&A)[5])
-{
-    uint32_t cy = acc[0] & A[0];
-    acc[0] ^= A[0];
-#pragma unroll
-    for (int i = 1; i < 5; ++i) {
-        uint32_t s, c;
-        full_add(acc[i], A[i], cy, s, c);
-        acc[i] = s;
-        cy = c;
-    }
-#pragma unroll
-    for (int i = 5; i < kPlanes; ++i) {
-        const uint32_t c = acc[i] & cy;
-        acc[i] ^= cy;
-        cy = c;
-    }
-}
-
-// acc += popcount-per-lane of four words (3-bit partial sum, then ripple).
-__device__ __forceinline__ void acc_add_words4(uint32_t (&acc)[kPlanes], uint32_t w0, uint32_t w1,
-                                               uint32_t w2, uint32_t w3)
-{
-    uint32_t s, c1;
-    full_add(w0, w1, w2, s, c1);
-    const uint32_t b0 = s ^ w3, c2 = s & w3;
-    const uint32_t b1 = c1 ^ c2, b2 = c1 & c2;
-    uint32_t A[5] = {b0, b1, b2, 0u, 0u};
-    acc_add5(acc, A);
-}
-
-// 32x32 bit transpose across a warp: afterwards bit j of lane b's word is
-// bit b of lane j's word before.
-__device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane)
-{
-#define EA_TSTEP(S, M)                                                              \
-    {                                                                               \
-        const uint32_t y = __shfl_xor_sync(kFull, x, S);                            \
-        x = (lane & S) ? ((x & ~(M)) | ((y >> S) & (M))) : ((x & (M)) | ((y << S) & ~(M))); \
-    }
-    EA_TSTEP(16, 0x0000FFFFu)
-    EA_TSTEP(8, 0x00FF00FFu)
-    EA_TSTEP(4, 0x0F0F0F0Fu)
-    EA_TSTEP(2, 0x33333333u)
-    EA_TSTEP(1, 0x55555555u)
-#undef EA_TSTEP
-    return x;
-}
-
-// Adds each thread's bit-sliced per-lane counter into out[group][lane],
-// where a group is tpl consecutive threads (tpl a power of two dividing 32,
-// or a multiple of 32).  The whole warp must call this.
-__device__ __forceinline__ void reduce_counters(const uint32_t (&acc)[kPlanes], int tpl,
-                                                int *out, int lane, int warp)
-{
-    uint32_t y[kPlanes];
-#pragma unroll
-    for (int p = 0; p < kPlanes; ++p) y[p] = warp_transpose(acc[p], lane);
-    if (tpl >= 32) {
-        int cnt = 0;
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) cnt += __popc(y[p]) << p;
-        const int grp = (warp * 32) / tpl;
-        atomicAdd(&out[grp * kLanes + lane], cnt);
-    } else {
-        const int ng = 32 / tpl;
-        const uint32_t base = (tpl == 32) ? kFull : ((1u << tpl) - 1u);
-        for (int gi = 0; gi < ng; ++gi) {
-            const uint32_t gm = base << (gi * tpl);
-            int cnt = 0;
-#pragma unroll
-            for (int p = 0; p < kPlanes; ++p) cnt += __popc(y[p] & gm) << p;
-            const int grp = (warp * 32 + gi * tpl) / tpl;
-            atomicAdd(&out[grp * kLanes + lane], cnt);
-        }
-    }
-}
-
-// One half-sweep (colour col) of one lattice by the tpl threads of its group;
-// thread tl takes quads tl, tl + tpl, ...  With WITH_E, acc receives the
-// post-update unsatisfied-bond counts of the colour-1 sites (every bond has
-// exactly one colour-1 end, so they sum to U, E = 2U - 3N).
-template <int L, bool WITH_E>
-__device__ __forceinline__ void half_sweep(uint32_t *S, const uint32_t *J, int col, int tl, int tpl,
-                                           int qper, uint32_t s, uint32_t g, uint32_t ctag,
-                                           const RoundKeys &rk, uint32_t t0, uint32_t t1,
-                                           uint32_t t2, uint32_t (&acc)[kPlanes])
-{
-    using Gm = Geo<L>;
-    uint32_t *Sc = S + col * Gm::H;
-    for (int j = 0; j < qper; ++j) {
-        const int q = tl + j * tpl;
-        if (q >= Gm::Q) break;
-        Quad o;
-        load_quad<L>(S, J, col, q, o);
-        const uint4 r = philox((uint32_t)q, s, g, ctag, rk);
-        const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-        uint32_t x0[4], x1[4], x2[4], ns[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            uint32_t u0, u1, u2;
-            unsat_count(o.s[i], o.nb, o.jb, i, u0, u1, u2);
-            const uint32_t f = flip_mask(u0, u1, u2, rr[i], t0, t1, t2);
-            ns[i] = o.s[i] ^ f;
-            if constexpr (WITH_E) {
-                // after a flip the six bonds change state: u' = 6 - u
-                x0[i] = u0;
-                x1[i] = u1 ^ (f & ~u0);
-                x2[i] = u2 ^ (f & ~(u0 & u1));
-            }
-        }
-        *reinterpret_cast<uint4 *>(Sc + 4 * q) = make_uint4(ns[0], ns[1], ns[2], ns[3]);
-        if constexpr (WITH_E) {
-            uint32_t A[5];
-            quad_sum(x0, x1, x2, A);
-            acc_add5(acc, A);
-        }
-    }
-}
-
-__device__ __forceinline__ bool swap_after(uint64_t s, uint32_t swap_every)
-{
-    return swap_every != 0 && ((s + 1) % swap_every) == 0;
-}
-__device__ __forceinline__ bool measured(uint64_t s, uint64_t from, uint32_t every)
-{
-    return every != 0 && s >= from && ((s - from) % every) == 0;
-}
-
-// Number of leading entries of a non-increasing threshold row above r: the
-// swap of pair p is accepted iff E_p - E_{p+1} >= -4 * K (Sec. 2.4 with the
-// integer table of Sec. 4.3.2).
-__device__ __forceinline__ int accept_bound(const uint32_t *row, uint32_t len, uint32_t r)
-{
-    uint32_t lo = 0, hi = len;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(row + mid) > r) lo = mid + 1; else hi = mid;
-    }
-    return -4 * (int)lo;
-}
-
-__device__ __forceinline__ uint32_t swap_uniform(const RoundKeys &rk, int p, int b, uint64_t P,
-                                                 uint32_t g, int c)
-{
-    const uint4 v = philox(((uint32_t)p << 3) | ((uint32_t)b >> 2), (uint32_t)P, g,
-                           (1u << 24) | ((uint32_t)c << 8), rk);
-    const int w = b & 3;
-    return w == 0 ? v.x : w == 1 ? v.y : w == 2 ? v.z : v.w;
-}
-
 // ------------------------------------------------------------------ unit kernel
 // One CTA owns all NT lattices of one (group, copy) unit in shared memory and
 // runs the whole sweep range: Metropolis half-sweeps, per-lane energies,
@@ -371,17 +14,9 @@ __device__ __forceinline__ uint32_t swap_uniform(const RoundKeys &rk, int p, int
 // measurement the two copies of a group form a 2-CTA cluster and read each
 // other's lattices through distributed shared memory.
 
-struct UnitSmem {
-    static size_t bytes(int N, int NT)
-    {
-        return (size_t)NT * N * 4 + (size_t)3 * N * 4 + (size_t)kMaxTemps * kLanes * 4 * 3 +
-               (size_t)kMaxTemps * 4;
-    }
-};
-
 template <int L>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure)
+k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure, int swap_in_smem)
 {
     using Gm = Geo<L>;
     constexpr int N = Gm::N;
@@ -389,10 +24,11 @@ k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure
     const int NT = (int)a.NT;
     uint32_t *S = reinterpret_cast<uint32_t *>(smem_u4);     // [NT][2][H]
     uint32_t *Js = S + (size_t)NT * N;                        // [3][2][H]
-    int *E = reinterpret_cast<int *>(Js + 3 * N);             // [64][32] U, then E, by slot
+    int *E = reinterpret_cast<int *>(Js + 3 * N);             // [64][32] energies by slot
     int *bnd = E + kMaxTemps * kLanes;                        // [64][32] swap accept bounds
     int *nd = bnd + kMaxTemps * kLanes;                       // [64][32] overlap counts
     uint32_t *msk = reinterpret_cast<uint32_t *>(nd + kMaxTemps * kLanes);  // [64]
+    uint32_t *Tsw = msk + kMaxTemps;                          // [NT-1][swap_len] if swap_in_smem
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t unit = blockIdx.x;
@@ -407,6 +43,12 @@ k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure
         reinterpret_cast<uint4 *>(S)[w] = reinterpret_cast<const uint4 *>(gS)[w];
     for (int w = tid; w < 3 * N / 4; w += nthr)
         reinterpret_cast<uint4 *>(Js)[w] = reinterpret_cast<const uint4 *>(gJ)[w];
+    const uint32_t *swt = a.swapt;
+    if (swap_in_smem) {
+        const int nsw = (NT - 1) * (int)a.swap_len;
+        for (int w = tid; w < nsw; w += nthr) Tsw[w] = a.swapt[w];
+        swt = Tsw;
+    }
     const uint32_t t0 = a.metro[l * 3 + 0], t1 = a.metro[l * 3 + 1], t2 = a.metro[l * 3 + 2];
     uint32_t *mine = S + (size_t)l * N;
     __syncthreads();
@@ -415,66 +57,74 @@ k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure
     uint32_t pass_local = a.pass_local0;
     for (uint32_t n = 0; n < a.n_sweeps; ++n) {
         const uint64_t s = a.s0 + n;
-        const bool swap_now = swap_after(s, a.swap_every);
+        const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
         const bool meas = measured(s, a.measure_from, a.measure_every);
         const bool needE = swap_now || a.energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
         uint32_t acc[kPlanes];
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-        if (needE)
-            for (int i = tid; i < NT * kLanes; i += nthr) E[i] = 0;
+        if (needE)   // counters add 2 per unsatisfied bond: E = 2U - 3N
+            for (int i = tid; i < NT * kLanes; i += nthr) E[i] = -3 * N;
+        if (swap_now) {
+            // Swap acceptance bounds depend only on the pass index: compute them
+            // now; they are read after the half-sweeps' barriers.
+            for (int i = tid; i < (NT - 1) * kLanes; i += nthr) {
+                const int p = i >> 5, b = i & 31;
+                const uint32_t r = swap_uniform(a.rk, p, b, P, g, c);
+                bnd[i] = accept_bound(swt + (size_t)p * a.swap_len, a.swap_len, r);
+            }
+        }
         half_sweep<L, false>(mine, Js, 0, tl, tpl, qper, (uint32_t)s, g,
                              (0u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
         __syncthreads();
         if (needE) {
             half_sweep<L, true>(mine, Js, 1, tl, tpl, qper, (uint32_t)s, g,
                                 (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
-            reduce_counters(acc, tpl, E, lane, warp);
-            __syncthreads();
-            for (int i = tid; i < NT * kLanes; i += nthr) E[i] = 2 * E[i] - 3 * N;
-            __syncthreads();
+            reduce_counters(acc, tpl, E, lane, warp, 2);
         } else {
             half_sweep<L, false>(mine, Js, 1, tl, tpl, qper, (uint32_t)s, g,
                                  (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
+        }
+        __syncthreads();
+        if (swap_now) {
+            if (warp == 0) {
+                // Sequential pairs (0,1), (1,2), ... per realization lane; the
+                // configuration carried upward is `cur`.  Loads run one pair ahead.
+                int cur = E[lane];
+                int nxt = E[kLanes + lane];
+                int bb = bnd[lane];
+                for (int p = 0; p + 1 < NT; ++p) {
+                    const int nxt2 = (p + 2 < NT) ? E[(p + 2) * kLanes + lane] : 0;
+                    const int bb2 = (p + 2 < NT) ? bnd[(p + 1) * kLanes + lane] : 0;
+                    const bool ok = (cur - nxt) >= bb;
+                    const uint32_t m = __ballot_sync(kFull, ok);
+                    E[p * kLanes + lane] = ok ? nxt : cur;
+                    cur = ok ? cur : nxt;
+                    if (lane == 0) msk[p] = m;
+                    nxt = nxt2;
+                    bb = bb2;
+                }
+                E[(NT - 1) * kLanes + lane] = cur;
+            }
+            __syncthreads();
+            // Masked exchange chain, pairs in order (0,1), (1,2), ..., two words a thread
+            for (int w = tid; w < N / 2; w += nthr) {
+                uint2 x = reinterpret_cast<const uint2 *>(S)[w];
+                for (int p = 0; p + 1 < NT; ++p) {
+                    const uint2 y = reinterpret_cast<const uint2 *>(S + (size_t)(p + 1) * N)[w];
+                    const uint32_t m = msk[p];
+                    const uint32_t dx = (x.x ^ y.x) & m, dy = (x.y ^ y.y) & m;
+                    reinterpret_cast<uint2 *>(S + (size_t)p * N)[w] = make_uint2(x.x ^ dx, x.y ^ dy);
+                    x = make_uint2(y.x ^ dx, y.y ^ dy);
+                }
+                reinterpret_cast<uint2 *>(S + (size_t)(NT - 1) * N)[w] = x;
+            }
+            if (a.swap_log != nullptr)
+                for (int p = tid; p + 1 < NT; p += nthr)
+                    a.swap_log[(((size_t)pass_local * a.G + g) * a.C + c) * (NT - 1) + p] = msk[p];
             __syncthreads();
         }
-        if (swap_now) {
-            if (NT > 1) {
-                for (int i = tid; i < (NT - 1) * kLanes; i += nthr) {
-                    const int p = i >> 5, b = i & 31;
-                    const uint32_t r = swap_uniform(a.rk, p, b, P, g, c);
-                    bnd[i] = accept_bound(a.swapt + (size_t)p * a.swap_len, a.swap_len, r);
-                }
-                __syncthreads();
-                if (warp == 0) {
-                    int cur = E[lane];
-                    for (int p = 0; p + 1 < NT; ++p) {
-                        const int nxt = E[(p + 1) * kLanes + lane];
-                        const bool ok = (cur - nxt) >= bnd[p * kLanes + lane];
-                        const uint32_t m = __ballot_sync(kFull, ok);
-                        E[p * kLanes + lane] = ok ? nxt : cur;
-                        cur = ok ? cur : nxt;
-                        if (lane == 0) msk[p] = m;
-                    }
-                    E[(NT - 1) * kLanes + lane] = cur;
-                }
-                __syncthreads();
-                // Masked exchange chain, pairs in order (0,1), (1,2), ...
-                for (int w = tid; w < N; w += nthr) {
-                    uint32_t x = S[w];
-                    for (int p = 0; p + 1 < NT; ++p) {
-                        const uint32_t y = S[(size_t)(p + 1) * N + w];
-                        const uint32_t d = (x ^ y) & msk[p];
-                        S[(size_t)p * N + w] = x ^ d;
-                        x = y ^ d;
-                    }
-                    S[(size_t)(NT - 1) * N + w] = x;
-                }
-                if (a.swap_log != nullptr)
-                    for (int p = tid; p + 1 < NT; p += nthr)
-                        a.swap_log[(((size_t)pass_local * a.G + g) * a.C + c) * (NT - 1) + p] = msk[p];
-                __syncthreads();
-            }
+        if (swap_after(s, a.swap_every)) {
             ++P;
             ++pass_local;
         }
@@ -486,7 +136,7 @@ k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure
             }
         }
         if (meas) {
-            if (a.esum != nullptr && warp < NT) {
+            if (a.esum != nullptr) {
                 // one warp per slot
                 for (int t = warp; t < NT; t += nthr / 32) {
                     long long v = E[t * kLanes + lane];
@@ -513,7 +163,7 @@ k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure
                         acc_add_words4(oacc, x.x ^ y.x, x.y ^ y.y, x.z ^ y.z, x.w ^ y.w);
                     }
                 }
-                reduce_counters(oacc, tpl, nd, lane, warp);
+                reduce_counters(oacc, tpl, nd, lane, warp, 1);
                 cl.sync();   // the other copy may now modify its lattices again
                 if (a.qhist != nullptr)
                     for (int i = tid; i < NT * kLanes; i += nthr) {
@@ -522,8 +172,8 @@ k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure
                             atomicAdd(reinterpret_cast<unsigned long long *>(
                                           a.qhist + (size_t)t * (N + 1) + nd[i]), 1ull);
                     }
-                __syncthreads();
             }
+            __syncthreads();   // E and nd are rewritten by the next sweep
         }
     }
     // energies of the final state, spins back to global memory
@@ -583,7 +233,7 @@ k_sweep_chunk(const __grid_constant__ SweepLaunch a, int tpl, int nlat)
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
         if (needE)
-            for (int i = tid; i < kMaxTemps * kLanes; i += nthr) E[i] = 0;
+            for (int i = tid; i < kMaxTemps * kLanes; i += nthr) E[i] = -3 * N;
         if (active)
             half_sweep<L, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g,
                                  (0u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
@@ -592,10 +242,10 @@ k_sweep_chunk(const __grid_constant__ SweepLaunch a, int tpl, int nlat)
             if (active)
                 half_sweep<L, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g,
                                     (1u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
-            reduce_counters(acc, tpl, E, lane, warp);
+            reduce_counters(acc, tpl, E, lane, warp, 2);
             __syncthreads();
             for (int i = tid; i < nl_here * kLanes; i += nthr) {
-                const int e = 2 * E[i] - 3 * N;
+                const int e = E[i];
                 const int t = tbase + (i >> 5), b = i & 31;
                 if (a.energy_log != nullptr) {
                     const size_t row = (size_t)(s - a.log_s0);
@@ -849,7 +499,8 @@ cudaError_t launch_unit_L(const SweepLaunch &a, const Plan &plan, bool cluster_m
     }
     cfg.attrs = attr;
     cfg.numAttrs = nattr;
-    return cudaLaunchKernelEx(&cfg, kern, a, plan.threads_per_lattice, cluster_measure ? 1 : 0);
+    return cudaLaunchKernelEx(&cfg, kern, a, plan.threads_per_lattice, cluster_measure ? 1 : 0,
+                              plan.swap_in_smem ? 1 : 0);
 }
 
 template <int L>
@@ -918,36 +569,37 @@ static int pow2_at_least(int x)
     return p;
 }
 
-bool make_plan(int L, int NT, int C, size_t smem_optin, int tpl_override, Plan *plan)
+static bool unit_generic_plan(int L, int NT, uint32_t swap_len, size_t smem_optin, int tpl_pref,
+                              Plan *plan)
 {
-    (void)C;
-    if (NT < 1 || NT > kMaxTemps) return false;
     const int N = L * L * L, Q = N / 8;
     const int tpl_min = pow2_at_least((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
-    auto fix_tpl = [&](int tpl, int nlat) {
-        if (tpl < tpl_min) tpl = tpl_min;
-        // whole warps only: shuffles in the energy reduction use full masks
-        while ((tpl * nlat) % 32 != 0) tpl *= 2;
-        return tpl;
-    };
-    // unit form: all NT lattices of a (group, copy) in one CTA
-    {
-        int tpl = tpl_override > 0 ? tpl_override : pow2_at_least((Q + 3) / 4);
-        tpl = fix_tpl(tpl, NT);
-        while (tpl * NT > kMaxThreads && tpl / 2 >= tpl_min && ((tpl / 2) * NT) % 32 == 0) tpl /= 2;
-        const size_t smem = UnitSmem::bytes(N, NT);
-        // overlap counting: per-thread words N / tpl must fit the 8-plane counter
-        if (tpl * NT <= kMaxThreads && smem <= smem_optin && (N + tpl - 1) / tpl <= 255) {
-            plan->unit = true;
-            plan->threads_per_lattice = tpl;
-            plan->lattices_per_cta = NT;
-            plan->threads = tpl * NT;
-            plan->smem = smem;
-            plan->j_in_smem = true;
-            return true;
-        }
-    }
-    // chunked form: nlat lattices per CTA, swaps in their own kernels
+    int tpl = tpl_pref > 0 ? tpl_pref : pow2_at_least((Q + 3) / 4);
+    if (tpl < tpl_min) tpl = tpl_min;
+    // whole warps only: shuffles in the energy reduction use full masks
+    while ((tpl * NT) % 32 != 0) tpl *= 2;
+    while (tpl * NT > kMaxThreads && tpl / 2 >= tpl_min && ((tpl / 2) * NT) % 32 == 0) tpl /= 2;
+    size_t smem = UnitSmem::base_bytes(N, NT);
+    const size_t sw = UnitSmem::swap_bytes(NT, swap_len);
+    const bool sw_smem = smem + sw <= smem_optin;
+    if (sw_smem) smem += sw;
+    // overlap counting: per-thread words N / tpl must fit the 8-plane counter
+    if (tpl * NT > kMaxThreads || smem > smem_optin || (N + tpl - 1) / tpl > 255) return false;
+    plan->form = kFormUnit;
+    plan->unit = true;
+    plan->threads_per_lattice = tpl;
+    plan->lattices_per_cta = NT;
+    plan->threads = tpl * NT;
+    plan->smem = smem;
+    plan->j_in_smem = true;
+    plan->swap_in_smem = sw_smem;
+    return true;
+}
+
+static bool chunk_plan(int L, int NT, size_t smem_optin, int tpl_pref, int nlat_cap, Plan *plan)
+{
+    const int N = L * L * L, Q = N / 8;
+    const int tpl_min = pow2_at_least((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
     const size_t lat_bytes = (size_t)N * 4, j_bytes = (size_t)3 * N * 4;
     const size_t e_bytes = (size_t)kMaxTemps * kLanes * 4;
     const bool j_smem = j_bytes + lat_bytes + e_bytes <= smem_optin;
@@ -955,7 +607,8 @@ bool make_plan(int L, int NT, int C, size_t smem_optin, int tpl_override, Plan *
     int nlat = (int)(budget / lat_bytes);
     if (nlat < 1) return false;
     if (nlat > NT) nlat = NT;
-    int tpl = tpl_override > 0 ? tpl_override : pow2_at_least((Q + 3) / 4);
+    if (nlat_cap > 0 && nlat > nlat_cap) nlat = nlat_cap;
+    int tpl = tpl_pref > 0 ? tpl_pref : pow2_at_least((Q + 3) / 4);
     if (tpl < tpl_min) tpl = tpl_min;
     if (tpl > kMaxThreads) tpl = kMaxThreads;
     if (tpl < tpl_min) return false;
@@ -964,15 +617,77 @@ bool make_plan(int L, int NT, int C, size_t smem_optin, int tpl_override, Plan *
     // prefer a divisor of NT so every CTA is full
     for (int d = nlat; d >= 1; --d)
         if (NT % d == 0) { nlat = d; break; }
-    tpl = fix_tpl(tpl, nlat);
+    while ((tpl * nlat) % 32 != 0) tpl *= 2;
     if (nlat * tpl > kMaxThreads) return false;
+    plan->form = kFormChunked;
     plan->unit = false;
     plan->threads_per_lattice = tpl;
     plan->lattices_per_cta = nlat;
     plan->threads = tpl * nlat;
     plan->smem = (size_t)nlat * lat_bytes + (j_smem ? j_bytes : 0) + e_bytes;
     plan->j_in_smem = j_smem;
+    plan->swap_in_smem = false;
     return true;
+}
+
+std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin)
+{
+    (void)C;
+    std::vector<Plan> out;
+    if (NT < 1 || NT > kMaxTemps || !supported_L(L)) return out;
+    const int N = L * L * L;
+    // fast unit form (L % 8 == 0): best first
+    {
+        size_t smem = UnitSmem::base_bytes(N, NT);
+        const size_t sw = UnitSmem::swap_bytes(NT, swap_len);
+        const bool sw_smem = smem + sw <= smem_optin;
+        if (sw_smem) smem += sw;
+        const int hps[] = {8, 4, 64, 32};
+        if (smem <= smem_optin)
+            for (int hp : hps) {
+                const int t = fast_unit_threads(L, hp, NT);
+                if (t == 0) continue;
+                Plan p;
+                p.form = kFormUnitFast;
+                p.unit = true;
+                p.threads_per_lattice = hp;
+                p.lattices_per_cta = NT;
+                p.threads = t;
+                p.smem = smem;
+                p.j_in_smem = true;
+                p.swap_in_smem = sw_smem;
+                out.push_back(p);
+            }
+    }
+    // generic unit form with a few group sizes
+    {
+        const int prefs[] = {0, 8, 16, 32, 64, 128};
+        for (int tp : prefs) {
+            Plan p;
+            if (!unit_generic_plan(L, NT, swap_len, smem_optin, tp, &p)) continue;
+            bool dup = false;
+            for (const Plan &q : out)
+                if (q.form == p.form && q.threads_per_lattice == p.threads_per_lattice) dup = true;
+            if (!dup) out.push_back(p);
+        }
+    }
+    // chunked form: always possible when one lattice fits
+    {
+        const int caps[] = {0, 1, 2, 4};
+        const int prefs[] = {0, 128, 256};
+        for (int cap : caps)
+            for (int tp : prefs) {
+                Plan p;
+                if (!chunk_plan(L, NT, smem_optin, tp, cap, &p)) continue;
+                bool dup = false;
+                for (const Plan &q : out)
+                    if (q.form == p.form && q.threads_per_lattice == p.threads_per_lattice &&
+                        q.lattices_per_cta == p.lattices_per_cta)
+                        dup = true;
+                if (!dup) out.push_back(p);
+            }
+    }
+    return out;
 }
 
 cudaError_t launch_import(const uint32_t *api_spins, const uint32_t *api_bonds, uint32_t *spins,

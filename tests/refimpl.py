@@ -96,8 +96,8 @@ def metropolis_rn(seed: int, L: int, g: int, t: int, c: int, s: int, colour: int
     x, y, z = i % L, (i // L) % L, i // (L * L)
     sel = i[((x + y + z) & 1) == colour]
     k = sel >> 1
-    ctr = np.stack([k >> 2, np.full_like(k, s), np.full_like(k, g),
-                    np.full_like(k, (colour << 16) | (c << 8) | t)], axis=1)
+    ctr = np.stack([k >> 2, np.full_like(k, (colour << 16) | (c << 8) | t), np.full_like(k, s),
+                    np.full_like(k, g)], axis=1)
     keys = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint64), (len(k), 1))
     out = torch_philox(ctr, keys)
     r = np.zeros(N, np.uint64)
@@ -109,8 +109,8 @@ def swap_rn(seed: int, g: int, c: int, P: int, NT: int) -> np.ndarray:
     """Uniforms of one swap pass: array [NT-1][32]."""
     p, b = np.meshgrid(np.arange(NT - 1), np.arange(32), indexing="ij")
     p, b = p.ravel(), b.ravel()
-    ctr = np.stack([(p << 3) | (b >> 2), np.full_like(p, P), np.full_like(p, g),
-                    np.full_like(p, (1 << 24) | (c << 8))], axis=1)
+    ctr = np.stack([(p << 3) | (b >> 2), np.full_like(p, (1 << 24) | (c << 8)), np.full_like(p, P),
+                    np.full_like(p, g)], axis=1)
     keys = np.tile(np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint64), (len(p), 1))
     out = torch_philox(ctr, keys)
     return out[np.arange(len(p)), b & 3].reshape(NT - 1, 32)

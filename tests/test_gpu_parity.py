@@ -188,3 +188,50 @@ def test_full_size_sampled_groups(name, inst, n, swap_every, groups):
     on sampled word-groups (groups are independent, counters use global indices)."""
     gpu, sims, _ = pair(inst, groups=groups)
     compare(gpu, sims, n, swap_every, threads=16)
+
+
+@pytest.mark.parametrize("L,G,NT,C", [(8, 3, 24, 2), (16, 2, 6, 2), (4, 2, 16, 2), (12, 1, 28, 2),
+                                      (16, 1, 32, 2), (8, 2, 40, 1)])
+def test_every_plan_is_bit_identical(L, G, NT, C):
+    """All kernel plans (unit, specialised unit, chunked; several CTA shapes)
+    give the oracle's trajectory, including swap logs and the q histogram."""
+    inst = W.Instance(L=L, G=G, NT=NT, C=C, seed=77 + L, tmin=0.9, tmax=2.0, input_seed=NT + L)
+    inp = W.draw_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    probe = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
+                        metro, swapt)
+    plans = probe.plans()
+    assert len(plans) >= 2
+    sim = oracle.OracleSim(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
+                           metro, swapt)
+    n, se = 12, 2
+    qh_o = np.zeros((NT, inst.N + 1), np.uint64) if C == 2 else None
+    ref = sim.sweep(n, se, energy_log=True, swap_log=True, qhist=qh_o, measure_from=4,
+                    measure_every=3 if C == 2 else 0)
+    ref_spins = sim.spins()
+    for i, p in enumerate(plans):
+        gpu = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
+                          metro, swapt)
+        gpu.select_plan(i)
+        qh = torch.zeros((NT, inst.N + 1), dtype=torch.int64, device="cuda") if C == 2 else None
+        out = gpu.sweep(n, se, energy_log=True, swap_log=True, qhist=qh, measure_from=4,
+                        measure_every=3 if C == 2 else 0)
+        msg = f"plan {i}: {p}"
+        np.testing.assert_array_equal(i32(out["energy_log"]), ref["energy_log"], err_msg=msg)
+        np.testing.assert_array_equal(u32(out["swap_log"]), ref["swap_log"], err_msg=msg)
+        np.testing.assert_array_equal(u32(gpu.read_spins()), ref_spins, err_msg=msg)
+        if C == 2:
+            np.testing.assert_array_equal(qh.cpu().numpy().view(np.uint64), qh_o, err_msg=msg)
+
+
+def test_autotune_keeps_state_and_picks_a_plan():
+    inst = W.Instance(L=8, G=4, NT=24, C=2, seed=5, tmin=0.9, tmax=2.0, input_seed=55)
+    gpu, sims, _ = pair(inst, groups=[0, 3])
+    gpu.sweep(3, 1)
+    for _, sim in sims:
+        sim.sweep(3, 1)
+    ms = gpu.autotune(probe_sweeps=20, swap_every=1)
+    assert len(ms) == len(gpu.plans()) and all(m > 0 for m in ms)
+    assert gpu.plan == int(np.argmin(ms))
+    assert gpu.counters == (3, 3)
+    compare(gpu, sims, 10, 1)

@@ -417,8 +417,8 @@ MUTANTS = {
     "colour_order": ("for (int colour = 0; colour < 2; ++colour) {",
                      "for (int colour = 1; colour >= 0; --colour) {"),
     "energy_update": ("en(m, g, c, b)[rr] += dE;", "en(m, g, c, b)[rr] -= dE;"),
-    "counter_layout": ("k >> 2, (uint32_t)s, (uint32_t)(m->group_base + g),",
-                       "k >> 2, (uint32_t)(m->group_base + g), (uint32_t)s,"),
+    "counter_layout": ("(uint32_t)s, (uint32_t)(m->group_base + g), (int)(k & 3u));",
+                       "(uint32_t)(m->group_base + g), (uint32_t)s, (int)(k & 3u));"),
     "z_step": ("if (d == 2) z += step;", "if (d == 2) z += 1;"),
 }
 
