@@ -183,6 +183,26 @@ int ea_autotune(ea_ctx *ctx, uint32_t probe_sweeps, uint32_t swap_every, float *
 int ea_run(const ea_config *cfg, const ea_sweep_args *args, void *stream, int32_t *energies_host,
            uint32_t *spins_host, uint64_t *qhist_host, int64_t *esum_host);
 
+/* One replica-exchange pass that allocates no device memory.  The paper has
+ * no counterpart: this exists for callers that cannot call cudaMalloc while
+ * they run (an application that pre-reserves all device memory for its own
+ * pool, a host thread that must not stall other streams on an allocation).
+ * It performs the pass of ea_pt_swap on caller-owned DEVICE buffers:
+ *   spins    [G][NT][C][N] by slot (the layout of ea_read_spins), exchanged in place;
+ *   energies [G][NT][C][32] int32 of those spins (as ea_measure returns them),
+ *            permuted in place to follow the exchanged configurations;
+ *   swapt    [NT-1][swap_len] as at creation; masks [G][C][NT-1] or NULL.
+ * seed and pass_index give the random numbers (pass P of the context API).
+ * Its scratch (the accepted-pair masks between its two kernels) is a static
+ * device array of the library sized for G * C <= 4096; larger ensembles get
+ * EA_EINVAL.  The first call on each device looks up that array's device
+ * address (make it before any stream capture).  Every call shares the array:
+ * calls whose kernels overlap on the GPU (other streams, other host threads)
+ * race; calls on one stream are ordered.  Asynchronous on stream. */
+int ea_pt_swap_static(uint32_t *spins, int32_t *energies, const uint32_t *swapt, uint32_t swap_len,
+                      uint32_t L, uint32_t n_groups, uint32_t n_temps, uint32_t n_copies,
+                      uint64_t seed, uint64_t pass_index, uint32_t *masks, void *stream);
+
 /* Static description of an error code. */
 const char *ea_strerror(int code);
 

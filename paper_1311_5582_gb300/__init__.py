@@ -56,7 +56,8 @@ PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked"}
 EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_sweep",
            "ea_pt_swap", "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
            "ea_get_counters", "ea_sync", "ea_launch_count", "ea_plan_count", "ea_plan_current",
-           "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_run", "ea_strerror"]
+           "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_run", "ea_pt_swap_static",
+           "ea_strerror"]
 
 
 def load_library(path: str | None = None):
@@ -95,12 +96,13 @@ def load_library(path: str | None = None):
     lib.ea_plan_select.argtypes = [vp, i32]
     lib.ea_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_float)]
     lib.ea_run.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_SweepArgs), vp, vp, vp, vp, vp]
+    lib.ea_pt_swap_static.argtypes = [vp, vp, vp, u32, u32, u32, u32, u32, u64, u64, vp, vp]
     lib.ea_strerror.argtypes = [i32]
     lib.ea_strerror.restype = ctypes.c_char_p
     for name in ("ea_build_tables", "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
                  "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
                  "ea_get_counters", "ea_sync", "ea_run", "ea_plan_count", "ea_plan_current",
-                 "ea_plan_info", "ea_plan_select", "ea_autotune"):
+                 "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_pt_swap_static"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -311,3 +313,18 @@ def ea_run(L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every, 
     _check(lib.ea_run(ctypes.byref(cfg), ctypes.byref(args), handle, _ptr(energies), _ptr(sp),
                       _ptr(qh), _ptr(es)), "ea_run")
     return {"energies": energies, "spins": sp, "qhist": qh, "esum": es}
+
+
+def ea_pt_swap_static(spins, energies, swapt, L, n_groups, n_temps, n_copies, seed, pass_index,
+                      masks=None, stream=None):
+    """Allocation-free replica-exchange pass on caller-owned device tensors (in place).
+
+    spins: int32/uint32 device tensor [G][NT][C][N]; energies: int32 [G][NT][C][32];
+    swapt: device tensor [NT-1][swap_len]; masks: optional int32 [G][C][NT-1]."""
+    lib = load_library()
+    handle, _ = _stream_handle(stream)
+    swap_len = int(swapt.shape[1]) if swapt is not None and swapt.dim() == 2 else 0
+    _check(lib.ea_pt_swap_static(_ptr(spins), _ptr(energies),
+                                 _ptr(swapt) if swap_len else None, swap_len, int(L),
+                                 int(n_groups), int(n_temps), int(n_copies), int(seed),
+                                 int(pass_index), _ptr(masks), handle), "ea_pt_swap_static")
