@@ -276,8 +276,9 @@ int run_sweeps(ea_ctx *c, const ea_sweep_args *args, const ea::Plan &plan)
         a.pass_local0 = 0;
         const bool overlaps = c->C == 2 && args->qhist != nullptr && args->measure_every != 0;
         if (plan.form == ea::kFormUnitFast)
-            EA_TRY(ea::launch_sweep_unit_fast(a, (int)c->L, plan.threads_per_lattice, plan.smem,
-                                              plan.swap_in_smem, overlaps, st, &c->launches));
+            EA_TRY(ea::launch_sweep_unit_fast(a, (int)c->L, plan.threads_per_lattice,
+                                              plan.swap_in_smem, overlaps, c->smem_optin, st,
+                                              &c->launches));
         else
             EA_TRY(ea::launch_sweep_unit(a, (int)c->L, plan, overlaps, st, &c->launches));
         return EA_OK;

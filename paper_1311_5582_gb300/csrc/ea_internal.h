@@ -76,8 +76,11 @@ bool supported_L(int L);
 std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin);
 
 int fast_unit_threads(int L, int HP, int NT);
-cudaError_t launch_sweep_unit_fast(const SweepLaunch &a, int L, int HP, size_t smem,
-                                   bool swap_in_smem, bool cluster_measure, cudaStream_t st,
+// Dynamic shared memory of the specialised unit kernel (with or without the
+// swap table, the measurement snapshots and the shared-memory histogram).
+size_t fast_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem, bool snap, bool hist_smem);
+cudaError_t launch_sweep_unit_fast(const SweepLaunch &a, int L, int HP, bool swap_in_smem,
+                                   bool cluster_measure, size_t smem_optin, cudaStream_t st,
                                    uint64_t *launches);
 
 // Launchers: return cudaSuccess or the launch error.  Each adds its kernel

@@ -638,11 +638,9 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
     const int N = L * L * L;
     // fast unit form (L % 8 == 0): best first
     {
-        size_t smem = UnitSmem::base_bytes(N, NT);
-        const size_t sw = UnitSmem::swap_bytes(NT, swap_len);
-        const bool sw_smem = smem + sw <= smem_optin;
-        if (sw_smem) smem += sw;
-        const int hps[] = {8, 4, 64, 32};
+        const bool sw_smem = fast_unit_smem(L, NT, swap_len, true, false, false) <= smem_optin;
+        const size_t smem = fast_unit_smem(L, NT, swap_len, sw_smem, false, false);
+        const int hps[] = {8, 16, 4, 64, 32};
         if (smem <= smem_optin)
             for (int hp : hps) {
                 const int t = fast_unit_threads(L, hp, NT);
