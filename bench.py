@@ -40,18 +40,58 @@ ALG_OPS_PER_SITE_WORD = 32
 ALU_LANES_PER_CLK_PER_SM = 64     # integer ALU pipe (LOP3/IADD3/ISETP/SEL) of one SM
 
 
-def workload():
-    inst = W.SCALE
-    n = W.SCALE_SWEEPS
+WORKLOADS = {
+    # name: (instance, sweeps per step, swap every, measurement over the second half)
+    "scale": (W.SCALE, W.SCALE_SWEEPS, W.SCALE_SWAP_EVERY, True),
+    "small": (W.SMALL, W.SMALL_SWEEPS, W.SMALL_SWAP_EVERY, False),
+    "large16": (W.LARGE16, W.LARGE_SWEEPS, W.LARGE_SWAP_EVERY, False),
+    "large32": (W.LARGE32, W.LARGE_SWEEPS, W.LARGE_SWAP_EVERY, False),
+}
+
+
+def workload(name="scale", sweeps=None):
+    inst, n, swap_every, meas = WORKLOADS[name]
+    if sweeps:
+        n = sweeps
+    text = (f"EA +-J L={inst.L} ({inst.N} sites), {32 * inst.G} realizations "
+            f"({inst.G} words/site), {inst.NT} temperatures geometric in "
+            f"[{inst.tmin},{inst.tmax}] x {inst.C} copies, {n} sweeps, PT swap every "
+            f"{'sweep' if swap_every == 1 else f'{swap_every} sweeps'}"
+            + (", energy + overlap-q histograms over the second half" if meas else ""))
     return {
-        "inst": inst, "sweeps": n, "swap_every": W.SCALE_SWAP_EVERY,
-        "measure_from": n // 2, "measure_every": 1,
-        "flips": n * inst.N * inst.NT * inst.C * 32 * inst.G,
-        "name": (f"EA +-J L={inst.L} ({inst.N} sites), {32 * inst.G} realizations "
-                 f"({inst.G} words/site), {inst.NT} temperatures geometric in "
-                 f"[{inst.tmin},{inst.tmax}] x {inst.C} copies, {n} sweeps, PT swap every sweep, "
-                 f"energy + overlap-q histograms over the second half"),
+        "key": name, "inst": inst, "sweeps": n, "swap_every": swap_every,
+        "measure_from": n // 2 if meas else 0, "measure_every": 1 if meas else 0,
+        "flips": n * inst.N * inst.NT * inst.C * 32 * inst.G, "name": text,
     }
+
+
+def kernel_source_hash() -> str:
+    """SHA-256 over the CUDA sources: a traffic figure measured on other sources is stale."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1311_5582_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_key: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
+    (profiles/*.md line 'traffic-record: <workload> <bytes per launch> <source hash>'),
+    or None when absent or taken on different kernel sources."""
+    import glob
+    want = kernel_source_hash()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as f:
+            for line in f:
+                parts = line.strip().strip("`").split()
+                if len(parts) == 4 and parts[0] == "traffic-record:" and parts[1] == workload_key:
+                    if parts[3] == want:
+                        return float(parts[2])
+    return None
 
 
 def dist_env():
@@ -150,8 +190,9 @@ def cpu_baseline(wl, budget_s=15.0, threads=None):
         qh = np.zeros((inst.NT, inst.N + 1), np.uint64)
         es = np.zeros(inst.NT, np.int64)
         t0 = time.perf_counter()
-        sim.sweep(n, wl["swap_every"], qhist=qh, esum=es, measure_from=n // 2, measure_every=1,
-                  threads=threads)
+        me = wl["measure_every"]
+        sim.sweep(n, wl["swap_every"], qhist=qh if me else None, esum=es if me else None,
+                  measure_from=n // 2 if me else 0, measure_every=me, threads=threads)
         return time.perf_counter() - t0
 
     t_probe = run(10)
@@ -183,8 +224,9 @@ def run_reference(args, wl):
         qh = np.zeros((inst.NT, inst.N + 1), np.uint64)
         es = np.zeros(inst.NT, np.int64)
         t0 = time.perf_counter()
-        sim.sweep(n, wl["swap_every"], qhist=qh, esum=es, measure_from=n // 2, measure_every=1,
-                  threads=threads)
+        me = wl["measure_every"]
+        sim.sweep(n, wl["swap_every"], qhist=qh if me else None, esum=es if me else None,
+                  measure_from=n // 2 if me else 0, measure_every=me, threads=threads)
         return time.perf_counter() - t0
 
     t_probe = step(10)
@@ -214,15 +256,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--sweeps", type=int, default=None, help="override sweeps per step (debug)")
+    ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS),
+                    help="scale (default): the L=8 ensemble of the headline metric")
+    ap.add_argument("--sweeps", type=int, default=None,
+                    help="sweeps per step (default: the workload's full run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    wl = workload()
-    if args.sweeps:
-        wl["sweeps"] = args.sweeps
-        wl["measure_from"] = args.sweeps // 2
-        inst = wl["inst"]
-        wl["flips"] = args.sweeps * inst.N * inst.NT * inst.C * 32 * inst.G
+    wl = workload(args.workload, args.sweeps)
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -288,6 +328,8 @@ def main():
     mhz = peaks.get("sm_max_mhz", 2070.0)
     peak_tops = sms * ALU_LANES_PER_CLK_PER_SM * mhz * 1e6 / 1e12
     site_words = wl["sweeps"] * inst.N * inst.NT * inst.C * inst.G
+    # the dominant kernel's launches per step (1 for the unit form; the chunked form
+    # launches a sweep kernel per swap interval, timed here as the whole step)
     launch_s = statistics.mean(step_ms) / 1e3
     achieved = site_words * ALG_OPS_PER_SITE_WORD / launch_s / 1e12
 
@@ -326,7 +368,8 @@ def main():
                        "sweeps_per_step": wl["sweeps"], "swap_every": wl["swap_every"],
                        "kernel_launches_per_step": launches / args.steps},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                         "frac": achieved / peak_tops, "traffic": None,
+                         "frac": achieved / peak_tops, "traffic": recorded_traffic(wl["key"]),
+                         "traffic_source_hash": kernel_source_hash(),
                          "peak_basis": f"{sms} SMs x {ALU_LANES_PER_CLK_PER_SM} int-ALU lanes/clk x "
                                        f"{mhz:.0f} MHz (max SM clock of measured peaks file)",
                          "alg_ops_per_site_word": ALG_OPS_PER_SITE_WORD},

@@ -506,3 +506,18 @@ def test_group_subset_reproduces_full_ensemble():
         np.testing.assert_array_equal(out["energy_log"][:, 0], full["energy_log"][:, g])
         np.testing.assert_array_equal(out["swap_log"][:, 0], full["swap_log"][:, g])
         np.testing.assert_array_equal(sub.spins()[0], fs[g])
+
+
+def test_overlap_counts_match_numpy_definition():
+    """n_diff = number of sites where the two copies at a slot differ (q = 1 - 2 n_diff / N)."""
+    L, G, NT = 6, 2, 4
+    sim, _ = make_sim(L, G, NT, 2, 41, 14)
+    sim.sweep(9, 1)
+    sp = sim.spins()
+    ov = sim.overlaps()
+    for g in range(G):
+        for t in range(NT):
+            a = refimpl.unpack_lanes(sp[g, t, 0], L)
+            b = refimpl.unpack_lanes(sp[g, t, 1], L)
+            want = (a != b).reshape(32, -1).sum(axis=1)
+            np.testing.assert_array_equal(ov[g, t], want)
