@@ -174,6 +174,40 @@ int ea_plan_select(ea_ctx *ctx, int index);
  * be NULL).  Synchronises the stream. */
 int ea_autotune(ea_ctx *ctx, uint32_t probe_sweeps, uint32_t swap_every, float *ms_out);
 
+/* Batched form: one persistent launch advances several ensembles together.
+ *
+ * A batch holds contexts (any supported L, ladder and size, on one device).
+ * ea_batch_sweep advances every member by n sweeps with the given swap
+ * schedule; each member's trajectory, energies and counters are exactly those
+ * of ea_sweep on it alone (same random-number counters), without logs or
+ * measurements.  The work of all members is cut into tasks -- whole
+ * (group, copy) units resident in one CTA for a segment of sweeps, or slot
+ * chunks of units too large for one CTA for one swap interval, whose last
+ * chunk runs the unit's swap pass -- and run by one persistent launch from a
+ * device-side queue, longest unit first.  The paper simulates one ensemble at
+ * a time (Sec. 3); batching several is this library's own addition, and the
+ * arithmetic of each member is that of Sec. 2.3 (sweeps) and Sec. 2.4 (swaps)
+ * exactly as in ea_sweep.  The launch and its
+ * uploads are captured in a CUDA graph and replayed while the batch's shape
+ * is unchanged.  Asynchronous on the batch's stream (NULL = legacy default);
+ * members must not be used on other streams until ea_batch_sync returns.
+ * A device-side wait that runs out (it never should) makes ea_batch_sync
+ * return EA_ETIMEOUT instead of hanging. */
+typedef struct ea_batch ea_batch;
+int ea_batch_create(void *stream, ea_batch **out);
+/* ctx must outlive its membership; adding a member twice is EA_EINVAL. */
+int ea_batch_add(ea_batch *batch, ea_ctx *ctx);
+int ea_batch_clear(ea_batch *batch);
+/* Plan a member runs under in the batch (index into its ea_plan_* list, or
+ * -1 for automatic); plans wider than 512 threads are refused. */
+int ea_batch_set_plan(ea_batch *batch, uint32_t member, int plan_index);
+/* Work of one unit task in site-word updates (sweeps x N x NT); 0 = default. */
+int ea_batch_set_segment(ea_batch *batch, uint32_t site_words);
+int ea_batch_sweep(ea_batch *batch, uint32_t n_sweeps, uint32_t swap_every);
+int ea_batch_sync(ea_batch *batch);
+uint64_t ea_batch_launch_count(const ea_batch *batch);
+void ea_batch_destroy(ea_batch *batch);
+
 /* Host-buffer entry point: creates a context from cfg, runs the sweeps of
  * args (its DEVICE output pointers must be NULL), copies the results to the
  * HOST buffers below (each may be NULL), destroys the context and

@@ -56,8 +56,10 @@ PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked"}
 EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_sweep",
            "ea_pt_swap", "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
            "ea_get_counters", "ea_sync", "ea_launch_count", "ea_plan_count", "ea_plan_current",
-           "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_run", "ea_pt_swap_static",
-           "ea_strerror"]
+           "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_batch_create", "ea_batch_add",
+           "ea_batch_clear", "ea_batch_set_plan", "ea_batch_set_segment", "ea_batch_sweep",
+           "ea_batch_sync", "ea_batch_launch_count", "ea_batch_destroy", "ea_run",
+           "ea_pt_swap_static", "ea_strerror"]
 
 
 def load_library(path: str | None = None):
@@ -97,12 +99,25 @@ def load_library(path: str | None = None):
     lib.ea_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_float)]
     lib.ea_run.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_SweepArgs), vp, vp, vp, vp, vp]
     lib.ea_pt_swap_static.argtypes = [vp, vp, vp, u32, u32, u32, u32, u32, u64, u64, vp, vp]
+    lib.ea_batch_create.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.ea_batch_add.argtypes = [vp, vp]
+    lib.ea_batch_clear.argtypes = [vp]
+    lib.ea_batch_set_plan.argtypes = [vp, u32, i32]
+    lib.ea_batch_set_segment.argtypes = [vp, u32]
+    lib.ea_batch_sweep.argtypes = [vp, u32, u32]
+    lib.ea_batch_sync.argtypes = [vp]
+    lib.ea_batch_launch_count.argtypes = [vp]
+    lib.ea_batch_launch_count.restype = u64
+    lib.ea_batch_destroy.argtypes = [vp]
+    lib.ea_batch_destroy.restype = None
     lib.ea_strerror.argtypes = [i32]
     lib.ea_strerror.restype = ctypes.c_char_p
     for name in ("ea_build_tables", "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
                  "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
                  "ea_get_counters", "ea_sync", "ea_run", "ea_plan_count", "ea_plan_current",
-                 "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_pt_swap_static"):
+                 "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_pt_swap_static",
+                 "ea_batch_create", "ea_batch_add", "ea_batch_clear", "ea_batch_set_plan",
+                 "ea_batch_set_segment", "ea_batch_sweep", "ea_batch_sync"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -293,6 +308,58 @@ class Ensemble:
         ms = (ctypes.c_float * n)()
         _check(self.lib.ea_autotune(self.ctx, int(probe_sweeps), int(swap_every), ms), "ea_autotune")
         return list(ms)
+
+
+class Batch:
+    """Several ensembles advanced together by one persistent launch (ea_batch_*).
+
+    Members keep their own state and counters; after ``sweep(n, k)`` each is
+    exactly where ``member.sweep(n, k)`` alone would have left it."""
+
+    def __init__(self, ensembles=(), stream=None):
+        self.lib = load_library()
+        self.handle, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p(None)
+        _check(self.lib.ea_batch_create(self.handle, ctypes.byref(h)), "ea_batch_create")
+        self.b = h
+        self.members = []
+        for e in ensembles:
+            self.add(e)
+
+    def add(self, ens: Ensemble):
+        _check(self.lib.ea_batch_add(self.b, ens.ctx), "ea_batch_add")
+        self.members.append(ens)
+
+    def clear(self):
+        _check(self.lib.ea_batch_clear(self.b), "ea_batch_clear")
+        self.members = []
+
+    def set_plan(self, member: int, plan_index: int):
+        _check(self.lib.ea_batch_set_plan(self.b, int(member), int(plan_index)), "ea_batch_set_plan")
+
+    def set_segment(self, site_words: int):
+        _check(self.lib.ea_batch_set_segment(self.b, int(site_words)), "ea_batch_set_segment")
+
+    def sweep(self, n_sweeps: int, swap_every: int):
+        _check(self.lib.ea_batch_sweep(self.b, int(n_sweeps), int(swap_every)), "ea_batch_sweep")
+
+    def sync(self):
+        _check(self.lib.ea_batch_sync(self.b), "ea_batch_sync")
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.ea_batch_launch_count(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.ea_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ea_run(L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every, measure_from=0,

@@ -10,22 +10,6 @@
 #include "../../include/ea.h"
 #include "ea_internal.h"
 
-struct ea_ctx {
-    uint32_t L, G, NT, C, N, swap_len;
-    uint64_t seed;
-    cudaStream_t stream;
-    int device;
-    size_t smem_optin;
-    uint32_t *d_spins, *d_bonds, *d_metro, *d_swapt, *d_masks;
-    int32_t *d_energy;
-    int *d_err;
-    uint64_t sweep, pass;
-    uint64_t launches;
-    std::vector<ea::Plan> plans;   // every kernel plan that can run this ensemble
-    int plan_idx;
-    ea::Plan plan;                 // plans[plan_idx]
-    ea::RoundKeys rk;
-};
 
 namespace {
 

@@ -266,9 +266,10 @@ __device__ __forceinline__ uint32_t warp_transpose(uint32_t x, int lane)
 
 // Adds scale x each thread's bit-sliced per-lane counter into out[group][lane],
 // where a group is tpl consecutive threads (tpl a power of two dividing 32,
-// or a multiple of 32).  The whole warp must call this.
+// or a multiple of 32); groups at or beyond ngroups are idle threads and add
+// nothing.  The whole warp must call this.
 __device__ __forceinline__ void reduce_counters(const uint32_t (&acc)[kPlanes], int tpl,
-                                                int *out, int lane, int warp, int scale)
+                                                int *out, int lane, int warp, int scale, int ngroups)
 {
     uint32_t y[kPlanes];
 #pragma unroll
@@ -278,7 +279,7 @@ __device__ __forceinline__ void reduce_counters(const uint32_t (&acc)[kPlanes], 
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) cnt += __popc(y[p]) << p;
         const int grp = (warp * 32) / tpl;
-        atomicAdd(&out[grp * kLanes + lane], scale * cnt);
+        if (grp < ngroups) atomicAdd(&out[grp * kLanes + lane], scale * cnt);
     } else {
         const int ng = 32 / tpl;
         const uint32_t base = (tpl == 32) ? kFull : ((1u << tpl) - 1u);
@@ -288,7 +289,7 @@ __device__ __forceinline__ void reduce_counters(const uint32_t (&acc)[kPlanes], 
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p) cnt += __popc(y[p] & gm) << p;
             const int grp = (warp * 32 + gi * tpl) / tpl;
-            atomicAdd(&out[grp * kLanes + lane], scale * cnt);
+            if (grp < ngroups) atomicAdd(&out[grp * kLanes + lane], scale * cnt);
         }
     }
 }

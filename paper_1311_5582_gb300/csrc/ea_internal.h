@@ -106,3 +106,22 @@ cudaError_t launch_measure(const uint32_t *spins, const int32_t *energy, int L, 
                            uint64_t *qhist, int64_t *esum, cudaStream_t st, uint64_t *launches);
 
 }  // namespace ea
+
+// One ensemble's device state and counters (the opaque ea_ctx of the C ABI).
+struct ea_ctx {
+    uint32_t L, G, NT, C, N, swap_len;
+    uint64_t seed;
+    cudaStream_t stream;
+    int device;
+    size_t smem_optin;
+    uint32_t *d_spins, *d_bonds, *d_metro, *d_swapt, *d_masks;
+    int32_t *d_energy;
+    int *d_err;
+    uint64_t sweep, pass;
+    uint64_t launches;
+    std::vector<ea::Plan> plans;   // every kernel plan that can run this ensemble
+    int plan_idx;
+    ea::Plan plan;                 // plans[plan_idx]
+    ea::RoundKeys rk;
+};
+

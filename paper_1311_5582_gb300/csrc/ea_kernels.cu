@@ -2,265 +2,27 @@
 // +-J Edwards-Anderson model for sm_103a (any supported even L): the unit and
 // chunked sweep kernels, the global swap pass, energy recomputation,
 // measurement and layout conversion, plus the launch plan.
-#include "ea_device.cuh"
+#include "ea_bodies.cuh"
 
 namespace ea {
 
 namespace {
-// ------------------------------------------------------------------ unit kernel
-// One CTA owns all NT lattices of one (group, copy) unit in shared memory and
-// runs the whole sweep range: Metropolis half-sweeps, per-lane energies,
-// replica-exchange passes and measurements.  With C = 2 and overlap
-// measurement the two copies of a group form a 2-CTA cluster and read each
-// other's lattices through distributed shared memory.
-
 template <int L>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure, int swap_in_smem)
 {
-    using Gm = Geo<L>;
-    constexpr int N = Gm::N;
     extern __shared__ uint4 smem_u4[];
-    const int NT = (int)a.NT;
-    uint32_t *S = reinterpret_cast<uint32_t *>(smem_u4);     // [NT][2][H]
-    uint32_t *Js = S + (size_t)NT * N;                        // [3][2][H]
-    int *E = reinterpret_cast<int *>(Js + 3 * N);             // [64][32] energies by slot
-    int *bnd = E + kMaxTemps * kLanes;                        // [64][32] swap accept bounds
-    int *nd = bnd + kMaxTemps * kLanes;                       // [64][32] overlap counts
-    uint32_t *msk = reinterpret_cast<uint32_t *>(nd + kMaxTemps * kLanes);  // [64]
-    uint32_t *Tsw = msk + kMaxTemps;                          // [NT-1][swap_len] if swap_in_smem
-
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t unit = blockIdx.x;
-    const int c = (int)(unit % a.C);
-    const uint32_t g = unit / a.C;
-    const int l = tid / tpl, tl = tid - l * tpl;   // my slot and rank in its group
-    const int qper = (Gm::Q + tpl - 1) / tpl;
-
-    uint32_t *gS = a.spins + (size_t)unit * NT * N;
-    const uint32_t *gJ = a.bonds + (size_t)g * 3 * N;
-    for (int w = tid; w < NT * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(S)[w] = reinterpret_cast<const uint4 *>(gS)[w];
-    for (int w = tid; w < 3 * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(Js)[w] = reinterpret_cast<const uint4 *>(gJ)[w];
-    const uint32_t *swt = a.swapt;
-    if (swap_in_smem) {
-        const int nsw = (NT - 1) * (int)a.swap_len;
-        for (int w = tid; w < nsw; w += nthr) Tsw[w] = a.swapt[w];
-        swt = Tsw;
-    }
-    const uint32_t t0 = a.metro[l * 3 + 0], t1 = a.metro[l * 3 + 1], t2 = a.metro[l * 3 + 2];
-    uint32_t *mine = S + (size_t)l * N;
-    __syncthreads();
-
-    uint64_t P = a.P0;
-    uint32_t pass_local = a.pass_local0;
-    for (uint32_t n = 0; n < a.n_sweeps; ++n) {
-        const uint64_t s = a.s0 + n;
-        const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
-        const bool meas = measured(s, a.measure_from, a.measure_every);
-        const bool needE = swap_now || a.energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
-        uint32_t acc[kPlanes];
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-        if (needE)   // counters add 2 per unsatisfied bond: E = 2U - 3N
-            for (int i = tid; i < NT * kLanes; i += nthr) E[i] = -3 * N;
-        if (swap_now) {
-            // Swap acceptance bounds depend only on the pass index: compute them
-            // now; they are read after the half-sweeps' barriers.
-            for (int i = tid; i < (NT - 1) * kLanes; i += nthr) {
-                const int p = i >> 5, b = i & 31;
-                const uint32_t r = swap_uniform(a.rk, p, b, P, g, c);
-                bnd[i] = accept_bound(swt + (size_t)p * a.swap_len, a.swap_len, r);
-            }
-        }
-        half_sweep<L, false>(mine, Js, 0, tl, tpl, qper, (uint32_t)s, g,
-                             (0u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
-        __syncthreads();
-        if (needE) {
-            half_sweep<L, true>(mine, Js, 1, tl, tpl, qper, (uint32_t)s, g,
-                                (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
-            reduce_counters(acc, tpl, E, lane, warp, 2);
-        } else {
-            half_sweep<L, false>(mine, Js, 1, tl, tpl, qper, (uint32_t)s, g,
-                                 (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
-        }
-        __syncthreads();
-        if (swap_now) {
-            if (warp == 0) {
-                // Sequential pairs (0,1), (1,2), ... per realization lane; the
-                // configuration carried upward is `cur`.  Loads run one pair ahead.
-                int cur = E[lane];
-                int nxt = E[kLanes + lane];
-                int bb = bnd[lane];
-                for (int p = 0; p + 1 < NT; ++p) {
-                    const int nxt2 = (p + 2 < NT) ? E[(p + 2) * kLanes + lane] : 0;
-                    const int bb2 = (p + 2 < NT) ? bnd[(p + 1) * kLanes + lane] : 0;
-                    const bool ok = (cur - nxt) >= bb;
-                    const uint32_t m = __ballot_sync(kFull, ok);
-                    E[p * kLanes + lane] = ok ? nxt : cur;
-                    cur = ok ? cur : nxt;
-                    if (lane == 0) msk[p] = m;
-                    nxt = nxt2;
-                    bb = bb2;
-                }
-                E[(NT - 1) * kLanes + lane] = cur;
-            }
-            __syncthreads();
-            // Masked exchange chain, pairs in order (0,1), (1,2), ..., two words a thread
-            for (int w = tid; w < N / 2; w += nthr) {
-                uint2 x = reinterpret_cast<const uint2 *>(S)[w];
-                for (int p = 0; p + 1 < NT; ++p) {
-                    const uint2 y = reinterpret_cast<const uint2 *>(S + (size_t)(p + 1) * N)[w];
-                    const uint32_t m = msk[p];
-                    const uint32_t dx = (x.x ^ y.x) & m, dy = (x.y ^ y.y) & m;
-                    reinterpret_cast<uint2 *>(S + (size_t)p * N)[w] = make_uint2(x.x ^ dx, x.y ^ dy);
-                    x = make_uint2(y.x ^ dx, y.y ^ dy);
-                }
-                reinterpret_cast<uint2 *>(S + (size_t)(NT - 1) * N)[w] = x;
-            }
-            if (a.swap_log != nullptr)
-                for (int p = tid; p + 1 < NT; p += nthr)
-                    a.swap_log[(((size_t)pass_local * a.G + g) * a.C + c) * (NT - 1) + p] = msk[p];
-            __syncthreads();
-        }
-        if (swap_after(s, a.swap_every)) {
-            ++P;
-            ++pass_local;
-        }
-        if (a.energy_log != nullptr) {
-            const size_t row = (size_t)(s - a.log_s0);
-            for (int i = tid; i < NT * kLanes; i += nthr) {
-                const int t = i >> 5, b = i & 31;
-                a.energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = E[i];
-            }
-        }
-        if (meas) {
-            if (a.esum != nullptr) {
-                // one warp per slot
-                for (int t = warp; t < NT; t += nthr / 32) {
-                    long long v = E[t * kLanes + lane];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-                    if (lane == 0)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.esum + t),
-                                  (unsigned long long)v);
-                }
-            }
-            if (cluster_measure) {
-                cg::cluster_group cl = cg::this_cluster();
-                for (int i = tid; i < NT * kLanes; i += nthr) nd[i] = 0;
-                cl.sync();   // both copies have finished sweep s and its swap pass
-                const uint32_t *other = cl.map_shared_rank(S, c ^ 1);
-                uint32_t oacc[kPlanes];
-#pragma unroll
-                for (int p = 0; p < kPlanes; ++p) oacc[p] = 0;
-                if ((l & 1) == c) {
-                    const uint4 *A4 = reinterpret_cast<const uint4 *>(S + (size_t)l * N);
-                    const uint4 *B4 = reinterpret_cast<const uint4 *>(other + (size_t)l * N);
-                    for (int w = tl; w < N / 4; w += tpl) {
-                        const uint4 x = A4[w], y = B4[w];
-                        acc_add_words4(oacc, x.x ^ y.x, x.y ^ y.y, x.z ^ y.z, x.w ^ y.w);
-                    }
-                }
-                reduce_counters(oacc, tpl, nd, lane, warp, 1);
-                cl.sync();   // the other copy may now modify its lattices again
-                if (a.qhist != nullptr)
-                    for (int i = tid; i < NT * kLanes; i += nthr) {
-                        const int t = i >> 5;
-                        if ((t & 1) == c)
-                            atomicAdd(reinterpret_cast<unsigned long long *>(
-                                          a.qhist + (size_t)t * (N + 1) + nd[i]), 1ull);
-                    }
-            }
-            __syncthreads();   // E and nd are rewritten by the next sweep
-        }
-    }
-    // energies of the final state, spins back to global memory
-    for (int i = tid; i < NT * kLanes; i += nthr) a.energy[(size_t)unit * NT * kLanes + i] = E[i];
-    for (int w = tid; w < NT * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(gS)[w] = reinterpret_cast<const uint4 *>(S)[w];
+    unit_body<L>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, tpl, cluster_measure,
+                 swap_in_smem);
 }
-
-// ------------------------------------------------------------------ chunked kernel
-// For ensembles whose NT lattices do not fit one CTA: each CTA stages
-// lattices [t0, t0 + nlat) of one unit, runs the sweeps up to the next swap
-// point, and writes them back; the swap pass runs as its own kernels.
 
 template <int L, bool J_SMEM>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 k_sweep_chunk(const __grid_constant__ SweepLaunch a, int tpl, int nlat)
 {
-    using Gm = Geo<L>;
-    constexpr int N = Gm::N;
     extern __shared__ uint4 smem_u4[];
-    uint32_t *S = reinterpret_cast<uint32_t *>(smem_u4);                // [nlat][2][H]
-    uint32_t *Js = S + (size_t)nlat * N;                                 // [3][2][H] if J_SMEM
-    int *E = reinterpret_cast<int *>(Js + (J_SMEM ? 3 * N : 0));         // [64][32]
-
-    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t unit = blockIdx.x;
-    const int c = (int)(unit % a.C);
-    const uint32_t g = unit / a.C;
-    const int tbase = (int)blockIdx.y * nlat;
-    const int NT = (int)a.NT;
-    const int l = tid / tpl, tl = tid - l * tpl;
-    const int slot = tbase + l;
-    const int nl_here = min(nlat, NT - tbase);
-    const bool active = l < nl_here;
-    const int qper = (Gm::Q + tpl - 1) / tpl;
-
-    uint32_t *gS = a.spins + ((size_t)unit * NT + tbase) * N;
-    const uint32_t *gJ = a.bonds + (size_t)g * 3 * N;
-    for (int w = tid; w < nl_here * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(S)[w] = reinterpret_cast<const uint4 *>(gS)[w];
-    const uint32_t *J = gJ;
-    if constexpr (J_SMEM) {
-        for (int w = tid; w < 3 * N / 4; w += nthr)
-            reinterpret_cast<uint4 *>(Js)[w] = reinterpret_cast<const uint4 *>(gJ)[w];
-        J = Js;
-    }
-    uint32_t t0 = 0, t1 = 0, t2 = 0;
-    if (active) { t0 = a.metro[slot * 3]; t1 = a.metro[slot * 3 + 1]; t2 = a.metro[slot * 3 + 2]; }
-    uint32_t *mine = S + (size_t)l * N;
-    __syncthreads();
-
-    for (uint32_t n = 0; n < a.n_sweeps; ++n) {
-        const uint64_t s = a.s0 + n;
-        const bool last = n + 1 == a.n_sweeps;
-        const bool needE = a.energy_log != nullptr || (last && a.compute_energy_last);
-        uint32_t acc[kPlanes];
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-        if (needE)
-            for (int i = tid; i < kMaxTemps * kLanes; i += nthr) E[i] = -3 * N;
-        if (active)
-            half_sweep<L, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g,
-                                 (0u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
-        __syncthreads();
-        if (needE) {
-            if (active)
-                half_sweep<L, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g,
-                                    (1u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
-            reduce_counters(acc, tpl, E, lane, warp, 2);
-            __syncthreads();
-            for (int i = tid; i < nl_here * kLanes; i += nthr) {
-                const int e = E[i];
-                const int t = tbase + (i >> 5), b = i & 31;
-                if (a.energy_log != nullptr) {
-                    const size_t row = (size_t)(s - a.log_s0);
-                    a.energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = e;
-                }
-                if (last) a.energy[((size_t)unit * NT + t) * kLanes + b] = e;
-            }
-        } else if (active) {
-            half_sweep<L, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g,
-                                 (1u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
-        }
-        __syncthreads();
-    }
-    for (int w = tid; w < nl_here * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(gS)[w] = reinterpret_cast<const uint4 *>(S)[w];
+    chunk_body<L, J_SMEM>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, (int)blockIdx.y, tpl,
+                          nlat);
 }
 
 // Swap decision of one pass for every unit: one CTA per unit.  Reads the

@@ -1,0 +1,171 @@
+"""Batched form: one persistent launch advancing several ensembles of mixed
+shapes must leave each exactly where its own sweeps would (bit for bit), and
+where the oracle does.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU hosts too; every test here needs a device
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1311_5582_gb300 as ea  # noqa: E402
+
+# (L, G, NT, C): unit form (L 4, 6, 10), the L % 8 == 0 unit kernel (L 8, L 16 with
+# few slots) and chunked units (L 12 and 16 with 32 slots)
+MIX = [(4, 3, 16, 2), (6, 2, 7, 1), (8, 3, 24, 2), (10, 2, 9, 2), (12, 1, 32, 2),
+       (16, 2, 32, 2), (16, 1, 5, 2)]
+
+
+def instances(mix=MIX, base_seed=500):
+    return [W.Instance(L=L, G=G, NT=NT, C=C, seed=base_seed + i, tmin=0.9, tmax=2.0,
+                       input_seed=base_seed + 17 * i) for i, (L, G, NT, C) in enumerate(mix)]
+
+
+def make(inst: W.Instance):
+    inp = W.draw_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    gpu = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
+                      metro, swapt)
+    return gpu, inp, metro, swapt
+
+
+def state(gpu):
+    torch.cuda.synchronize()
+    sp = gpu.read_spins().cpu().numpy().view(np.uint32).copy()
+    en = gpu.measure()[0].cpu().numpy().copy()
+    return sp, en, gpu.counters
+
+
+def run_alone(inst, schedule):
+    gpu, *_ = make(inst)
+    for n, k in schedule:
+        gpu.sweep(n, k)
+    return state(gpu)
+
+
+def test_mixed_batch_matches_each_member_alone_and_the_oracle():
+    insts = instances()
+    members = [make(i) for i in insts]
+    batch = ea.Batch([m[0] for m in members])
+    schedule = [(37, 3), (25, 10), (6, 0), (11, 1)]
+    for n, k in schedule:
+        batch.sweep(n, k)
+    batch.sync()
+    total = sum(n for n, _ in schedule)
+    for inst, (gpu, inp, metro, swapt) in zip(insts, members):
+        sp, en, ctr = state(gpu)
+        sp_a, en_a, ctr_a = run_alone(inst, schedule)
+        tag = f"L={inst.L} G={inst.G} NT={inst.NT} C={inst.C}"
+        assert ctr == ctr_a and ctr[0] == total, tag
+        np.testing.assert_array_equal(sp, sp_a, err_msg=f"spins vs alone, {tag}")
+        np.testing.assert_array_equal(en, en_a, err_msg=f"energies vs alone, {tag}")
+        sim = oracle.OracleSim(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"],
+                               inp["spins"], metro, swapt)
+        for n, k in schedule:
+            sim.sweep(n, k, threads=8)
+        np.testing.assert_array_equal(sp, sim.spins(), err_msg=f"spins vs oracle, {tag}")
+        np.testing.assert_array_equal(en, sim.energies(), err_msg=f"energies vs oracle, {tag}")
+        assert ctr == (sim.sweep_index, sim.pass_index), tag
+
+
+@pytest.mark.parametrize("segment", [1, 5000, 1 << 24])
+def test_segment_length_does_not_change_results(segment):
+    """Unit pieces of 8 sweeps up to whole calls: the same trajectories."""
+    insts = instances([(4, 2, 16, 2), (8, 2, 24, 2), (10, 1, 9, 2), (16, 1, 32, 2)], 900)
+    members = [make(i) for i in insts]
+    batch = ea.Batch([m[0] for m in members])
+    batch.set_segment(segment)
+    schedule = [(53, 10), (19, 4)]
+    for n, k in schedule:
+        batch.sweep(n, k)
+    batch.sync()
+    for inst, (gpu, *_rest) in zip(insts, members):
+        sp, en, ctr = state(gpu)
+        sp_a, en_a, ctr_a = run_alone(inst, schedule)
+        np.testing.assert_array_equal(sp, sp_a, err_msg=f"L={inst.L} segment={segment}")
+        np.testing.assert_array_equal(en, en_a)
+        assert ctr == ctr_a
+
+
+def test_every_hostable_plan_gives_the_same_result():
+    inst = W.Instance(L=8, G=2, NT=24, C=2, seed=77, tmin=0.9, tmax=2.0, input_seed=78)
+    ref = run_alone(inst, [(30, 3)])
+    probe, *_ = make(inst)
+    plans = probe.plans()
+    tried = 0
+    for idx, p in enumerate(plans):
+        if p["threads"] > 512:
+            continue
+        gpu, *_ = make(inst)
+        batch = ea.Batch([gpu])
+        batch.set_plan(0, idx)
+        batch.sweep(30, 3)
+        batch.sync()
+        sp, en, ctr = state(gpu)
+        np.testing.assert_array_equal(sp, ref[0], err_msg=f"plan {idx}: {p}")
+        np.testing.assert_array_equal(en, ref[1])
+        assert ctr == ref[2]
+        tried += 1
+    assert tried >= 2
+
+
+def test_graph_replay_over_repeated_calls():
+    """Same-shape calls replay the captured launch; the state keeps advancing correctly."""
+    insts = instances([(6, 2, 8, 2), (16, 1, 32, 1)], 1300)
+    members = [make(i) for i in insts]
+    batch = ea.Batch([m[0] for m in members])
+    for _ in range(5):
+        batch.sweep(10, 10)
+    batch.sync()
+    assert batch.launches == 10
+    for inst, (gpu, *_rest) in zip(insts, members):
+        sp, en, ctr = state(gpu)
+        sp_a, en_a, ctr_a = run_alone(inst, [(10, 10)] * 5)
+        np.testing.assert_array_equal(sp, sp_a)
+        np.testing.assert_array_equal(en, en_a)
+        assert ctr == ctr_a == (50, 5)
+
+
+def test_members_interleave_with_their_own_sweeps_and_rejoin():
+    inst_a, inst_b = instances([(8, 1, 24, 2), (12, 1, 32, 2)], 1700)
+    (a, *_), (b, *_) = make(inst_a), make(inst_b)
+    batch = ea.Batch([a, b])
+    batch.sweep(12, 5)
+    batch.sync()
+    a.sweep(7, 5)          # alone, between batched calls (counters continue)
+    batch.clear()
+    batch.add(b)
+    batch.sweep(9, 5)
+    batch.add(a)
+    batch.sweep(4, 2)
+    batch.sync()
+    sa = state(a)
+    sb = state(b)
+    ra = run_alone(inst_a, [(12, 5), (7, 5), (4, 2)])
+    rb = run_alone(inst_b, [(12, 5), (9, 5), (4, 2)])
+    for s, r in ((sa, ra), (sb, rb)):
+        np.testing.assert_array_equal(s[0], r[0])
+        np.testing.assert_array_equal(s[1], r[1])
+        assert s[2] == r[2]
+
+
+def test_empty_batch_and_zero_sweeps_are_no_ops():
+    batch = ea.Batch()
+    batch.sweep(10, 1)
+    batch.sync()
+    inst = instances([(4, 1, 4, 2)], 2100)[0]
+    gpu, inp, *_ = make(inst)
+    batch.add(gpu)
+    batch.sweep(0, 1)
+    batch.sync()
+    assert gpu.counters == (0, 0)
+    np.testing.assert_array_equal(gpu.read_spins().cpu().numpy().view(np.uint32), inp["spins"])
+    assert batch.launches == 0
