@@ -160,6 +160,8 @@ typedef struct {
     int32_t group_threads;     /* threads per lattice (form 1: per lattice row-parity class) */
     int32_t lattices_per_cta;
     uint64_t smem_bytes;       /* dynamic shared memory per CTA */
+    int32_t units_per_cta;     /* unit forms: (group, copy) units a CTA runs in lockstep (1
+                                  outside batches); chunked: 0 */
 } ea_plan_desc;
 
 int ea_plan_count(const ea_ctx *ctx);
@@ -198,13 +200,31 @@ int ea_batch_create(void *stream, ea_batch **out);
 /* ctx must outlive its membership; adding a member twice is EA_EINVAL. */
 int ea_batch_add(ea_batch *batch, ea_ctx *ctx);
 int ea_batch_clear(ea_batch *batch);
-/* Plan a member runs under in the batch (index into its ea_plan_* list, or
- * -1 for automatic); plans wider than 512 threads are refused. */
+/* Plans a member can run under inside the batch kernel (its own list, made
+ * for CTAs of up to 512 threads: the L % 8 == 0 unit kernel, the generic unit
+ * body with several lockstep units per CTA, balanced slot chunks).  All give
+ * bit-identical results.  ea_batch_plan_current: the plan the next call uses
+ * (the explicit choice, else a default that keeps the most threads busy). */
+int ea_batch_plan_count(const ea_batch *batch, uint32_t member);
+int ea_batch_plan_info(const ea_batch *batch, uint32_t member, int index, ea_plan_desc *out);
+int ea_batch_plan_current(const ea_batch *batch, uint32_t member);
+/* Selects a member's plan by index into its batch list; -1 = automatic. */
 int ea_batch_set_plan(ea_batch *batch, uint32_t member, int plan_index);
-/* Work of one unit task in site-word updates (sweeps x N x NT); 0 = default. */
+/* Width of the batch kernel: 384 or 512 threads a CTA, 0 = automatic (384
+ * unless a chosen plan needs more).  Plans wider than the width fail the
+ * next ea_batch_sweep with EA_EUNSUPPORTED. */
+int ea_batch_set_width(ea_batch *batch, int threads);
+/* Work of one unit task in site-word updates (sweeps x N x NT x units); 0 = default. */
 int ea_batch_set_segment(ea_batch *batch, uint32_t site_words);
 int ea_batch_sweep(ea_batch *batch, uint32_t n_sweeps, uint32_t swap_every);
 int ea_batch_sync(ea_batch *batch);
+/* Batch autotuner: for each kernel width, a coordinate descent over every
+ * member's plans, each probe a warm call and a timed call of probe_sweeps
+ * sweeps of the whole batch from the current state (restored after each
+ * call); keeps the fastest width and plans.  Spins, energies and counters are
+ * unchanged.  best_ms (may be NULL) receives the best probe's milliseconds.
+ * Allocates a copy of every member's state while it runs; synchronises. */
+int ea_batch_autotune(ea_batch *batch, uint32_t probe_sweeps, uint32_t swap_every, float *best_ms);
 uint64_t ea_batch_launch_count(const ea_batch *batch);
 void ea_batch_destroy(ea_batch *batch);
 

@@ -48,7 +48,7 @@ class _SweepArgs(ctypes.Structure):
 class _PlanDesc(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("group_threads", ctypes.c_int32), ("lattices_per_cta", ctypes.c_int32),
-                ("smem_bytes", ctypes.c_uint64)]
+                ("smem_bytes", ctypes.c_uint64), ("units_per_cta", ctypes.c_int32)]
 
 
 PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked"}
@@ -57,8 +57,9 @@ EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_s
            "ea_pt_swap", "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
            "ea_get_counters", "ea_sync", "ea_launch_count", "ea_plan_count", "ea_plan_current",
            "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_batch_create", "ea_batch_add",
-           "ea_batch_clear", "ea_batch_set_plan", "ea_batch_set_segment", "ea_batch_sweep",
-           "ea_batch_sync", "ea_batch_launch_count", "ea_batch_destroy", "ea_run",
+           "ea_batch_clear", "ea_batch_plan_count", "ea_batch_plan_info", "ea_batch_plan_current",
+           "ea_batch_set_plan", "ea_batch_set_width", "ea_batch_set_segment", "ea_batch_sweep",
+           "ea_batch_sync", "ea_batch_autotune", "ea_batch_launch_count", "ea_batch_destroy", "ea_run",
            "ea_pt_swap_static", "ea_strerror"]
 
 
@@ -102,7 +103,12 @@ def load_library(path: str | None = None):
     lib.ea_batch_create.argtypes = [vp, ctypes.POINTER(vp)]
     lib.ea_batch_add.argtypes = [vp, vp]
     lib.ea_batch_clear.argtypes = [vp]
+    lib.ea_batch_plan_count.argtypes = [vp, u32]
+    lib.ea_batch_plan_info.argtypes = [vp, u32, i32, ctypes.POINTER(_PlanDesc)]
+    lib.ea_batch_plan_current.argtypes = [vp, u32]
     lib.ea_batch_set_plan.argtypes = [vp, u32, i32]
+    lib.ea_batch_set_width.argtypes = [vp, i32]
+    lib.ea_batch_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_float)]
     lib.ea_batch_set_segment.argtypes = [vp, u32]
     lib.ea_batch_sweep.argtypes = [vp, u32, u32]
     lib.ea_batch_sync.argtypes = [vp]
@@ -117,11 +123,19 @@ def load_library(path: str | None = None):
                  "ea_get_counters", "ea_sync", "ea_run", "ea_plan_count", "ea_plan_current",
                  "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_pt_swap_static",
                  "ea_batch_create", "ea_batch_add", "ea_batch_clear", "ea_batch_set_plan",
-                 "ea_batch_set_segment", "ea_batch_sweep", "ea_batch_sync"):
+                 "ea_batch_set_segment", "ea_batch_sweep", "ea_batch_sync", "ea_batch_plan_count",
+                 "ea_batch_plan_info", "ea_batch_plan_current", "ea_batch_set_width",
+                 "ea_batch_autotune"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
         _lib = lib
     return lib
+
+
+def _plan_dict(d: _PlanDesc) -> dict:
+    return {"form": PLAN_FORMS.get(d.form, d.form), "threads": d.threads,
+            "group_threads": d.group_threads, "lattices_per_cta": d.lattices_per_cta,
+            "smem_bytes": d.smem_bytes, "units_per_cta": d.units_per_cta}
 
 
 def _check(rc: int, what: str):
@@ -290,9 +304,7 @@ class Ensemble:
         for i in range(self.lib.ea_plan_count(self.ctx)):
             d = _PlanDesc()
             _check(self.lib.ea_plan_info(self.ctx, i, ctypes.byref(d)), "ea_plan_info")
-            out.append({"form": PLAN_FORMS.get(d.form, d.form), "threads": d.threads,
-                        "group_threads": d.group_threads, "lattices_per_cta": d.lattices_per_cta,
-                        "smem_bytes": d.smem_bytes})
+            out.append(_plan_dict(d))
         return out
 
     @property
@@ -334,8 +346,37 @@ class Batch:
         _check(self.lib.ea_batch_clear(self.b), "ea_batch_clear")
         self.members = []
 
+    def plans(self, member: int) -> list[dict]:
+        """The member's batch plans (its own list for the batch kernel)."""
+        n = self.lib.ea_batch_plan_count(self.b, int(member))
+        if n < 0:
+            raise EAError(n, "ea_batch_plan_count")
+        out = []
+        for i in range(n):
+            d = _PlanDesc()
+            _check(self.lib.ea_batch_plan_info(self.b, int(member), i, ctypes.byref(d)),
+                   "ea_batch_plan_info")
+            out.append(_plan_dict(d))
+        return out
+
+    def plan(self, member: int) -> int:
+        r = self.lib.ea_batch_plan_current(self.b, int(member))
+        if r < -1:
+            raise EAError(r, "ea_batch_plan_current")
+        return int(r)
+
     def set_plan(self, member: int, plan_index: int):
         _check(self.lib.ea_batch_set_plan(self.b, int(member), int(plan_index)), "ea_batch_set_plan")
+
+    def set_width(self, threads: int):
+        _check(self.lib.ea_batch_set_width(self.b, int(threads)), "ea_batch_set_width")
+
+    def autotune(self, probe_sweeps: int = 100, swap_every: int = 10) -> float:
+        """Times plan choices on the whole batch (state restored); keeps the fastest."""
+        ms = ctypes.c_float(0.0)
+        _check(self.lib.ea_batch_autotune(self.b, int(probe_sweeps), int(swap_every),
+                                          ctypes.byref(ms)), "ea_batch_autotune")
+        return float(ms.value)
 
     def set_segment(self, site_words: int):
         _check(self.lib.ea_batch_set_segment(self.b, int(site_words)), "ea_batch_set_segment")

@@ -338,6 +338,7 @@ int ea_plan_info(const ea_ctx *c, int index, ea_plan_desc *out)
     out->group_threads = p.threads_per_lattice;
     out->lattices_per_cta = p.lattices_per_cta;
     out->smem_bytes = p.smem;
+    out->units_per_cta = p.unit ? 1 : 0;
     return EA_OK;
 }
 

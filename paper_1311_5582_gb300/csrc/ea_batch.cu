@@ -41,18 +41,101 @@ __global__ void k_batch_init(const BatchHdr *hdr, uint32_t *ready, BatchCtl *ctl
     }
 }
 
-size_t plan_task_smem(const ea_ctx *c, const Plan &p)
+
+// Thread counts of the two batch kernels: 384 (up to 168 registers a
+// thread, which the L % 8 == 0 unit kernel needs to run without spills) and 512.
+constexpr int kBatchSmallThreads = 384;
+
+// One way to run a member inside the batch kernel.
+struct BPlan {
+    int form;               // BatchForm
+    int p1, p2;             // as in BatchInst
+    int threads;            // threads the plan keeps busy
+    bool swap_smem, j_smem;
+    size_t smem;            // dynamic shared memory a task needs
+};
+
+int pow2_ceil(int x)
 {
-    const int N = (int)c->N, NT = (int)c->NT;
-    size_t b = 0;
-    if (p.form == kFormUnitFast)
-        b = fast_unit_smem((int)c->L, NT, c->swap_len, p.swap_in_smem, false, false);
-    else if (p.form == kFormUnit)
-        b = UnitSmem::base_bytes(N, NT) + (p.swap_in_smem ? UnitSmem::swap_bytes(NT, c->swap_len) : 0);
-    else
-        b = p.smem;
-    const size_t swap_need = (size_t)(kMaxTemps * kLanes + kMaxTemps) * 4;
-    return b > swap_need ? b : swap_need;
+    int p = 1;
+    while (p < x) p *= 2;
+    return p;
+}
+
+size_t swap_scratch_bytes() { return (size_t)(kMaxTemps * kLanes + kMaxTemps) * 4; }
+
+// Candidate plans of a context for batch kernels of up to 512 threads: the
+// L % 8 == 0 unit kernel, the generic unit body with as many lockstep units
+// per CTA as fit, and slot chunks balanced over the fewest CTAs.
+std::vector<BPlan> batch_candidates(const ea_ctx *c, size_t optin)
+{
+    std::vector<BPlan> out;
+    const int L = (int)c->L, NT = (int)c->NT, N = L * L * L, Q = N / 8;
+    const uint32_t units = c->G * c->C;
+    const int tpl_min = pow2_ceil((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
+    const int tpl_max = pow2_ceil(Q);
+    auto add = [&](const BPlan &p) {
+        if (p.threads < 1 || p.threads > kBatchMaxThreads) return;
+        if ((p.smem > swap_scratch_bytes() ? p.smem : swap_scratch_bytes()) > optin) return;
+        for (const BPlan &q : out)
+            if (q.form == p.form && q.p1 == p.p1 && q.p2 == p.p2) return;
+        out.push_back(p);
+    };
+    // specialised unit kernel (variants compiled into the batch kernel)
+    const int fast[][2] = {{8, 8}, {8, 4}, {16, 32}, {16, 64}};
+    for (const auto &v : fast) {
+        if (v[0] != L) continue;
+        const int t = fast_unit_threads(L, v[1], NT);
+        if (t == 0 || t > kBatchMaxThreads) continue;
+        const bool sw = fast_unit_smem(L, NT, c->swap_len, true, false, false) <= optin;
+        add({kBFast, v[1], 0, t, sw, true, fast_unit_smem(L, NT, c->swap_len, sw, false, false)});
+    }
+    // generic unit body, m lockstep units per CTA
+    for (int tpl = tpl_min; tpl <= tpl_max; tpl *= 2)
+        for (int maxt : {kBatchSmallThreads, kBatchMaxThreads}) {
+            int m = maxt / (tpl * NT);
+            if (m > kMaxTemps / NT) m = kMaxTemps / NT;
+            if ((uint32_t)m > units) m = (int)units;
+            for (; m >= 1; --m) {
+                size_t smem = UnitSmem::base_bytes(N, NT, m);
+                if (smem > optin) continue;
+                const size_t sw = UnitSmem::swap_bytes(NT, c->swap_len);
+                const bool sws = smem + sw <= optin;
+                add({kBUnit, tpl, m, tpl * m * NT, sws, true, smem + (sws ? sw : 0)});
+                break;
+            }
+        }
+    // slot chunks: nlat lattices per CTA, as few CTAs per unit as fit, balanced
+    const size_t lat = (size_t)N * 4, jb = (size_t)3 * N * 4, eb = (size_t)kMaxTemps * kLanes * 4;
+    for (int tpl = tpl_min; tpl <= tpl_max && tpl <= kBatchMaxThreads; tpl *= 2)
+        for (int maxt : {kBatchSmallThreads, kBatchMaxThreads}) {
+            const bool js = jb + lat + eb <= optin;
+            const size_t budget = optin - (js ? jb : 0) - eb;
+            int nlat = maxt / tpl;
+            if (nlat > NT) nlat = NT;
+            if ((size_t)nlat > budget / lat) nlat = (int)(budget / lat);
+            if (nlat < 1) continue;
+            const int chunks = (NT + nlat - 1) / nlat;
+            nlat = (NT + chunks - 1) / chunks;
+            add({kBChunk, tpl, nlat, tpl * nlat, false, js, (size_t)nlat * lat + (js ? jb : 0) + eb});
+        }
+    return out;
+}
+
+// Default: the candidate within `maxt` threads that keeps most threads busy;
+// ties go to the specialised kernel, then the unit body, then chunks.
+int default_candidate(const std::vector<BPlan> &cands, int maxt)
+{
+    int best = -1;
+    auto rank = [](const BPlan &p) { return p.form == kBFast ? 2 : p.form == kBUnit ? 1 : 0; };
+    for (int i = 0; i < (int)cands.size(); ++i) {
+        const BPlan &p = cands[(size_t)i];
+        if (p.threads > maxt) continue;
+        if (best < 0) { best = i; continue; }
+        const BPlan &q = cands[(size_t)best];
+        if (p.threads > q.threads || (p.threads == q.threads && rank(p) > rank(q))) best = i;
+    }
+    return best;
 }
 
 }  // namespace
@@ -61,9 +144,12 @@ size_t plan_task_smem(const ea_ctx *c, const Plan &p)
 struct ea_batch {
     cudaStream_t stream;
     int device;
+    size_t optin;
     std::vector<ea_ctx *> ctxs;
-    std::vector<int> plan_override;        // per context: plan index or -1 (automatic)
-    uint32_t seg_target;                   // site-words per unit piece (0: default)
+    std::vector<std::vector<ea::BPlan>> cands;  // per member: batch candidate plans
+    std::vector<int> choice;                    // per member: candidate index, -1 automatic
+    int force_threads;                          // 0, or the batch kernel's width (384 / 512)
+    uint32_t seg_target;                        // site-words per unit piece (0: default)
     // device buffers: upload area (header + instance table), task queue, flags, joins
     unsigned char *d_up;
     ea::BatchTask *d_tasks;
@@ -118,25 +204,43 @@ cudaError_t grow_host(T **p, size_t *cap, size_t need)
     return e;
 }
 
-// Thread counts of the two batch kernels: 384 (up to 168 registers a
-// thread, which the L % 8 == 0 unit kernel needs to run without spills) and 512.
-constexpr int kBatchSmallThreads = 384;
-
-// The plan a context runs under in a batch: an explicit choice if the batch
-// kernel can host it (<= 512 threads); else its selected plan, or the first
-// in its list, that fits 384 threads; else the first that fits 512.
-const ea::Plan *batch_plan(const ea_ctx *c, int override_idx)
+// Width of the batch kernel: forced, else 384 if every member's plan fits.
+int kernel_width(const ea_batch *b, const std::vector<int> &resolved)
 {
-    if (override_idx >= 0 && override_idx < (int)c->plans.size() &&
-        c->plans[(size_t)override_idx].threads <= ea::kBatchMaxThreads)
-        return &c->plans[(size_t)override_idx];
-    if (c->plan.threads <= kBatchSmallThreads) return &c->plan;
-    for (const ea::Plan &p : c->plans)
-        if (p.threads <= kBatchSmallThreads) return &p;
-    if (c->plan.threads <= ea::kBatchMaxThreads) return &c->plan;
-    for (const ea::Plan &p : c->plans)
-        if (p.threads <= ea::kBatchMaxThreads) return &p;
-    return nullptr;
+    if (b->force_threads) return b->force_threads;
+    for (size_t i = 0; i < resolved.size(); ++i)
+        if (b->cands[i][(size_t)resolved[i]].threads > ea::kBatchSmallThreads) return ea::kBatchMaxThreads;
+    return ea::kBatchSmallThreads;
+}
+
+// Candidate index each member runs under: its explicit choice, else the
+// default for the forced width (or 384, then 512).  -1 if none fits.
+std::vector<int> resolve(const ea_batch *b)
+{
+    std::vector<int> r(b->ctxs.size(), -1);
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        if (b->choice[i] >= 0) { r[i] = b->choice[i]; continue; }
+        const int w = b->force_threads ? b->force_threads : ea::kBatchSmallThreads;
+        r[i] = ea::default_candidate(b->cands[i], w);
+        if (r[i] < 0 && !b->force_threads) r[i] = ea::default_candidate(b->cands[i], ea::kBatchMaxThreads);
+    }
+    return r;
+}
+
+int wait_pending(ea_batch *b)
+{
+    if (!b->pending) return EA_OK;
+    cudaError_t e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return cuda_err(e);
+    b->pending = false;
+    ea::BatchCtl ctl;
+    e = cudaMemcpy(&ctl, b->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(e);
+    if (ctl.err) {
+        b->have_graph = false;           // re-capture: join counters are zeroed again
+        return EA_ETIMEOUT;
+    }
+    return EA_OK;
 }
 
 }  // namespace
@@ -150,7 +254,9 @@ int ea_batch_create(void *stream, ea_batch **out)
     ea_batch *b = new (std::nothrow) ea_batch();
     if (!b) return EA_ENOMEM;
     b->stream = (cudaStream_t)stream;
+    int optin = 0;
     cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ctl, sizeof(ea::BatchCtl));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -158,6 +264,8 @@ int ea_batch_create(void *stream, ea_batch **out)
         delete b;
         return cuda_err(e);
     }
+    // static shared memory of the batch kernel comes out of the same budget
+    b->optin = (size_t)optin > 1024 ? (size_t)optin - 1024 : 0;
     *out = b;
     return EA_OK;
 }
@@ -166,11 +274,13 @@ int ea_batch_add(ea_batch *b, ea_ctx *ctx)
 {
     if (!b || !ctx) return EA_EINVAL;
     if (ctx->device != b->device) return EA_EINVAL;
-    if (!batch_plan(ctx, -1)) return EA_EUNSUPPORTED;
     for (const ea_ctx *m : b->ctxs)
         if (m == ctx) return EA_EINVAL;      // a member runs once per call
+    std::vector<ea::BPlan> c = ea::batch_candidates(ctx, b->optin);
+    if (c.empty()) return EA_EUNSUPPORTED;
     b->ctxs.push_back(ctx);
-    b->plan_override.push_back(-1);
+    b->cands.push_back(std::move(c));
+    b->choice.push_back(-1);
     b->have_graph = false;
     return EA_OK;
 }
@@ -179,19 +289,53 @@ int ea_batch_clear(ea_batch *b)
 {
     if (!b) return EA_EINVAL;
     b->ctxs.clear();
-    b->plan_override.clear();
+    b->cands.clear();
+    b->choice.clear();
     b->have_graph = false;
     return EA_OK;
+}
+
+int ea_batch_plan_count(const ea_batch *b, uint32_t member)
+{
+    if (!b || member >= b->ctxs.size()) return EA_EINVAL;
+    return (int)b->cands[member].size();
+}
+
+int ea_batch_plan_info(const ea_batch *b, uint32_t member, int index, ea_plan_desc *out)
+{
+    if (!b || !out || member >= b->ctxs.size() || index < 0 || index >= (int)b->cands[member].size())
+        return EA_EINVAL;
+    const ea::BPlan &p = b->cands[member][(size_t)index];
+    const int NT = (int)b->ctxs[member]->NT;
+    out->form = p.form == ea::kBFast ? 1 : p.form == ea::kBUnit ? 0 : 2;
+    out->threads = p.threads;
+    out->group_threads = p.p1;
+    out->lattices_per_cta = p.form == ea::kBChunk ? p.p2 : p.form == ea::kBUnit ? p.p2 * NT : NT;
+    out->smem_bytes = p.smem;
+    out->units_per_cta = p.form == ea::kBChunk ? 0 : p.form == ea::kBUnit ? p.p2 : 1;
+    return EA_OK;
+}
+
+int ea_batch_plan_current(const ea_batch *b, uint32_t member)
+{
+    if (!b || member >= b->ctxs.size()) return EA_EINVAL;
+    return resolve(b)[member];
 }
 
 int ea_batch_set_plan(ea_batch *b, uint32_t member, int plan_index)
 {
     if (!b || member >= b->ctxs.size()) return EA_EINVAL;
-    const ea_ctx *c = b->ctxs[member];
-    if (plan_index >= (int)c->plans.size()) return EA_EINVAL;
-    if (plan_index >= 0 && c->plans[(size_t)plan_index].threads > ea::kBatchMaxThreads)
-        return EA_EUNSUPPORTED;
-    b->plan_override[member] = plan_index;
+    if (plan_index < -1 || plan_index >= (int)b->cands[member].size()) return EA_EINVAL;
+    b->choice[member] = plan_index;
+    b->have_graph = false;
+    return EA_OK;
+}
+
+int ea_batch_set_width(ea_batch *b, int threads)
+{
+    if (!b || (threads != 0 && threads != ea::kBatchSmallThreads && threads != ea::kBatchMaxThreads))
+        return EA_EINVAL;
+    b->force_threads = threads;
     b->have_graph = false;
     return EA_OK;
 }
@@ -209,20 +353,14 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
     using namespace ea;
     if (!b) return EA_EINVAL;
     if (n_sweeps == 0 || b->ctxs.empty()) return EA_OK;
-    cudaError_t e = cudaSuccess;
     // the pinned upload buffers are rewritten below: the previous call must be done
-    if (b->pending) {
-        e = cudaEventSynchronize(b->done);
-        if (e != cudaSuccess) return cuda_err(e);
-        b->pending = false;
-        BatchCtl ctl;
-        e = cudaMemcpy(&ctl, b->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_err(e);
-        if (ctl.err) {
-            b->have_graph = false;           // re-capture: join counters are zeroed again
-            return EA_ETIMEOUT;
-        }
-    }
+    int rc = wait_pending(b);
+    if (rc != EA_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    const std::vector<int> plan_of = resolve(b);
+    for (int r : plan_of)
+        if (r < 0) return EA_EUNSUPPORTED;
+    const int threads = kernel_width(b, plan_of);
     const size_t ninst = b->ctxs.size();
     const size_t up_bytes = sizeof(BatchHdr) + ninst * sizeof(BatchInst);
     if ((e = grow_host(&b->h_up, &b->cap_h_up, up_bytes)) != cudaSuccess) return cuda_err(e);
@@ -232,14 +370,13 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
     std::vector<uint64_t> work;      // work left in the task's unit (ordering key)
     uint64_t total = 0;
     uint32_t njoin = 0;
-    size_t smem = 0;
-    int maxt = 0;
+    size_t smem = swap_scratch_bytes();
     const uint32_t seg_target = b->seg_target ? b->seg_target : (1u << 21);
     std::vector<uint64_t> passes(ninst);
     for (size_t i = 0; i < ninst; ++i) {
         ea_ctx *c = b->ctxs[i];
-        const Plan *p = batch_plan(c, b->plan_override[i]);
-        if (!p) return EA_EUNSUPPORTED;
+        const BPlan &p = b->cands[i][(size_t)plan_of[i]];
+        if (p.threads > threads) return EA_EUNSUPPORTED;
         BatchInst &I = insts[i];
         std::memset(&I, 0, sizeof(I));
         I.a.spins = c->d_spins;
@@ -258,16 +395,16 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
         I.a.swap_every = swap_every;
         I.a.P0 = c->pass;
         I.L = (int32_t)c->L;
+        I.form = p.form;
+        I.p1 = p.p1;
+        I.p2 = p.p2;
         I.units = c->G * c->C;
-        I.swap_smem = p->swap_in_smem ? 1 : 0;
-        I.j_smem = p->j_in_smem ? 1 : 0;
+        I.swap_smem = p.swap_smem ? 1 : 0;
+        I.j_smem = p.j_smem ? 1 : 0;
         passes[i] = swaps_between(c->sweep, c->sweep + n_sweeps, swap_every);
         const uint64_t unit_work = (uint64_t)n_sweeps * c->N * c->NT;
-        if (p->form == kFormChunked) {
-            I.form = kBChunk;
-            I.p1 = p->threads_per_lattice;
-            I.p2 = p->lattices_per_cta;
-            I.nchunks = (c->NT + (uint32_t)p->lattices_per_cta - 1) / (uint32_t)p->lattices_per_cta;
+        if (p.form == kBChunk) {
+            I.nchunks = (c->NT + (uint32_t)p.p2 - 1) / (uint32_t)p.p2;
             I.pieces = intervals_of(c->sweep, n_sweeps, swap_every);
             I.join_base = njoin;
             njoin += I.units;
@@ -278,23 +415,21 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
                     work.push_back(unit_work);
                 }
         } else {
-            I.form = p->form == kFormUnitFast ? kBFast : kBUnit;
-            I.p1 = p->threads_per_lattice;
-            const uint64_t per_sweep = (uint64_t)c->N * c->NT;
+            const uint32_t m = p.form == kBUnit ? (uint32_t)p.p2 : 1u;
+            const uint64_t per_sweep = (uint64_t)c->N * c->NT * m;
             uint64_t seg = seg_target / (per_sweep ? per_sweep : 1);
             if (seg < 8) seg = 8;
             if (seg > n_sweeps) seg = n_sweeps;
             I.seg = (uint32_t)seg;
             I.pieces = (uint32_t)((n_sweeps + seg - 1) / seg);
-            total += (uint64_t)I.units * I.pieces;
-            for (uint32_t u = 0; u < I.units; ++u) {
+            const uint32_t tasks = (I.units + m - 1) / m;
+            total += (uint64_t)tasks * I.pieces;
+            for (uint32_t u = 0; u < I.units; u += m) {
                 init.push_back({(uint32_t)i, u, 0u, 0u});
                 work.push_back(unit_work);
             }
         }
-        const size_t need = plan_task_smem(c, *p);
-        if (need > smem) smem = need;
-        if (p->threads > maxt) maxt = p->threads;
+        if (p.smem > smem) smem = p.smem;
     }
     if (total > 0xFFFFFFF0ull) return EA_EINVAL;
     // longest unit first
@@ -309,7 +444,6 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
     hdr->ninit = (uint32_t)init.size();
     hdr->ninst = (uint32_t)ninst;
 
-    const int threads = maxt <= kBatchSmallThreads ? kBatchSmallThreads : kBatchMaxThreads;
     const void *kern = threads == kBatchSmallThreads ? batch_kernel_384() : batch_kernel_512();
     const bool same_shape = b->have_graph && b->g_ninst == ninst && b->g_ninit == init.size() &&
                             b->g_total == total && b->g_smem == smem && b->g_threads == threads;
@@ -398,18 +532,107 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
 int ea_batch_sync(ea_batch *b)
 {
     if (!b) return EA_EINVAL;
-    if (!b->pending) return EA_OK;
-    cudaError_t e = cudaEventSynchronize(b->done);
-    if (e != cudaSuccess) return cuda_err(e);
-    b->pending = false;
-    ea::BatchCtl ctl;
-    e = cudaMemcpy(&ctl, b->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_err(e);
-    if (ctl.err) {
-        b->have_graph = false;
-        return EA_ETIMEOUT;
+    return wait_pending(b);
+}
+
+int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, float *best_ms)
+{
+    using namespace ea;
+    if (!b || probe_sweeps == 0) return EA_EINVAL;
+    if (b->ctxs.empty()) return EA_OK;
+    int rc = wait_pending(b);
+    if (rc != EA_OK) return rc;
+    // save every member's state; each probe starts from it and is undone
+    const size_t n = b->ctxs.size();
+    std::vector<uint32_t *> sp(n, nullptr);
+    std::vector<int32_t *> en(n, nullptr);
+    std::vector<uint64_t> sw(n), ps(n), ln(n);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    auto bytes_s = [&](size_t i) { const ea_ctx *c = b->ctxs[i]; return (size_t)c->G * c->C * c->NT * c->N * 4; };
+    auto bytes_e = [&](size_t i) { const ea_ctx *c = b->ctxs[i]; return (size_t)c->G * c->C * c->NT * kLanes * 4; };
+    for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        ea_ctx *c = b->ctxs[i];
+        sw[i] = c->sweep; ps[i] = c->pass; ln[i] = c->launches;
+        e = cudaMalloc(&sp[i], bytes_s(i));
+        if (e == cudaSuccess) e = cudaMalloc(&en[i], bytes_e(i));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sp[i], c->d_spins, bytes_s(i), cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(en[i], c->d_energy, bytes_e(i), cudaMemcpyDeviceToDevice, b->stream);
     }
-    return EA_OK;
+    auto restore = [&]() -> int {
+        int r = wait_pending(b);
+        for (size_t i = 0; i < n; ++i) {
+            ea_ctx *c = b->ctxs[i];
+            cudaError_t x = cudaMemcpyAsync(c->d_spins, sp[i], bytes_s(i), cudaMemcpyDeviceToDevice, b->stream);
+            if (x == cudaSuccess) x = cudaMemcpyAsync(c->d_energy, en[i], bytes_e(i), cudaMemcpyDeviceToDevice, b->stream);
+            if (x != cudaSuccess && r == EA_OK) r = cuda_err(x);
+            c->sweep = sw[i]; c->pass = ps[i]; c->launches = ln[i];
+        }
+        return r;
+    };
+    // one probe: a warm call (captures the graph), then a timed one
+    auto probe = [&](float *ms) -> int {
+        int r = ea_batch_sweep(b, probe_sweeps, swap_every);
+        if (r == EA_OK) r = restore();
+        if (r == EA_OK && cudaEventRecord(t0, b->stream) != cudaSuccess) r = EA_ECUDA;
+        if (r == EA_OK) r = ea_batch_sweep(b, probe_sweeps, swap_every);
+        if (r == EA_OK && cudaEventRecord(t1, b->stream) != cudaSuccess) r = EA_ECUDA;
+        if (r == EA_OK) r = restore();
+        if (r == EA_OK && cudaEventSynchronize(t1) != cudaSuccess) r = EA_ECUDA;
+        if (r == EA_OK && cudaEventElapsedTime(ms, t0, t1) != cudaSuccess) r = EA_ECUDA;
+        return r;
+    };
+    const std::vector<int> choice0 = b->choice;
+    const int force0 = b->force_threads;
+    std::vector<int> best_choice = choice0;
+    int best_width = force0;
+    float best = 3.0e38f;
+    rc = e == cudaSuccess ? EA_OK : cuda_err(e);
+    // coordinate descent over each member's candidates, per kernel width
+    for (int width : {kBatchSmallThreads, kBatchMaxThreads}) {
+        if (rc != EA_OK) break;
+        b->force_threads = width;
+        std::vector<int> cur(n, -1);
+        bool ok = true;
+        for (size_t i = 0; i < n; ++i) {
+            cur[i] = default_candidate(b->cands[i], width);
+            if (cur[i] < 0) ok = false;
+        }
+        if (!ok) continue;
+        b->choice = cur;
+        b->have_graph = false;
+        float t = 0.f;
+        if ((rc = probe(&t)) != EA_OK) break;
+        for (size_t i = 0; i < n && rc == EA_OK; ++i)
+            for (int j = 0; j < (int)b->cands[i].size(); ++j) {
+                if (j == cur[i] || b->cands[i][(size_t)j].threads > width) continue;
+                b->choice = cur;
+                b->choice[i] = j;
+                float tj = 0.f;
+                if ((rc = probe(&tj)) != EA_OK) break;
+                if (tj < t) { t = tj; cur[i] = j; }
+            }
+        if (rc == EA_OK && t < best) {
+            best = t;
+            best_choice = cur;
+            best_width = width;
+        }
+    }
+    b->choice = rc == EA_OK ? best_choice : choice0;
+    b->force_threads = rc == EA_OK ? best_width : force0;
+    b->have_graph = false;
+    const int r2 = restore();
+    cudaStreamSynchronize(b->stream);
+    for (size_t i = 0; i < n; ++i) {
+        cudaFree(sp[i]);
+        cudaFree(en[i]);
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    if (rc == EA_OK) rc = r2;
+    if (rc == EA_OK && best_ms) *best_ms = best;
+    return rc;
 }
 
 uint64_t ea_batch_launch_count(const ea_batch *b) { return b ? b->launches : 0; }

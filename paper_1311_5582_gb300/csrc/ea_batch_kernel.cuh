@@ -17,9 +17,10 @@ enum BatchForm { kBUnit = 0, kBFast = 1, kBChunk = 2 };
 
 struct BatchInst {
     SweepLaunch a;          // s0, n_sweeps, P0, swap_every of this call
-    int32_t L, form, p1, p2;    // p1: threads per lattice (unit, chunk) or HP (fast); p2: nlat
+    int32_t L, form, p1, p2;    // p1: threads per lattice (unit, chunk) or HP (fast);
+                                // p2: units per task (unit) or lattices per chunk (chunked)
     int32_t swap_smem, j_smem;
-    uint32_t units;         // G * C
+    uint32_t units;         // G * C; a unit task starts at unit `task.unit`
     uint32_t pieces;        // unit forms: sweep segments; chunked: swap intervals
     uint32_t seg;           // unit forms: sweeps per segment
     uint32_t nchunks;       // chunked: CTAs per unit and interval
@@ -81,10 +82,10 @@ __host__ __device__ inline uint32_t intervals_of(uint64_t s_begin, uint32_t n, u
 namespace {
 
 __device__ __forceinline__ void run_unit(int L, uint32_t *base, const SweepLaunch &a, uint32_t unit,
-                                         int tpl, int swap_smem)
+                                         int tpl, int swap_smem, int m)
 {
     switch (L) {
-#define EA_U(X) case X: unit_body<X>(base, a, unit, tpl, 0, swap_smem); break;
+#define EA_U(X) case X: unit_body<X>(base, a, unit, tpl, 0, swap_smem, m); break;
         EA_U(4) EA_U(6) EA_U(8) EA_U(10) EA_U(12) EA_U(14) EA_U(16) EA_U(20) EA_U(24) EA_U(32)
 #undef EA_U
     default: break;
@@ -199,7 +200,9 @@ k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tas
         if (s_state) break;
         const BatchTask t = s_t;
         const BatchInst &I = insts[t.inst];
-        if (I.form == kBUnit) run_unit(I.L, base, s_a, t.unit, I.p1, I.swap_smem);
+        if (I.form == kBUnit)
+            run_unit(I.L, base, s_a, t.unit, I.p1, I.swap_smem,
+                     (int)min((uint32_t)I.p2, I.units - t.unit));
         else if (I.form == kBFast) run_fast(I.L, I.p1, base, s_a, t.unit, I.swap_smem);
         else run_chunk(I.L, I.j_smem, base, s_a, t.unit, (int)t.chunk, I.p1, I.p2);
         __syncthreads();

@@ -16,35 +16,44 @@ namespace {
 // replica-exchange passes and measurements.  With C = 2 and overlap
 // measurement the two copies of a group form a 2-CTA cluster and read each
 // other's lattices through distributed shared memory.
+//
+// The persistent batch kernel may give one CTA m > 1 consecutive units of an
+// ensemble (m * NT <= 64), run in lockstep: slot l of the CTA is slot l % NT
+// of unit unit0 + l / NT.  Measurements and the cluster form need m = 1.
 
 template <int L>
-__device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, uint32_t unit, int tpl,
-                                          int cluster_measure, int swap_in_smem)
+__device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, uint32_t unit0, int tpl,
+                                          int cluster_measure, int swap_in_smem, int m = 1)
 {
     using Gm = Geo<L>;
     constexpr int N = Gm::N;
     const int NT = (int)a.NT;
-    uint32_t *S = base;                                       // [NT][2][H]
-    uint32_t *Js = S + (size_t)NT * N;                        // [3][2][H]
-    int *E = reinterpret_cast<int *>(Js + 3 * N);             // [64][32] energies by slot
+    const int MT = m * NT;                                    // slots of the CTA
+    uint32_t *S = base;                                       // [m][NT][2][H]
+    uint32_t *Js = S + (size_t)MT * N;                        // [m][3][2][H]
+    int *E = reinterpret_cast<int *>(Js + (size_t)m * 3 * N); // [64][32] energies by slot
     int *bnd = E + kMaxTemps * kLanes;                        // [64][32] swap accept bounds
     int *nd = bnd + kMaxTemps * kLanes;                       // [64][32] overlap counts
     uint32_t *msk = reinterpret_cast<uint32_t *>(nd + kMaxTemps * kLanes);  // [64]
     uint32_t *Tsw = msk + kMaxTemps;                          // [NT-1][swap_len] if swap_in_smem
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const bool act = tid < tpl * MT;                    // threads beyond the units' groups idle
+    const int lf = act ? tid / tpl : 0, tl = tid - (tid / tpl) * tpl;   // my CTA slot and rank
+    const int ui = lf / NT, l = lf - ui * NT;            // my unit (within the CTA) and slot
+    const uint32_t unit = unit0 + (uint32_t)ui;
     const int c = (int)(unit % a.C);
     const uint32_t g = unit / a.C;
-    const bool act = tid < tpl * NT;                    // threads beyond the unit's groups idle
-    const int l = act ? tid / tpl : 0, tl = tid - (tid / tpl) * tpl;   // my slot and rank
     const int qper = (Gm::Q + tpl - 1) / tpl;
 
-    uint32_t *gS = a.spins + (size_t)unit * NT * N;
-    const uint32_t *gJ = a.bonds + (size_t)g * 3 * N;
-    for (int w = tid; w < NT * N / 4; w += nthr)
+    uint32_t *gS = a.spins + (size_t)unit0 * NT * N;
+    for (int w = tid; w < MT * N / 4; w += nthr)
         reinterpret_cast<uint4 *>(S)[w] = __ldcg(reinterpret_cast<const uint4 *>(gS) + w);
-    for (int w = tid; w < 3 * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(Js)[w] = reinterpret_cast<const uint4 *>(gJ)[w];
+    for (int w = tid; w < m * 3 * N / 4; w += nthr) {
+        const int i = w / (3 * N / 4), r = w - i * (3 * N / 4);
+        const uint32_t gi = (unit0 + (uint32_t)i) / a.C;
+        reinterpret_cast<uint4 *>(Js)[w] = reinterpret_cast<const uint4 *>(a.bonds + (size_t)gi * 3 * N)[r];
+    }
     const uint32_t *swt = a.swapt;
     if (swap_in_smem) {
         const int nsw = (NT - 1) * (int)a.swap_len;
@@ -52,7 +61,8 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
         swt = Tsw;
     }
     const uint32_t t0 = a.metro[l * 3 + 0], t1 = a.metro[l * 3 + 1], t2 = a.metro[l * 3 + 2];
-    uint32_t *mine = S + (size_t)l * N;
+    uint32_t *mine = S + (size_t)lf * N;
+    const uint32_t *myJ = Js + (size_t)ui * 3 * N;
     __syncthreads();
 
     uint64_t P = a.P0;
@@ -66,66 +76,80 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
         if (needE)   // counters add 2 per unsatisfied bond: E = 2U - 3N
-            for (int i = tid; i < NT * kLanes; i += nthr) E[i] = -3 * N;
+            for (int i = tid; i < MT * kLanes; i += nthr) E[i] = -3 * N;
         if (swap_now) {
             // Swap acceptance bounds depend only on the pass index: compute them
-            // now; they are read after the half-sweeps' barriers.
-            for (int i = tid; i < (NT - 1) * kLanes; i += nthr) {
-                const int p = i >> 5, b = i & 31;
-                const uint32_t r = swap_uniform(a.rk, p, b, P, g, c);
+            // now; they are read after the half-sweeps' barriers.  Row
+            // i * (NT - 1) + p: pair p of unit i.
+            for (int i = tid; i < m * (NT - 1) * kLanes; i += nthr) {
+                const int row = i >> 5, b = i & 31;
+                const int ub = row / (NT - 1), p = row - ub * (NT - 1);
+                const uint32_t un = unit0 + (uint32_t)ub;
+                const uint32_t r = swap_uniform(a.rk, p, b, P, un / a.C, (int)(un % a.C));
                 bnd[i] = accept_bound(swt + (size_t)p * a.swap_len, a.swap_len, r);
             }
         }
         if (act)
-            half_sweep<L, false>(mine, Js, 0, tl, tpl, qper, (uint32_t)s, g,
+            half_sweep<L, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g,
                                  (0u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
         __syncthreads();
         if (needE) {
             if (act)
-                half_sweep<L, true>(mine, Js, 1, tl, tpl, qper, (uint32_t)s, g,
+                half_sweep<L, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g,
                                     (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
-            reduce_counters(acc, tpl, E, lane, warp, 2, NT);
+            reduce_counters(acc, tpl, E, lane, warp, 2, MT);
         } else if (act) {
-            half_sweep<L, false>(mine, Js, 1, tl, tpl, qper, (uint32_t)s, g,
+            half_sweep<L, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g,
                                  (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
         }
         __syncthreads();
         if (swap_now) {
-            if (warp == 0) {
-                // Sequential pairs (0,1), (1,2), ... per realization lane; the
-                // configuration carried upward is `cur`.  Loads run one pair ahead.
-                int cur = E[lane];
-                int nxt = E[kLanes + lane];
-                int bb = bnd[lane];
+            for (int uw = warp; uw < m; uw += nthr / 32) {
+                // Sequential pairs (0,1), (1,2), ... of unit `uw` per realization
+                // lane; the configuration carried upward is `cur`.  Loads run one
+                // pair ahead.
+                int *Eu = E + uw * NT * kLanes;
+                const int *bu = bnd + uw * (NT - 1) * kLanes;
+                uint32_t *mu = msk + uw * (NT - 1);
+                int cur = Eu[lane];
+                int nxt = Eu[kLanes + lane];
+                int bb = bu[lane];
                 for (int p = 0; p + 1 < NT; ++p) {
-                    const int nxt2 = (p + 2 < NT) ? E[(p + 2) * kLanes + lane] : 0;
-                    const int bb2 = (p + 2 < NT) ? bnd[(p + 1) * kLanes + lane] : 0;
+                    const int nxt2 = (p + 2 < NT) ? Eu[(p + 2) * kLanes + lane] : 0;
+                    const int bb2 = (p + 2 < NT) ? bu[(p + 1) * kLanes + lane] : 0;
                     const bool ok = (cur - nxt) >= bb;
-                    const uint32_t m = __ballot_sync(kFull, ok);
-                    E[p * kLanes + lane] = ok ? nxt : cur;
+                    const uint32_t msk_p = __ballot_sync(kFull, ok);
+                    Eu[p * kLanes + lane] = ok ? nxt : cur;
                     cur = ok ? cur : nxt;
-                    if (lane == 0) msk[p] = m;
+                    if (lane == 0) mu[p] = msk_p;
                     nxt = nxt2;
                     bb = bb2;
                 }
-                E[(NT - 1) * kLanes + lane] = cur;
+                Eu[(NT - 1) * kLanes + lane] = cur;
             }
             __syncthreads();
             // Masked exchange chain, pairs in order (0,1), (1,2), ..., two words a thread
-            for (int w = tid; w < N / 2; w += nthr) {
-                uint2 x = reinterpret_cast<const uint2 *>(S)[w];
+            for (int wf = tid; wf < m * (N / 2); wf += nthr) {
+                const int ub = wf / (N / 2), w = wf - ub * (N / 2);
+                uint32_t *Su = S + (size_t)ub * NT * N;
+                const uint32_t *mu = msk + ub * (NT - 1);
+                uint2 x = reinterpret_cast<const uint2 *>(Su)[w];
                 for (int p = 0; p + 1 < NT; ++p) {
-                    const uint2 y = reinterpret_cast<const uint2 *>(S + (size_t)(p + 1) * N)[w];
-                    const uint32_t m = msk[p];
-                    const uint32_t dx = (x.x ^ y.x) & m, dy = (x.y ^ y.y) & m;
-                    reinterpret_cast<uint2 *>(S + (size_t)p * N)[w] = make_uint2(x.x ^ dx, x.y ^ dy);
+                    const uint2 y = reinterpret_cast<const uint2 *>(Su + (size_t)(p + 1) * N)[w];
+                    const uint32_t mp = mu[p];
+                    const uint32_t dx = (x.x ^ y.x) & mp, dy = (x.y ^ y.y) & mp;
+                    reinterpret_cast<uint2 *>(Su + (size_t)p * N)[w] = make_uint2(x.x ^ dx, x.y ^ dy);
                     x = make_uint2(y.x ^ dx, y.y ^ dy);
                 }
-                reinterpret_cast<uint2 *>(S + (size_t)(NT - 1) * N)[w] = x;
+                reinterpret_cast<uint2 *>(Su + (size_t)(NT - 1) * N)[w] = x;
             }
             if (a.swap_log != nullptr)
-                for (int p = tid; p + 1 < NT; p += nthr)
-                    a.swap_log[(((size_t)pass_local * a.G + g) * a.C + c) * (NT - 1) + p] = msk[p];
+                for (int i = tid; i < m * (NT - 1); i += nthr) {
+                    const int ub = i / (NT - 1), p = i - ub * (NT - 1);
+                    const uint32_t un = unit0 + (uint32_t)ub;
+                    a.swap_log[(((size_t)pass_local * a.G + un / a.C) * a.C + un % a.C) * (NT - 1) + p] =
+                        msk[i];
+                }
             __syncthreads();
         }
         if (swap_after(s, a.swap_every)) {
@@ -134,9 +158,11 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
         }
         if (a.energy_log != nullptr) {
             const size_t row = (size_t)(s - a.log_s0);
-            for (int i = tid; i < NT * kLanes; i += nthr) {
-                const int t = i >> 5, b = i & 31;
-                a.energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = E[i];
+            for (int i = tid; i < MT * kLanes; i += nthr) {
+                const int lf2 = i >> 5, b = i & 31;
+                const int ub = lf2 / NT, t = lf2 - ub * NT;
+                const uint32_t un = unit0 + (uint32_t)ub;
+                a.energy_log[(((row * a.G + un / a.C) * NT + t) * a.C + un % a.C) * kLanes + b] = E[i];
             }
         }
         if (meas) {
@@ -181,8 +207,8 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
         }
     }
     // energies of the final state, spins back to global memory
-    for (int i = tid; i < NT * kLanes; i += nthr) a.energy[(size_t)unit * NT * kLanes + i] = E[i];
-    for (int w = tid; w < NT * N / 4; w += nthr)
+    for (int i = tid; i < MT * kLanes; i += nthr) a.energy[(size_t)unit0 * NT * kLanes + i] = E[i];
+    for (int w = tid; w < MT * N / 4; w += nthr)
         reinterpret_cast<uint4 *>(gS)[w] = reinterpret_cast<const uint4 *>(S)[w];
 }
 

@@ -369,9 +369,10 @@ __device__ __forceinline__ uint32_t swap_uniform(const RoundKeys &rk, int p, int
 
 
 struct UnitSmem {
-    static size_t base_bytes(int N, int NT)
+    // m units of NT lattices and their bonds, energies, bounds, overlap counts, masks
+    static size_t base_bytes(int N, int NT, int m = 1)
     {
-        return (size_t)NT * N * 4 + (size_t)3 * N * 4 + (size_t)kMaxTemps * kLanes * 4 * 3 +
+        return (size_t)m * NT * N * 4 + (size_t)m * 3 * N * 4 + (size_t)kMaxTemps * kLanes * 4 * 3 +
                (size_t)kMaxTemps * 4;
     }
     static size_t swap_bytes(int NT, uint32_t swap_len)

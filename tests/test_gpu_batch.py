@@ -95,26 +95,59 @@ def test_segment_length_does_not_change_results(segment):
         assert ctr == ctr_a
 
 
-def test_every_hostable_plan_gives_the_same_result():
-    inst = W.Instance(L=8, G=2, NT=24, C=2, seed=77, tmin=0.9, tmax=2.0, input_seed=78)
+@pytest.mark.parametrize("L,G,NT,C", [(8, 2, 24, 2), (4, 3, 16, 2), (6, 2, 20, 2), (10, 2, 28, 1),
+                                       (16, 1, 32, 2)])
+def test_every_batch_plan_gives_the_same_result(L, G, NT, C):
+    """Each plan of the member's batch list (lockstep multi-unit bodies, the
+    specialised kernel, balanced chunks) at both kernel widths."""
+    inst = W.Instance(L=L, G=G, NT=NT, C=C, seed=77 + L, tmin=0.9, tmax=2.0, input_seed=78 + L)
     ref = run_alone(inst, [(30, 3)])
     probe, *_ = make(inst)
-    plans = probe.plans()
-    tried = 0
+    plans = ea.Batch([probe]).plans(0)
+    assert len(plans) >= 2
+    forms = set()
     for idx, p in enumerate(plans):
-        if p["threads"] > 512:
-            continue
-        gpu, *_ = make(inst)
-        batch = ea.Batch([gpu])
-        batch.set_plan(0, idx)
-        batch.sweep(30, 3)
-        batch.sync()
+        for width in (384, 512):
+            if p["threads"] > width:
+                continue
+            gpu, *_ = make(inst)
+            batch = ea.Batch([gpu])
+            batch.set_width(width)
+            batch.set_plan(0, idx)
+            assert batch.plan(0) == idx
+            batch.sweep(30, 3)
+            batch.sync()
+            sp, en, ctr = state(gpu)
+            np.testing.assert_array_equal(sp, ref[0], err_msg=f"plan {idx} width {width}: {p}")
+            np.testing.assert_array_equal(en, ref[1])
+            assert ctr == ref[2]
+            forms.add((p["form"], p["units_per_cta"] > 1))
+    if L == 4:
+        assert ("unit", True) in forms        # several units per CTA were exercised
+
+
+def test_autotune_keeps_state_and_results():
+    insts = instances([(4, 4, 16, 2), (8, 2, 24, 2), (12, 1, 32, 2)], 1500)
+    members = [make(i) for i in insts]
+    batch = ea.Batch([m[0] for m in members])
+    batch.sweep(7, 3)
+    batch.sync()
+    before = [state(m[0]) for m in members]
+    ms = batch.autotune(probe_sweeps=20, swap_every=5)
+    assert ms > 0
+    for m, b in zip(members, before):
+        s = state(m[0])
+        np.testing.assert_array_equal(s[0], b[0])
+        np.testing.assert_array_equal(s[1], b[1])
+        assert s[2] == b[2]
+    batch.sweep(26, 5)
+    batch.sync()
+    for inst, (gpu, *_rest) in zip(insts, members):
         sp, en, ctr = state(gpu)
-        np.testing.assert_array_equal(sp, ref[0], err_msg=f"plan {idx}: {p}")
-        np.testing.assert_array_equal(en, ref[1])
-        assert ctr == ref[2]
-        tried += 1
-    assert tried >= 2
+        sp_a, en_a, ctr_a = run_alone(inst, [(7, 3), (26, 5)])
+        np.testing.assert_array_equal(sp, sp_a, err_msg=f"L={inst.L}")
+        np.testing.assert_array_equal(en, en_a)
+        assert ctr == ctr_a
 
 
 def test_graph_replay_over_repeated_calls():
