@@ -189,9 +189,10 @@ int ea_autotune(ea_ctx *ctx, uint32_t probe_sweeps, uint32_t swap_every, float *
  * device-side queue, longest unit first.  The paper simulates one ensemble at
  * a time (Sec. 3); batching several is this library's own addition, and the
  * arithmetic of each member is that of Sec. 2.3 (sweeps) and Sec. 2.4 (swaps)
- * exactly as in ea_sweep.  The launch and its
- * uploads are captured in a CUDA graph and replayed while the batch's shape
- * is unchanged.  Asynchronous on the batch's stream (NULL = legacy default);
+ * exactly as in ea_sweep.  A call whose shape (members, tasks, shared
+ * memory, width) repeats the previous call's is captured in a CUDA graph
+ * (upload, queue reset, launch) and replayed while the shape stays the same;
+ * other calls launch directly.  Asynchronous on the batch's stream (NULL = legacy default);
  * members must not be used on other streams until ea_batch_sync returns.
  * A device-side wait that runs out (it never should) makes ea_batch_sync
  * return EA_ETIMEOUT instead of hanging. */
@@ -217,6 +218,9 @@ int ea_batch_set_width(ea_batch *batch, int threads);
 /* Work of one unit task in site-word updates (sweeps x N x NT x units); 0 = default. */
 int ea_batch_set_segment(ea_batch *batch, uint32_t site_words);
 int ea_batch_sweep(ea_batch *batch, uint32_t n_sweeps, uint32_t swap_every);
+/* Per-member sweeps: member i advances n_sweeps[i] sweeps (0: left out of
+ * this call) with its own swap_every[i] (host arrays of the member count). */
+int ea_batch_sweep_each(ea_batch *batch, const uint32_t *n_sweeps, const uint32_t *swap_every);
 int ea_batch_sync(ea_batch *batch);
 /* Batch autotuner: for each kernel width, a coordinate descent over every
  * member's plans, each probe a warm call and a timed call of probe_sweeps
@@ -227,6 +231,51 @@ int ea_batch_sync(ea_batch *batch);
 int ea_batch_autotune(ea_batch *batch, uint32_t probe_sweeps, uint32_t swap_every, float *best_ms);
 uint64_t ea_batch_launch_count(const ea_batch *batch);
 void ea_batch_destroy(ea_batch *batch);
+
+/* Serving loop: a server accepts simulation requests from any thread, admits
+ * them in arrival order while their device memory fits its budget, keeps
+ * their state resident, and advances all resident requests together in
+ * rounds of one batched launch (ea_batch_sweep_each), each by up to the
+ * number of sweeps that makes the round last about round_ms; requests that
+ * arrive meanwhile join at the next round (continuous batching).  Each
+ * result is exactly what ea_create + ea_sweep would give alone.  The paper
+ * runs one simulation at a time (Sec. 3); serving is this library's own
+ * addition.  One worker thread per server owns its GPU work; the server uses
+ * the device that is current at ea_server_create. */
+typedef struct ea_server ea_server;
+typedef struct {
+    uint64_t mem_budget;       /* device bytes for resident requests; 0 = 81% of free memory
+                                  (never more than 90% of free memory at creation) */
+    uint32_t max_live;         /* most resident requests; 0 = 256 */
+    uint32_t round_ms;         /* target duration of a round; 0 = 20 */
+} ea_server_opts;
+int ea_server_create(const ea_server_opts *opts, ea_server **out);   /* opts may be NULL */
+
+typedef struct {
+    uint32_t n_sweeps, swap_every;
+    uint32_t *spins_out;       /* HOST [G][NT][C][N] final spins (slot order), or NULL */
+    int32_t *energies_out;     /* HOST [G][NT][C][32] final energies, or NULL */
+} ea_request;
+/* Copies cfg's host inputs and queues the request; *ticket identifies it.
+ * The output buffers must stay valid until ea_poll reports it finished.
+ * Shape errors return at once (EA_EINVAL / EA_EUNSUPPORTED); table errors
+ * and a request larger than the whole budget (EA_ENOMEM) finish the ticket. */
+int ea_submit(ea_server *server, const ea_config *cfg, const ea_request *req, uint64_t *ticket);
+/* Waits up to timeout_us for the ticket: EA_PENDING if unfinished; else the
+ * request's status (EA_OK: outputs written), after which the ticket is
+ * retired and polling it again is EA_EINVAL. */
+int ea_poll(ea_server *server, uint64_t ticket, uint32_t timeout_us);
+typedef struct {
+    uint64_t submitted, completed, failed, queued, live, rounds;
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* completion latency: submit -> outputs written */
+    double flip_attempts;      /* of completed requests: N x NT x C x 32G x sweeps */
+    double busy_s;             /* time with at least one request resident */
+    double span_s;             /* first submission -> last completion */
+    uint64_t mem_budget, peak_bytes;   /* budget and most device bytes resident at once */
+} ea_server_stats;
+int ea_server_stats_get(ea_server *server, ea_server_stats *out);
+/* Stops the worker; requests not yet finished are dropped. */
+void ea_server_destroy(ea_server *server);
 
 /* Host-buffer entry point: creates a context from cfg, runs the sweeps of
  * args (its DEVICE output pointers must be NULL), copies the results to the

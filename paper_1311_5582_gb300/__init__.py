@@ -45,6 +45,27 @@ class _SweepArgs(ctypes.Structure):
                 ("measure_from", ctypes.c_uint64), ("measure_every", ctypes.c_uint32)]
 
 
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_live", ctypes.c_uint32),
+                ("round_ms", ctypes.c_uint32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("n_sweeps", ctypes.c_uint32), ("swap_every", ctypes.c_uint32),
+                ("spins_out", ctypes.c_void_p), ("energies_out", ctypes.c_void_p)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("live", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("flip_attempts", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("span_s", ctypes.c_double), ("mem_budget", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64)]
+
+
 class _PlanDesc(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("group_threads", ctypes.c_int32), ("lattices_per_cta", ctypes.c_int32),
@@ -59,7 +80,9 @@ EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_s
            "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_batch_create", "ea_batch_add",
            "ea_batch_clear", "ea_batch_plan_count", "ea_batch_plan_info", "ea_batch_plan_current",
            "ea_batch_set_plan", "ea_batch_set_width", "ea_batch_set_segment", "ea_batch_sweep",
-           "ea_batch_sync", "ea_batch_autotune", "ea_batch_launch_count", "ea_batch_destroy", "ea_run",
+           "ea_batch_sweep_each", "ea_batch_sync", "ea_batch_autotune", "ea_batch_launch_count", "ea_batch_destroy",
+           "ea_server_create", "ea_submit", "ea_poll", "ea_server_stats_get", "ea_server_destroy",
+           "ea_run",
            "ea_pt_swap_static", "ea_strerror"]
 
 
@@ -111,11 +134,19 @@ def load_library(path: str | None = None):
     lib.ea_batch_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_float)]
     lib.ea_batch_set_segment.argtypes = [vp, u32]
     lib.ea_batch_sweep.argtypes = [vp, u32, u32]
+    lib.ea_batch_sweep_each.argtypes = [vp, vp, vp]
     lib.ea_batch_sync.argtypes = [vp]
     lib.ea_batch_launch_count.argtypes = [vp]
     lib.ea_batch_launch_count.restype = u64
     lib.ea_batch_destroy.argtypes = [vp]
     lib.ea_batch_destroy.restype = None
+    lib.ea_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(vp)]
+    lib.ea_submit.argtypes = [vp, ctypes.POINTER(_Config), ctypes.POINTER(_Request),
+                              ctypes.POINTER(u64)]
+    lib.ea_poll.argtypes = [vp, u64, u32]
+    lib.ea_server_stats_get.argtypes = [vp, ctypes.POINTER(_ServerStats)]
+    lib.ea_server_destroy.argtypes = [vp]
+    lib.ea_server_destroy.restype = None
     lib.ea_strerror.argtypes = [i32]
     lib.ea_strerror.restype = ctypes.c_char_p
     for name in ("ea_build_tables", "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
@@ -125,7 +156,8 @@ def load_library(path: str | None = None):
                  "ea_batch_create", "ea_batch_add", "ea_batch_clear", "ea_batch_set_plan",
                  "ea_batch_set_segment", "ea_batch_sweep", "ea_batch_sync", "ea_batch_plan_count",
                  "ea_batch_plan_info", "ea_batch_plan_current", "ea_batch_set_width",
-                 "ea_batch_autotune"):
+                 "ea_batch_autotune", "ea_batch_sweep_each", "ea_server_create", "ea_submit",
+                 "ea_poll", "ea_server_stats_get"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -384,6 +416,13 @@ class Batch:
     def sweep(self, n_sweeps: int, swap_every: int):
         _check(self.lib.ea_batch_sweep(self.b, int(n_sweeps), int(swap_every)), "ea_batch_sweep")
 
+    def sweep_each(self, n_sweeps, swap_every):
+        """Member i advances n_sweeps[i] sweeps (0: not this call), swap every swap_every[i]."""
+        n = np.ascontiguousarray(n_sweeps, dtype=np.uint32)
+        k = np.ascontiguousarray(swap_every, dtype=np.uint32)
+        assert n.shape == k.shape == (len(self.members),)
+        _check(self.lib.ea_batch_sweep_each(self.b, n.ctypes.data, k.ctypes.data), "ea_batch_sweep_each")
+
     def sync(self):
         _check(self.lib.ea_batch_sync(self.b), "ea_batch_sync")
 
@@ -395,6 +434,67 @@ class Batch:
         if getattr(self, "b", None):
             self.lib.ea_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (ea_server_*): requests are admitted by device memory, kept
+    resident and advanced together in batched rounds; results land in host arrays."""
+
+    def __init__(self, mem_budget: int = 0, max_live: int = 0, round_ms: int = 0):
+        self.lib = load_library()
+        opts = _ServerOpts(int(mem_budget), int(max_live), int(round_ms))
+        h = ctypes.c_void_p(None)
+        _check(self.lib.ea_server_create(ctypes.byref(opts), ctypes.byref(h)), "ea_server_create")
+        self.s = h
+        self._out = {}          # ticket -> (outputs dict, inputs kept alive)
+
+    def submit(self, L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every,
+               want_spins=True, want_energies=True) -> int:
+        cfg, keep = _config(L, G, NT, C, seed, bonds, spins, metro, swapt)
+        N = int(L) ** 3
+        out = {"spins": np.zeros((G, NT, C, N), np.uint32) if want_spins else None,
+               "energies": np.zeros((G, NT, C, 32), np.int32) if want_energies else None}
+        req = _Request(int(n_sweeps), int(swap_every), _ptr(out["spins"]), _ptr(out["energies"]))
+        t = ctypes.c_uint64(0)
+        _check(self.lib.ea_submit(self.s, ctypes.byref(cfg), ctypes.byref(req), ctypes.byref(t)),
+               "ea_submit")
+        self._out[t.value] = out
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """None while pending; the outputs dict when done; raises on a failed request."""
+        rc = self.lib.ea_poll(self.s, int(ticket), int(timeout_us))
+        if rc == EA_PENDING:
+            return None
+        out = self._out.pop(int(ticket), None)
+        _check(rc, f"request {ticket}")
+        return out
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        import time
+        end = time.monotonic() + timeout_s
+        while True:
+            r = self.poll(ticket, 100_000)
+            if r is not None:
+                return r
+            if time.monotonic() > end:
+                raise TimeoutError(f"request {ticket} still pending")
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(self.lib.ea_server_stats_get(self.s, ctypes.byref(st)), "ea_server_stats_get")
+        return {name: getattr(st, name) for name, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.ea_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

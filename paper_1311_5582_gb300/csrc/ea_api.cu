@@ -70,20 +70,50 @@ ea::SweepLaunch base_launch(ea_ctx *c)
     return a;
 }
 
-void free_ctx(ea_ctx *c)
+// Device memory of a context: plain allocations, or stream-ordered ones from
+// a memory pool (no implicit device synchronisation on either side).
+cudaError_t ctx_alloc(ea_ctx *c, void **p, size_t bytes, cudaStream_t st)
+{
+    if (c->pool) return cudaMallocFromPoolAsync(p, bytes, c->pool, st);
+    return cudaMalloc(p, bytes);
+}
+
+void ctx_free(ea_ctx *c, void *p, cudaStream_t st)
+{
+    if (!p) return;
+    if (c->pool) cudaFreeAsync(p, st);
+    else cudaFree(p);
+}
+
+void free_ctx(ea_ctx *c, cudaStream_t st)
 {
     if (!c) return;
-    cudaFree(c->d_spins);
-    cudaFree(c->d_bonds);
-    cudaFree(c->d_metro);
-    cudaFree(c->d_swapt);
-    cudaFree(c->d_masks);
-    cudaFree(c->d_energy);
-    cudaFree(c->d_err);
+    ctx_free(c, c->d_spins, st);
+    ctx_free(c, c->d_bonds, st);
+    ctx_free(c, c->d_metro, st);
+    ctx_free(c, c->d_swapt, st);
+    ctx_free(c, c->d_masks, st);
+    ctx_free(c, c->d_energy, st);
+    ctx_free(c, c->d_err, st);
     delete c;
 }
 
 }  // namespace
+
+namespace ea {
+
+size_t ctx_device_bytes(const ea_config *cfg)
+{
+    const size_t N = (size_t)cfg->L * cfg->L * cfg->L;
+    const size_t n_spin = (size_t)cfg->n_groups * cfg->n_temps * cfg->n_copies * N;
+    const size_t n_bond = (size_t)cfg->n_groups * 3 * N;
+    const size_t n_swap = (size_t)(cfg->n_temps > 1 ? cfg->n_temps - 1 : 0) * cfg->swap_len;
+    // resident arrays plus the import staging (spins and bonds once more)
+    return 2 * (n_spin + n_bond) * 4 + (size_t)cfg->n_temps * 12 + (n_swap ? n_swap : 1) * 4 +
+           (size_t)cfg->n_groups * cfg->n_copies * (kMaxTemps + cfg->n_temps * kLanes) * 4 + 4;
+}
+
+}  // namespace ea
 
 extern "C" {
 
@@ -141,6 +171,22 @@ int ea_build_tables(const double *beta, uint32_t n_temps, uint32_t n_sites, uint
 
 int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
 {
+    return ea::create_ctx(cfg, (cudaStream_t)stream, nullptr, out);
+}
+
+void ea_destroy(ea_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx, ctx->stream);
+}
+
+}  // extern "C"
+
+namespace ea {
+
+int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea_ctx **out)
+{
     if (!cfg || !out) return EA_EINVAL;
     *out = nullptr;
     const uint32_t L = cfg->L;
@@ -163,7 +209,8 @@ int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
     c->N = L * L * L;
     c->swap_len = cfg->swap_len;
     c->seed = cfg->seed;
-    c->stream = (cudaStream_t)stream;
+    c->stream = stream;
+    c->pool = pool;
     c->rk = ea::make_round_keys(cfg->seed);
 
     cudaError_t e = cudaGetDevice(&c->device);
@@ -184,24 +231,26 @@ int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
     const size_t n_bond = (size_t)c->G * 3 * c->N;
     const size_t n_swap = (size_t)(c->NT > 1 ? c->NT - 1 : 0) * c->swap_len;
     uint32_t *stage_s = nullptr, *stage_b = nullptr;
+    cudaStream_t st = c->stream;
     auto fail = [&](cudaError_t err) {
-        cudaFree(stage_s);
-        cudaFree(stage_b);
-        free_ctx(c);
+        if (pool) cudaStreamSynchronize(st);
+        ctx_free(c, stage_s, st);
+        ctx_free(c, stage_b, st);
+        free_ctx(c, st);
         return cuda_fail(err);
     };
-    if ((e = cudaMalloc(&c->d_spins, n_spin * 4)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->d_bonds, n_bond * 4)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->d_metro, (size_t)c->NT * 3 * 4)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->d_swapt, (n_swap ? n_swap : 1) * 4)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&c->d_masks, (size_t)c->G * c->C * ea::kMaxTemps * 4)) != cudaSuccess)
+    auto alloc = [&](auto **p, size_t bytes) { return ctx_alloc(c, reinterpret_cast<void **>(p), bytes, st); };
+    if ((e = alloc(&c->d_spins, n_spin * 4)) != cudaSuccess) return fail(e);
+    if ((e = alloc(&c->d_bonds, n_bond * 4)) != cudaSuccess) return fail(e);
+    if ((e = alloc(&c->d_metro, (size_t)c->NT * 3 * 4)) != cudaSuccess) return fail(e);
+    if ((e = alloc(&c->d_swapt, (n_swap ? n_swap : 1) * 4)) != cudaSuccess) return fail(e);
+    if ((e = alloc(&c->d_masks, (size_t)c->G * c->C * ea::kMaxTemps * 4)) != cudaSuccess)
         return fail(e);
-    if ((e = cudaMalloc(&c->d_energy, (size_t)c->G * c->C * c->NT * ea::kLanes * 4)) != cudaSuccess)
+    if ((e = alloc(&c->d_energy, (size_t)c->G * c->C * c->NT * ea::kLanes * 4)) != cudaSuccess)
         return fail(e);
-    if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&stage_s, n_spin * 4)) != cudaSuccess) return fail(e);
-    if ((e = cudaMalloc(&stage_b, n_bond * 4)) != cudaSuccess) return fail(e);
-    cudaStream_t st = c->stream;
+    if ((e = alloc(&c->d_err, sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = alloc(&stage_s, n_spin * 4)) != cudaSuccess) return fail(e);
+    if ((e = alloc(&stage_b, n_bond * 4)) != cudaSuccess) return fail(e);
     if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), st)) != cudaSuccess) return fail(e);
     if ((e = cudaMemcpyAsync(stage_s, cfg->spins0, n_spin * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return fail(e);
@@ -218,22 +267,28 @@ int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
     if ((e = ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)L, c->G, c->NT, c->C, st,
                                &c->launches)) != cudaSuccess)
         return fail(e);
-    // the staging buffers are freed once the copies above have run
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
-    cudaFree(stage_s);
-    cudaFree(stage_b);
+    if (pool) {
+        // stream-ordered: the staging buffers are released after the import
+        // kernels; the host waits for nothing (pageable sources are staged
+        // by the copy calls themselves)
+        ctx_free(c, stage_s, st);
+        ctx_free(c, stage_b, st);
+    } else {
+        // the staging buffers are freed once the copies above have run
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(e);
+        cudaFree(stage_s);
+        cudaFree(stage_b);
+    }
     *out = c;
     return EA_OK;
 }
 
-void ea_destroy(ea_ctx *ctx)
+void destroy_ctx(ea_ctx *c, cudaStream_t st)
 {
-    if (!ctx) return;
-    cudaStreamSynchronize(ctx->stream);
-    free_ctx(ctx);
+    free_ctx(c, st);
 }
 
-}  // extern "C"
+}  // namespace ea
 
 namespace {
 

@@ -15,8 +15,9 @@
 // completion without waiting, so the queue always progresses, whatever
 // number of CTAs is resident; waits are bounded all the same and raise an
 // error flag instead of hanging.  Initial tasks are ordered by the work left
-// in their unit (longest first).  The upload, the queue reset and the launch
-// are captured in a CUDA graph, replayed while the batch's shape is unchanged.
+// in their unit (longest first).  When a call repeats the previous call's
+// shape, its upload, queue reset and launch are captured in a CUDA graph that
+// is replayed while the shape stays the same.
 
 #include <algorithm>
 #include <cstring>
@@ -45,6 +46,19 @@ __global__ void k_batch_init(const BatchHdr *hdr, uint32_t *ready, BatchCtl *ctl
 // Thread counts of the two batch kernels: 384 (up to 168 registers a
 // thread, which the L % 8 == 0 unit kernel needs to run without spills) and 512.
 constexpr int kBatchSmallThreads = 384;
+
+// What a captured launch depends on besides the uploaded tables.
+struct BatchShape {
+    size_t ninst, ninit;
+    uint64_t total;
+    size_t smem;
+    int threads;
+    bool operator==(const BatchShape &o) const
+    {
+        return ninst == o.ninst && ninit == o.ninit && total == o.total && smem == o.smem &&
+               threads == o.threads;
+    }
+};
 
 // One way to run a member inside the batch kernel.
 struct BPlan {
@@ -161,12 +175,13 @@ struct ea_batch {
     ea::BatchTask *h_init;
     size_t cap_h_up, cap_h_init;
     uint32_t epoch;
-    // captured graph of the last shape
+    // captured graph (of g_shape) and the shape of the last call
     cudaGraphExec_t gexec;
     bool have_graph;
-    size_t g_ninst, g_ninit, g_total;
-    int g_grid, g_threads;
-    size_t g_smem;
+    ea::BatchShape g_shape, last_shape;
+    int g_grid;
+    size_t g_smem_set[2];                       // dynamic smem granted to the 384 / 512 kernels
+    bool joins_dirty;
     cudaEvent_t done;
     bool pending;
     uint64_t launches;
@@ -237,7 +252,7 @@ int wait_pending(ea_batch *b)
     e = cudaMemcpy(&ctl, b->d_ctl, sizeof(ctl), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_err(e);
     if (ctl.err) {
-        b->have_graph = false;           // re-capture: join counters are zeroed again
+        b->joins_dirty = true;           // an aborted call may leave join counts behind
         return EA_ETIMEOUT;
     }
     return EA_OK;
@@ -281,7 +296,6 @@ int ea_batch_add(ea_batch *b, ea_ctx *ctx)
     b->ctxs.push_back(ctx);
     b->cands.push_back(std::move(c));
     b->choice.push_back(-1);
-    b->have_graph = false;
     return EA_OK;
 }
 
@@ -291,7 +305,6 @@ int ea_batch_clear(ea_batch *b)
     b->ctxs.clear();
     b->cands.clear();
     b->choice.clear();
-    b->have_graph = false;
     return EA_OK;
 }
 
@@ -327,7 +340,6 @@ int ea_batch_set_plan(ea_batch *b, uint32_t member, int plan_index)
     if (!b || member >= b->ctxs.size()) return EA_EINVAL;
     if (plan_index < -1 || plan_index >= (int)b->cands[member].size()) return EA_EINVAL;
     b->choice[member] = plan_index;
-    b->have_graph = false;
     return EA_OK;
 }
 
@@ -336,7 +348,6 @@ int ea_batch_set_width(ea_batch *b, int threads)
     if (!b || (threads != 0 && threads != ea::kBatchSmallThreads && threads != ea::kBatchMaxThreads))
         return EA_EINVAL;
     b->force_threads = threads;
-    b->have_graph = false;
     return EA_OK;
 }
 
@@ -344,15 +355,18 @@ int ea_batch_set_segment(ea_batch *b, uint32_t site_words)
 {
     if (!b) return EA_EINVAL;
     b->seg_target = site_words;
-    b->have_graph = false;
     return EA_OK;
 }
 
-int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
+}  // extern "C"
+
+namespace {
+
+// One call: member i advances by n[i] sweeps with a swap pass after every
+// k[i]-th (members with n[i] == 0 are left out).
+int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
 {
     using namespace ea;
-    if (!b) return EA_EINVAL;
-    if (n_sweeps == 0 || b->ctxs.empty()) return EA_OK;
     // the pinned upload buffers are rewritten below: the previous call must be done
     int rc = wait_pending(b);
     if (rc != EA_OK) return rc;
@@ -361,7 +375,11 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
     for (int r : plan_of)
         if (r < 0) return EA_EUNSUPPORTED;
     const int threads = kernel_width(b, plan_of);
-    const size_t ninst = b->ctxs.size();
+    std::vector<size_t> members;
+    for (size_t i = 0; i < b->ctxs.size(); ++i)
+        if (n_of[i] > 0) members.push_back(i);
+    if (members.empty()) return EA_OK;
+    const size_t ninst = members.size();
     const size_t up_bytes = sizeof(BatchHdr) + ninst * sizeof(BatchInst);
     if ((e = grow_host(&b->h_up, &b->cap_h_up, up_bytes)) != cudaSuccess) return cuda_err(e);
     BatchHdr *hdr = reinterpret_cast<BatchHdr *>(b->h_up);
@@ -373,11 +391,13 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
     size_t smem = swap_scratch_bytes();
     const uint32_t seg_target = b->seg_target ? b->seg_target : (1u << 21);
     std::vector<uint64_t> passes(ninst);
-    for (size_t i = 0; i < ninst; ++i) {
+    for (size_t ii = 0; ii < ninst; ++ii) {
+        const size_t i = members[ii];
+        const uint32_t n_sweeps = n_of[i], swap_every = k_of[i];
         ea_ctx *c = b->ctxs[i];
         const BPlan &p = b->cands[i][(size_t)plan_of[i]];
         if (p.threads > threads) return EA_EUNSUPPORTED;
-        BatchInst &I = insts[i];
+        BatchInst &I = insts[ii];
         std::memset(&I, 0, sizeof(I));
         I.a.spins = c->d_spins;
         I.a.bonds = c->d_bonds;
@@ -401,7 +421,7 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
         I.units = c->G * c->C;
         I.swap_smem = p.swap_smem ? 1 : 0;
         I.j_smem = p.j_smem ? 1 : 0;
-        passes[i] = swaps_between(c->sweep, c->sweep + n_sweeps, swap_every);
+        passes[ii] = swaps_between(c->sweep, c->sweep + n_sweeps, swap_every);
         const uint64_t unit_work = (uint64_t)n_sweeps * c->N * c->NT;
         if (p.form == kBChunk) {
             I.nchunks = (c->NT + (uint32_t)p.p2 - 1) / (uint32_t)p.p2;
@@ -411,7 +431,7 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
             total += (uint64_t)I.units * I.pieces * I.nchunks;
             for (uint32_t u = 0; u < I.units; ++u)
                 for (uint32_t j = 0; j < I.nchunks; ++j) {
-                    init.push_back({(uint32_t)i, u, 0u, j});
+                    init.push_back({(uint32_t)ii, u, 0u, j});
                     work.push_back(unit_work);
                 }
         } else {
@@ -425,7 +445,7 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
             const uint32_t tasks = (I.units + m - 1) / m;
             total += (uint64_t)tasks * I.pieces;
             for (uint32_t u = 0; u < I.units; u += m) {
-                init.push_back({(uint32_t)i, u, 0u, 0u});
+                init.push_back({(uint32_t)ii, u, 0u, 0u});
                 work.push_back(unit_work);
             }
         }
@@ -445,9 +465,9 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
     hdr->ninst = (uint32_t)ninst;
 
     const void *kern = threads == kBatchSmallThreads ? batch_kernel_384() : batch_kernel_512();
-    const bool same_shape = b->have_graph && b->g_ninst == ninst && b->g_ninit == init.size() &&
-                            b->g_total == total && b->g_smem == smem && b->g_threads == threads;
-    if (!same_shape) {
+    const BatchShape shape{ninst, init.size(), total, smem, threads};
+    const bool replay = b->have_graph && b->g_shape == shape;
+    if (!replay) {
         if (b->have_graph) {
             cudaGraphExecDestroy(b->gexec);
             b->have_graph = false;
@@ -459,55 +479,66 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
             cudaFree(b->d_ready);
             b->d_ready = nullptr;
             if ((e = cudaMalloc(&b->d_ready, b->cap_tasks * sizeof(uint32_t))) != cudaSuccess) return cuda_err(e);
-            if ((e = cudaMemset(b->d_ready, 0, b->cap_tasks * sizeof(uint32_t))) != cudaSuccess) return cuda_err(e);
+            if ((e = cudaMemsetAsync(b->d_ready, 0, b->cap_tasks * sizeof(uint32_t), b->stream)) != cudaSuccess)
+                return cuda_err(e);
         }
         if (b->cap_join < (size_t)njoin || !b->d_join) {
             cudaFree(b->d_join);
             b->d_join = nullptr;
-            b->cap_join = njoin ? njoin : 1;
+            b->cap_join = njoin > 64 ? njoin : 64;
             if ((e = cudaMalloc(&b->d_join, b->cap_join * sizeof(uint32_t))) != cudaSuccess) return cuda_err(e);
+            b->joins_dirty = true;
         }
-        // joins are reset by the closing chunk of each interval; zero them once here
-        if ((e = cudaMemset(b->d_join, 0, b->cap_join * sizeof(uint32_t))) != cudaSuccess) return cuda_err(e);
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_err(e);
+        // joins are reset by the closing chunk of each interval; zero them
+        // after allocation or an aborted call
+        if (b->joins_dirty) {
+            if ((e = cudaMemsetAsync(b->d_join, 0, b->cap_join * sizeof(uint32_t), b->stream)) != cudaSuccess)
+                return cuda_err(e);
+            b->joins_dirty = false;
+        }
+        if (b->g_smem_set[threads == kBatchSmallThreads ? 0 : 1] < smem) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_err(e);
+            b->g_smem_set[threads == kBatchSmallThreads ? 0 : 1] = smem;
+        }
         int per_sm = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
         if (e != cudaSuccess) return cuda_err(e);
         if (per_sm < 1) return EA_EUNSUPPORTED;
         b->g_grid = per_sm * sms;
-        b->g_ninst = ninst;
-        b->g_ninit = init.size();
-        b->g_total = total;
-        b->g_smem = smem;
-        b->g_threads = threads;
-        // capture: upload, publish the initial tasks, the persistent launch
-        cudaStream_t cap = nullptr;
-        cudaGraph_t graph = nullptr;
-        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_up, b->h_up, up_bytes, cudaMemcpyHostToDevice, cap);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_tasks, b->h_init, init.size() * sizeof(BatchTask),
-                                cudaMemcpyHostToDevice, cap);
-        const BatchHdr *d_hdr = reinterpret_cast<const BatchHdr *>(b->d_up);
-        const BatchInst *d_insts = reinterpret_cast<const BatchInst *>(b->d_up + sizeof(BatchHdr));
-        if (e == cudaSuccess) {
-            k_batch_init<<<1, 1024, 0, cap>>>(d_hdr, b->d_ready, b->d_ctl);
-            e = cudaGetLastError();
+    }
+    const BatchHdr *d_hdr = reinterpret_cast<const BatchHdr *>(b->d_up);
+    const BatchInst *d_insts = reinterpret_cast<const BatchInst *>(b->d_up + sizeof(BatchHdr));
+    // upload, publish the initial tasks, the persistent launch
+    auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+        cudaError_t x = cudaMemcpyAsync(b->d_up, b->h_up, up_bytes, cudaMemcpyHostToDevice, st);
+        if (x == cudaSuccess)
+            x = cudaMemcpyAsync(b->d_tasks, b->h_init, init.size() * sizeof(BatchTask),
+                                cudaMemcpyHostToDevice, st);
+        if (x == cudaSuccess) {
+            k_batch_init<<<1, 1024, 0, st>>>(d_hdr, b->d_ready, b->d_ctl);
+            x = cudaGetLastError();
         }
-        if (e == cudaSuccess) {
+        if (x == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(b->g_grid);
             cfg.blockDim = dim3(threads);
             cfg.dynamicSmemBytes = smem;
-            cfg.stream = cap;
+            cfg.stream = st;
             void *args[] = {(void *)&d_hdr, (void *)&d_insts, (void *)&b->d_tasks, (void *)&b->d_ready,
                             (void *)&b->d_join, (void *)&b->d_ctl};
-            e = cudaLaunchKernelExC(&cfg, kern, args);
+            x = cudaLaunchKernelExC(&cfg, kern, args);
         }
+        return x;
+    };
+    if (!replay && b->last_shape == shape) {
+        // the same shape twice in a row: capture it and replay from now on
+        cudaStream_t cap = nullptr;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = enqueue(cap);
         const cudaError_t e2 = cap ? cudaStreamEndCapture(cap, &graph) : cudaSuccess;
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, graph, 0);
@@ -515,18 +546,41 @@ int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
         if (cap) cudaStreamDestroy(cap);
         if (e != cudaSuccess) return cuda_err(e);
         b->have_graph = true;
+        b->g_shape = shape;
     }
-    e = cudaGraphLaunch(b->gexec, b->stream);
+    if (b->have_graph && b->g_shape == shape) e = cudaGraphLaunch(b->gexec, b->stream);
+    else e = enqueue(b->stream);
+    b->last_shape = shape;
     if (e == cudaSuccess) e = cudaEventRecord(b->done, b->stream);
     if (e != cudaSuccess) return cuda_err(e);
     b->pending = true;
     b->launches += 2;
-    for (size_t i = 0; i < ninst; ++i) {
-        b->ctxs[i]->sweep += n_sweeps;
-        b->ctxs[i]->pass += passes[i];
-        b->ctxs[i]->launches += 1;
+    for (size_t ii = 0; ii < ninst; ++ii) {
+        ea_ctx *c = b->ctxs[members[ii]];
+        c->sweep += n_of[members[ii]];
+        c->pass += passes[ii];
+        c->launches += 1;
     }
     return EA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ea_batch_sweep(ea_batch *b, uint32_t n_sweeps, uint32_t swap_every)
+{
+    if (!b) return EA_EINVAL;
+    if (n_sweeps == 0 || b->ctxs.empty()) return EA_OK;
+    const std::vector<uint32_t> n(b->ctxs.size(), n_sweeps), k(b->ctxs.size(), swap_every);
+    return batch_sweep_impl(b, n.data(), k.data());
+}
+
+int ea_batch_sweep_each(ea_batch *b, const uint32_t *n_sweeps, const uint32_t *swap_every)
+{
+    if (!b || (!b->ctxs.empty() && (!n_sweeps || !swap_every))) return EA_EINVAL;
+    if (b->ctxs.empty()) return EA_OK;
+    return batch_sweep_impl(b, n_sweeps, swap_every);
 }
 
 int ea_batch_sync(ea_batch *b)
@@ -573,7 +627,10 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
     };
     // one probe: a warm call (captures the graph), then a timed one
     auto probe = [&](float *ms) -> int {
+        // two warm calls: the second captures the launch, the timed one replays it
         int r = ea_batch_sweep(b, probe_sweeps, swap_every);
+        if (r == EA_OK) r = restore();
+        if (r == EA_OK) r = ea_batch_sweep(b, probe_sweeps, swap_every);
         if (r == EA_OK) r = restore();
         if (r == EA_OK && cudaEventRecord(t0, b->stream) != cudaSuccess) r = EA_ECUDA;
         if (r == EA_OK) r = ea_batch_sweep(b, probe_sweeps, swap_every);
@@ -601,7 +658,6 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
         }
         if (!ok) continue;
         b->choice = cur;
-        b->have_graph = false;
         float t = 0.f;
         if ((rc = probe(&t)) != EA_OK) break;
         for (size_t i = 0; i < n && rc == EA_OK; ++i)
@@ -621,7 +677,6 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
     }
     b->choice = rc == EA_OK ? best_choice : choice0;
     b->force_threads = rc == EA_OK ? best_width : force0;
-    b->have_graph = false;
     const int r2 = restore();
     cudaStreamSynchronize(b->stream);
     for (size_t i = 0; i < n; ++i) {

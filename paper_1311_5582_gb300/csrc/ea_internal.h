@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/ea.h"
+
 namespace ea {
 
 constexpr int kLanes = 32;
@@ -112,6 +114,7 @@ struct ea_ctx {
     uint32_t L, G, NT, C, N, swap_len;
     uint64_t seed;
     cudaStream_t stream;
+    cudaMemPool_t pool;            // NULL: plain allocations; else stream-ordered from this pool
     int device;
     size_t smem_optin;
     uint32_t *d_spins, *d_bonds, *d_metro, *d_swapt, *d_masks;
@@ -125,3 +128,13 @@ struct ea_ctx {
     ea::RoundKeys rk;
 };
 
+namespace ea {
+// Creates a context (ea_create with an optional memory pool: with a pool every
+// allocation is stream-ordered on `stream` and nothing waits on the host).
+int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea_ctx **out);
+// Releases a context's device memory (stream-ordered on `st` for pooled
+// contexts) and the context itself.  The caller has ordered its last use.
+void destroy_ctx(ea_ctx *c, cudaStream_t st);
+// Device bytes create_ctx allocates for cfg, the import staging included.
+size_t ctx_device_bytes(const ea_config *cfg);
+}  // namespace ea

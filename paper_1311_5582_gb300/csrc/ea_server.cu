@@ -1,0 +1,483 @@
+// Serving loop: admits simulation requests by device memory, keeps their
+// state resident on the device, and advances every resident request together
+// in rounds of one persistent batched launch (continuous batching).
+//
+// One worker thread owns the GPU work.  Each round it
+//   1. launches one batched call (ea_batch_sweep_each) in which every resident
+//      request advances by min(q, sweeps left) sweeps, q sized so that the
+//      round lasts about round_ms at the measured rate;
+//   2. while that runs, admits queued requests in arrival order as long as
+//      their device bytes fit the budget (contexts are created on a second
+//      stream from a stream-ordered memory pool, so nothing waits for the
+//      round); they join the next round;
+//   3. waits for the round, then writes the outputs of finished requests to
+//      their host buffers and releases their memory.
+// Every request's trajectory is the one ea_sweep would give it alone: the
+// batch keeps each member's own counters, tables and swap schedule.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/ea.h"
+#include "ea_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_between(Clock::time_point a, Clock::time_point b)
+{
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+struct Request {
+    uint64_t ticket = 0;
+    ea_config cfg{};                              // points into the copies below
+    std::vector<uint32_t> bonds, spins0, metro, swapt;
+    uint32_t n_sweeps = 0, swap_every = 0;
+    uint32_t *spins_out = nullptr;
+    int32_t *energies_out = nullptr;
+    size_t bytes = 0;                             // device bytes while resident
+    Clock::time_point t_submit;
+    ea_ctx *ctx = nullptr;
+    uint32_t left = 0;                            // sweeps still to run
+    uint64_t words = 0;                           // site-words of one sweep (N * NT * C * G)
+};
+
+}  // namespace
+
+struct ea_server {
+    int device = 0;
+    size_t budget = 0, used = 0, peak = 0;
+    uint32_t max_live = 256;
+    double round_ms = 20.0;
+    cudaStream_t compute = nullptr, admit = nullptr;
+    cudaEvent_t admitted = nullptr;
+    cudaMemPool_t pool = nullptr;
+    ea_batch *batch = nullptr;
+    std::thread worker;
+    Clock::time_point t0;
+
+    std::mutex mu;                                // guards everything below up to `live`
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::deque<std::unique_ptr<Request>> queue;   // submitted, not yet admitted
+    std::unordered_set<uint64_t> open;            // submitted, not yet finished
+    std::unordered_map<uint64_t, int> finished;   // finished, not yet polled: status
+    uint64_t next_ticket = 1;
+    std::vector<double> lat_ms;
+    uint64_t submitted = 0, completed = 0, failed = 0, rounds = 0;
+    double flips = 0.0, busy_s = 0.0;
+    double first_submit_s = -1.0, last_done_s = 0.0;
+    size_t n_live = 0;
+
+    std::vector<std::unique_ptr<Request>> live;   // worker thread only
+    double rate = 2.0e8;                          // site-words per ms (updated each round)
+};
+
+namespace {
+
+// Records the end of a request (status EA_OK or an error); takes the lock.
+void finish(ea_server *s, Request &r, int status)
+{
+    const Clock::time_point now = Clock::now();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->open.erase(r.ticket);
+    s->finished[r.ticket] = status;
+    if (status == EA_OK) {
+        s->completed += 1;
+        s->lat_ms.push_back(ms_between(r.t_submit, now));
+        s->flips += (double)r.words * 32.0 * r.n_sweeps;
+        s->last_done_s = ms_between(s->t0, now) * 1e-3;
+    } else {
+        s->failed += 1;
+    }
+    s->cv_done.notify_all();
+}
+
+// Admits queued requests, in arrival order, while they fit the memory budget
+// and the resident-request limit.  Contexts are created on the admission
+// stream; the compute stream waits for them before its next launch.
+void admit(ea_server *s)
+{
+    bool any = false;
+    for (;;) {
+        std::unique_ptr<Request> r;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->queue.empty() || s->live.size() >= s->max_live) break;
+            Request &h = *s->queue.front();
+            if (s->used + h.bytes > s->budget) {
+                if (!s->live.empty() || h.bytes <= s->budget) break;   // waits for memory
+            }
+            r = std::move(s->queue.front());
+            s->queue.pop_front();
+        }
+        if (r->bytes > s->budget) {            // can never fit
+            finish(s, *r, EA_ENOMEM);
+            continue;
+        }
+        ea_ctx *ctx = nullptr;
+        const int rc = ea::create_ctx(&r->cfg, s->admit, s->pool, &ctx);
+        if (rc == EA_ENOMEM && !s->live.empty()) {
+            // the budget was optimistic: retry once resident requests finish
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->queue.push_front(std::move(r));
+            break;
+        }
+        if (rc != EA_OK) {
+            finish(s, *r, rc);
+            continue;
+        }
+        ctx->stream = s->compute;              // all later work of this context
+        r->ctx = ctx;
+        r->left = r->n_sweeps;
+        // the host copies of the inputs are no longer needed
+        std::vector<uint32_t>().swap(r->bonds);
+        std::vector<uint32_t>().swap(r->spins0);
+        s->used += r->bytes;
+        s->peak = std::max(s->peak, s->used);
+        s->live.push_back(std::move(r));
+        any = true;
+    }
+    if (any) {
+        cudaEventRecord(s->admitted, s->admit);
+        cudaStreamWaitEvent(s->compute, s->admitted, 0);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->n_live = s->live.size();
+}
+
+// Writes the outputs of the finished requests among live[0, n) and releases them.
+void complete(ea_server *s, std::vector<size_t> &done)
+{
+    if (done.empty()) return;
+    std::vector<int> status(done.size(), EA_OK);
+    std::vector<std::pair<uint32_t *, int32_t *>> scratch(done.size(), {nullptr, nullptr});
+    for (size_t j = 0; j < done.size(); ++j) {
+        Request &r = *s->live[done[j]];
+        ea_ctx *c = r.ctx;
+        const size_t nsp = (size_t)c->G * c->NT * c->C * c->N, nen = (size_t)c->G * c->NT * c->C * ea::kLanes;
+        cudaError_t e = cudaSuccess;
+        int rc = EA_OK;
+        if (r.energies_out) {
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&scratch[j].second), nen * 4, s->pool, s->compute);
+            if (e == cudaSuccess) rc = ea_measure(c, scratch[j].second, nullptr, nullptr);
+            if (e == cudaSuccess && rc == EA_OK)
+                e = cudaMemcpyAsync(r.energies_out, scratch[j].second, nen * 4, cudaMemcpyDeviceToHost, s->compute);
+        }
+        if (e == cudaSuccess && rc == EA_OK && r.spins_out) {
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&scratch[j].first), nsp * 4, s->pool, s->compute);
+            if (e == cudaSuccess) rc = ea_read_spins(c, scratch[j].first);
+            if (e == cudaSuccess && rc == EA_OK)
+                e = cudaMemcpyAsync(r.spins_out, scratch[j].first, nsp * 4, cudaMemcpyDeviceToHost, s->compute);
+        }
+        status[j] = e != cudaSuccess ? (e == cudaErrorMemoryAllocation ? EA_ENOMEM : EA_ECUDA) : rc;
+    }
+    const cudaError_t es = cudaStreamSynchronize(s->compute);
+    for (size_t j = 0; j < done.size(); ++j) {
+        Request &r = *s->live[done[j]];
+        if (scratch[j].first) cudaFreeAsync(scratch[j].first, s->compute);
+        if (scratch[j].second) cudaFreeAsync(scratch[j].second, s->compute);
+        ea::destroy_ctx(r.ctx, s->compute);
+        r.ctx = nullptr;
+        s->used -= r.bytes;
+        finish(s, r, es != cudaSuccess ? EA_ECUDA : status[j]);
+    }
+    // drop the finished entries (indices ascending)
+    for (size_t j = done.size(); j-- > 0;) s->live.erase(s->live.begin() + (std::ptrdiff_t)done[j]);
+    done.clear();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->n_live = s->live.size();
+}
+
+// One round over the resident requests live[0, n).
+void run_round(ea_server *s)
+{
+    const size_t n = s->live.size();
+    std::vector<size_t> done;
+    // requests with nothing to run (zero sweeps) finish at once
+    for (size_t i = 0; i < n; ++i)
+        if (s->live[i]->left == 0) done.push_back(i);
+    if (!done.empty()) {
+        complete(s, done);
+        return;
+    }
+    double words = 0.0;
+    for (size_t i = 0; i < n; ++i) words += (double)s->live[i]->words;
+    double qd = s->round_ms * s->rate / (words > 0 ? words : 1.0);
+    const uint32_t q = (uint32_t)std::max(1.0, std::min(qd, 1048576.0));
+    ea_batch_clear(s->batch);
+    std::vector<uint32_t> nsw(n), kev(n);
+    int rc = EA_OK;
+    for (size_t i = 0; i < n && rc == EA_OK; ++i) {
+        Request &r = *s->live[i];
+        rc = ea_batch_add(s->batch, r.ctx);
+        nsw[i] = std::min(q, r.left);
+        kev[i] = r.swap_every;
+    }
+    double work = 0.0;
+    for (size_t i = 0; i < n; ++i) work += (double)nsw[i] * (double)s->live[i]->words;
+    const Clock::time_point t_start = Clock::now();
+    if (rc == EA_OK) rc = ea_batch_sweep_each(s->batch, nsw.data(), kev.data());
+    admit(s);                                    // overlaps the round
+    if (rc == EA_OK) rc = ea_batch_sync(s->batch);
+    const double dt = ms_between(t_start, Clock::now());
+    if (rc == EA_OK && dt > 0.5) s->rate = 0.5 * s->rate + 0.5 * (work / dt);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->rounds += 1;
+    }
+    if (rc != EA_OK) {
+        // the round failed: every request in it fails with the round's status
+        for (size_t i = 0; i < n; ++i) {
+            Request &r = *s->live[i];
+            ea::destroy_ctx(r.ctx, s->compute);
+            r.ctx = nullptr;
+            s->used -= r.bytes;
+            finish(s, r, rc);
+        }
+        s->live.erase(s->live.begin(), s->live.begin() + (std::ptrdiff_t)n);
+        cudaStreamSynchronize(s->compute);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->n_live = s->live.size();
+        return;
+    }
+    for (size_t i = 0; i < n; ++i) {
+        Request &r = *s->live[i];
+        r.left -= nsw[i];
+        if (r.left == 0) done.push_back(i);
+    }
+    complete(s, done);
+}
+
+void worker_main(ea_server *s)
+{
+    cudaSetDevice(s->device);
+    Clock::time_point busy_from;
+    bool busy = false;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            if (s->live.empty())
+                s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            if (s->stop) break;
+        }
+        admit(s);
+        if (s->live.empty()) continue;
+        if (!busy) {
+            busy = true;
+            busy_from = Clock::now();
+        }
+        run_round(s);
+        if (s->live.empty() && busy) {
+            busy = false;
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->busy_s += ms_between(busy_from, Clock::now()) * 1e-3;
+        }
+    }
+    // shutting down: drop what is left
+    cudaStreamSynchronize(s->compute);
+    cudaStreamSynchronize(s->admit);
+    for (auto &r : s->live) {
+        ea::destroy_ctx(r->ctx, s->compute);
+        r->ctx = nullptr;
+    }
+    s->live.clear();
+    cudaStreamSynchronize(s->compute);
+}
+
+// Up-front checks of a request (the tables are validated at admission).
+int check_request(const ea_config *cfg)
+{
+    if (cfg->L < 4 || (cfg->L & 1u)) return EA_EINVAL;
+    if (!ea::supported_L((int)cfg->L)) return EA_EUNSUPPORTED;
+    if (cfg->n_groups == 0 || cfg->n_temps == 0 || cfg->n_temps > (uint32_t)ea::kMaxTemps) return EA_EINVAL;
+    if (cfg->n_copies < 1 || cfg->n_copies > 2) return EA_EINVAL;
+    if (!cfg->bonds || !cfg->spins0 || !cfg->metro) return EA_EINVAL;
+    if (cfg->n_temps > 1 && cfg->swap_len > 0 && !cfg->swapt) return EA_EINVAL;
+    return EA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ea_server_create(const ea_server_opts *opts, ea_server **out)
+{
+    if (!out) return EA_EINVAL;
+    *out = nullptr;
+    ea_server *s = new (std::nothrow) ea_server();
+    if (!s) return EA_ENOMEM;
+    s->t0 = Clock::now();
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    const size_t cap = free_b / 10 * 9;
+    s->budget = (opts && opts->mem_budget) ? std::min((size_t)opts->mem_budget, cap) : cap / 10 * 9;
+    if (opts && opts->max_live) s->max_live = opts->max_live;
+    if (opts && opts->round_ms) s->round_ms = opts->round_ms;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->admitted, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = s->device;
+        e = cudaMemPoolCreate(&s->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        // keep freed blocks for reuse up to the budget instead of returning them
+        uint64_t thr = s->budget;
+        e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    int rc = e == cudaSuccess ? EA_OK : EA_ECUDA;
+    if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch);
+    if (rc != EA_OK) {
+        if (s->batch) ea_batch_destroy(s->batch);
+        if (s->pool) cudaMemPoolDestroy(s->pool);
+        if (s->admitted) cudaEventDestroy(s->admitted);
+        if (s->admit) cudaStreamDestroy(s->admit);
+        if (s->compute) cudaStreamDestroy(s->compute);
+        delete s;
+        return rc;
+    }
+    try {
+        s->worker = std::thread(worker_main, s);
+    } catch (...) {
+        ea_batch_destroy(s->batch);
+        cudaMemPoolDestroy(s->pool);
+        cudaEventDestroy(s->admitted);
+        cudaStreamDestroy(s->admit);
+        cudaStreamDestroy(s->compute);
+        delete s;
+        return EA_ENOMEM;
+    }
+    *out = s;
+    return EA_OK;
+}
+
+int ea_submit(ea_server *s, const ea_config *cfg, const ea_request *req, uint64_t *ticket)
+{
+    if (!s || !cfg || !req || !ticket) return EA_EINVAL;
+    const int chk = check_request(cfg);
+    if (chk != EA_OK) return chk;
+    auto r = std::unique_ptr<Request>(new (std::nothrow) Request());
+    if (!r) return EA_ENOMEM;
+    const size_t N = (size_t)cfg->L * cfg->L * cfg->L;
+    const size_t nsp = (size_t)cfg->n_groups * cfg->n_temps * cfg->n_copies * N;
+    const size_t nbo = (size_t)cfg->n_groups * 3 * N;
+    const size_t nsw = (size_t)(cfg->n_temps > 1 ? cfg->n_temps - 1 : 0) * cfg->swap_len;
+    try {
+        r->bonds.assign(cfg->bonds, cfg->bonds + nbo);
+        r->spins0.assign(cfg->spins0, cfg->spins0 + nsp);
+        r->metro.assign(cfg->metro, cfg->metro + (size_t)cfg->n_temps * 3);
+        if (nsw) r->swapt.assign(cfg->swapt, cfg->swapt + nsw);
+    } catch (...) {
+        return EA_ENOMEM;
+    }
+    r->cfg = *cfg;
+    r->cfg.bonds = r->bonds.data();
+    r->cfg.spins0 = r->spins0.data();
+    r->cfg.metro = r->metro.data();
+    r->cfg.swapt = nsw ? r->swapt.data() : nullptr;
+    r->n_sweeps = req->n_sweeps;
+    r->swap_every = req->swap_every;
+    r->spins_out = req->spins_out;
+    r->energies_out = req->energies_out;
+    r->words = (uint64_t)nsp;
+    // resident state plus the output scratch taken at completion
+    r->bytes = ea::ctx_device_bytes(cfg) + (r->spins_out ? nsp * 4 : 0) +
+               (r->energies_out ? (size_t)cfg->n_groups * cfg->n_temps * cfg->n_copies * ea::kLanes * 4 : 0);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return EA_ESTATE;
+        r->ticket = s->next_ticket++;
+        *ticket = r->ticket;
+        s->open.insert(r->ticket);
+        s->submitted += 1;
+        if (s->first_submit_s < 0) s->first_submit_s = ms_between(s->t0, r->t_submit) * 1e-3;
+        s->queue.push_back(std::move(r));
+    }
+    s->cv_work.notify_one();
+    return EA_OK;
+}
+
+int ea_poll(ea_server *s, uint64_t ticket, uint32_t timeout_us)
+{
+    if (!s) return EA_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto ready = [&] { return s->finished.count(ticket) != 0; };
+    if (!ready()) {
+        if (!s->open.count(ticket)) return EA_EINVAL;     // unknown or already collected
+        if (timeout_us) s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+        if (!ready()) return EA_PENDING;
+    }
+    const int st = s->finished[ticket];
+    s->finished.erase(ticket);
+    return st;
+}
+
+int ea_server_stats_get(ea_server *s, ea_server_stats *out)
+{
+    if (!s || !out) return EA_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->failed = s->failed;
+    out->queued = s->queue.size();
+    out->live = s->n_live;
+    out->rounds = s->rounds;
+    out->flip_attempts = s->flips;
+    out->busy_s = s->busy_s;
+    out->span_s = s->first_submit_s >= 0 ? s->last_done_s - s->first_submit_s : 0.0;
+    out->mem_budget = s->budget;
+    out->peak_bytes = s->peak;
+    if (!s->lat_ms.empty()) {
+        std::vector<double> v = s->lat_ms;
+        std::sort(v.begin(), v.end());
+        auto rank = [&](double q) {
+            size_t k = (size_t)std::ceil(q * (double)v.size());
+            return v[k > 0 ? k - 1 : 0];
+        };
+        double sum = 0.0;
+        for (double x : v) sum += x;
+        out->p50_ms = rank(0.50);
+        out->p99_ms = rank(0.99);
+        out->mean_ms = sum / (double)v.size();
+        out->max_ms = v.back();
+    }
+    return EA_OK;
+}
+
+void ea_server_destroy(ea_server *s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    ea_batch_destroy(s->batch);
+    cudaMemPoolDestroy(s->pool);
+    cudaEventDestroy(s->admitted);
+    cudaStreamDestroy(s->admit);
+    cudaStreamDestroy(s->compute);
+    delete s;
+}
+
+}  // extern "C"
