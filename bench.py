@@ -3,10 +3,14 @@
 
 Workload (one step): the L=8 ensemble -- 512 sites, 2048 realizations (64 words
 per site), 24 temperatures geometric in [0.9, 2.0] x 2 copies -- run for 10^5
-checkerboard sweeps with a replica-exchange pass after every sweep and the
-energy / overlap-q histogram measurement over the second half.  Metric: ps per
-spin-flip attempt (Eq. tsf of the paper, copies counted):
+checkerboard sweeps with a replica-exchange pass after every sweep (energies of
+every slot computed every sweep for it).  Metric: ps per spin-flip attempt
+(Eq. tsf of the paper, copies counted), with measurements discarded as in the
+paper's own figure (Sec. 3):
     t = T / (sweeps * N * NT * C * realizations).
+The same workload with the energy / overlap-q histogram measurement after every
+sweep of the second half is reported beside it ("with_measurement"), and at
+N = 1 the batched mixed-size form and the served trace ("batched", "served").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch under torch.distributed.run; each rank runs its own ensemble
@@ -42,7 +46,8 @@ ALU_LANES_PER_CLK_PER_SM = 64     # integer ALU pipe (LOP3/IADD3/ISETP/SEL) of o
 
 WORKLOADS = {
     # name: (instance, sweeps per step, swap every, measurement over the second half)
-    "scale": (W.SCALE, W.SCALE_SWEEPS, W.SCALE_SWAP_EVERY, True),
+    "scale": (W.SCALE, W.SCALE_SWEEPS, W.SCALE_SWAP_EVERY, False),
+    "scale_measured": (W.SCALE, W.SCALE_SWEEPS, W.SCALE_SWAP_EVERY, True),
     "small": (W.SMALL, W.SMALL_SWEEPS, W.SMALL_SWAP_EVERY, False),
     "large16": (W.LARGE16, W.LARGE_SWEEPS, W.LARGE_SWAP_EVERY, False),
     "large32": (W.LARGE32, W.LARGE_SWEEPS, W.LARGE_SWAP_EVERY, False),
@@ -65,16 +70,27 @@ def workload(name="scale", sweeps=None):
     }
 
 
-def kernel_source_hash() -> str:
-    """SHA-256 over the CUDA sources: a traffic figure measured on other sources is stale."""
+# Sources each workload's dominant kernel is compiled from (its traffic record
+# goes stale when one of them changes).
+KERNEL_SOURCES = {
+    "scale": ["ea_unit_fast.cu", "ea_fast.cuh", "ea_device.cuh", "ea_internal.h"],
+    "scale_measured": ["ea_unit_fast.cu", "ea_fast.cuh", "ea_device.cuh", "ea_internal.h"],
+    "small": ["ea_kernels.cu", "ea_bodies.cuh", "ea_device.cuh", "ea_internal.h"],
+    "large16": ["ea_kernels.cu", "ea_bodies.cuh", "ea_device.cuh", "ea_internal.h"],
+    "large32": ["ea_kernels.cu", "ea_bodies.cuh", "ea_device.cuh", "ea_internal.h"],
+}
+
+
+def kernel_source_hash(workload_key: str = "scale") -> str:
+    """SHA-256 over the sources of the workload's dominant kernel: a traffic
+    figure measured on other sources is stale."""
     import hashlib
     d = os.path.join(ROOT, "paper_1311_5582_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in KERNEL_SOURCES[workload_key]:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -83,7 +99,7 @@ def recorded_traffic(workload_key: str):
     (profiles/*.md line 'traffic-record: <workload> <bytes per launch> <source hash>'),
     or None when absent or taken on different kernel sources."""
     import glob
-    want = kernel_source_hash()
+    want = kernel_source_hash(workload_key)
     for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
         with open(path) as f:
             for line in f:
@@ -112,6 +128,19 @@ def aggregate(times_s, flips_per_rank):
     """Job value: slowest rank's time over all ranks' flips (ps per flip)."""
     t = max(times_s)
     return t / (flips_per_rank * len(times_s)) * 1e12, t
+
+
+def reduce_max(x: float, world: int) -> float:
+    """Largest value of x over the ranks (the only cross-rank traffic of the
+    bench besides barriers): a CUDA tensor under NCCL, a CPU one under gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -204,6 +233,122 @@ def cpu_baseline(wl, budget_s=15.0, threads=None):
                       f"with the same swap and measurement schedule, {t:.1f} s"}
 
 
+def _flips(inst, sweeps):
+    return sweeps * inst.N * inst.NT * inst.C * 32 * inst.G
+
+
+def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVERY):
+    """The mixed ensemble (L in {4..16}, uneven sizes and ladders) advanced by one
+    persistent batched launch, against the same instances launched one after
+    another; both sides autotuned, both timed from warm state with L2 flushed."""
+    insts = W.batch_instances()
+    ens = []
+    for inst in insts:
+        inp = W.draw_inputs(inst)
+        metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+        ens.append(ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"],
+                               inp["spins"], metro, swapt))
+    flips = sum(_flips(i, sweeps) for i in insts)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def timed(fn):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    for e in ens:
+        e.autotune(probe_sweeps=200, swap_every=swap_every)
+
+    def plain():
+        for e in ens:
+            e.sweep(sweeps, swap_every)
+
+    l0 = sum(e.launches for e in ens)
+    timed(plain)                                 # warm
+    l1 = sum(e.launches for e in ens)
+    t_plain = timed(plain)
+    plain_launches = sum(e.launches for e in ens) - l1
+    batch = ea.Batch(ens)
+    batch.autotune(probe_sweeps=200, swap_every=swap_every)
+
+    def batched():
+        batch.sweep(sweeps, swap_every)
+        batch.sync()
+
+    timed(batched)                               # warm
+    b0 = batch.launches
+    t_batch = timed(batched)
+    del l0
+    plans = [batch.plans(i)[batch.plan(i)] for i in range(len(insts))]
+    return {
+        "workload": "EA +-J batched mix: " + ", ".join(
+            f"L={i.L} {32 * i.G} realizations x {i.NT} temps" for i in insts)
+            + f" (C=2, ladders geometric in [0.8,2.0]), {sweeps} sweeps, swap every {swap_every}",
+        "value": t_batch / flips * 1e12, "unit": UNIT, "plain_value": t_plain / flips * 1e12,
+        "speedup_vs_plain": t_plain / t_batch, "gpu_launches": batch.launches - b0,
+        "plain_gpu_launches": plain_launches, "flips": flips,
+        "plans": [f"{p['form']} t{p['threads']} g{p['group_threads']} u{p['units_per_cta']}"
+                  for p in plans],
+    }
+
+
+def bench_served(ea, n_requests=32, round_ms=20):
+    """Poisson-arriving requests (200/s) replayed in real time through the server,
+    against serving them one at a time with plain launches (arrival order); the
+    results of the two are compared bit for bit."""
+    trace = W.served_trace(n_requests)
+    data = []
+    for r in trace:
+        inst = r["inst"]
+        inp = W.draw_inputs(inst)
+        metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+        data.append((inst, inp, metro, swapt))
+    flips = sum(_flips(d[0], r["sweeps"]) for d, r in zip(data, trace))
+    srv = ea.Server(round_ms=round_ms)
+    start = time.monotonic()
+    tickets = []
+    for r, (inst, inp, metro, swapt) in zip(trace, data):
+        wait = r["arrival_s"] - (time.monotonic() - start)
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append(srv.submit(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"],
+                                  inp["spins"], metro, swapt, r["sweeps"], r["swap_every"]))
+    outs = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    lat, same = [], True
+    start = time.monotonic()
+    for r, (inst, inp, metro, swapt), o in zip(trace, data, outs):
+        wait = r["arrival_s"] - (time.monotonic() - start)
+        if wait > 0:
+            time.sleep(wait)
+        e = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
+                        metro, swapt)
+        e.sweep(r["sweeps"], r["swap_every"])
+        sp = e.read_spins_host()
+        en = e.measure()[0].cpu().numpy()
+        lat.append((time.monotonic() - start - r["arrival_s"]) * 1e3)
+        same = same and np.array_equal(sp, o["spins"]) and np.array_equal(en, o["energies"])
+        e.close()
+    span = time.monotonic() - start - trace[0]["arrival_s"]
+    lat.sort()
+    rank = lambda q: lat[max(0, int(np.ceil(q * len(lat))) - 1)]
+    return {
+        "workload": f"first {n_requests} requests of the served trace: Poisson arrivals at 200/s, "
+                    "L in {6..16}, 32-2048 realizations, 16-32 temps in [0.8,2.0], 10^3-10^5 "
+                    "sweeps log-uniform, swap every 10",
+        "value": st["span_s"] / st["flip_attempts"] * 1e12, "unit": UNIT,
+        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "rounds": st["rounds"],
+        "peak_bytes": st["peak_bytes"], "round_ms": round_ms,
+        "plain_value": span / flips * 1e12, "plain_p50_ms": rank(0.5), "plain_p99_ms": rank(0.99),
+        "identical_to_plain": bool(same), "flips": flips,
+    }
+
+
 def run_reference(args, wl):
     """Reference arm: the CPU oracle, timed as it stands on the host cores."""
     rank, world, _ = dist_env()
@@ -236,8 +381,8 @@ def run_reference(args, wl):
     ts = [step(n) for _ in range(args.steps)]
     flips = n * inst.N * inst.NT * inst.C * 32 * g
     val = sum(ts) / len(ts) / flips * 1e12
-    sample = (f"{g} of {inst.G} word-groups, {n} sweeps per step, swap every sweep, "
-              f"measurement over the second half")
+    sample = (f"{g} of {inst.G} word-groups, {n} sweeps per step, swap every "
+              f"{wl['swap_every']}" + (", measurement over the second half" if wl["measure_every"] else ""))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / len(ts),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
@@ -261,6 +406,9 @@ def main():
     ap.add_argument("--sweeps", type=int, default=None,
                     help="sweeps per step (default: the workload's full run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-mix and served-trace measurements (N=1 only)")
+    ap.add_argument("--served-requests", type=int, default=32)
     args = ap.parse_args()
     wl = workload(args.workload, args.sweeps)
     if args.impl == "reference":
@@ -314,13 +462,37 @@ def main():
             barrier()
         launches = ens.launches - l0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(tt.item())
+    t_total = reduce_max(sum(step_ms) / 1e3, world)
     value = t_total / (wl["flips"] * args.steps * world) * 1e12
     clocks = clk.summary()
+
+    # the same workload with the energy / overlap-q measurement after every sweep
+    # of the second half (the paper measures every few thousand sweeps and
+    # quotes its speed without measurements, Sec. 3): reported beside the value
+    with_meas = None
+    wm_key = args.workload + "_measured"
+    if world == 1 and not args.no_extras and wm_key in WORKLOADS:
+        wm = workload(wm_key, args.sweeps)
+
+        def mstep():
+            s0 = ens.sweep_index
+            ens.sweep(wm["sweeps"], wm["swap_every"], qhist=qh, esum=es,
+                      measure_from=s0 + wm["measure_from"], measure_every=wm["measure_every"])
+
+        with torch.cuda.stream(stream):
+            mstep()
+            mt = []
+            for i in range(2):
+                flush.fill_(i)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                mstep()
+                b.record(stream)
+                b.synchronize()
+                mt.append(a.elapsed_time(b))
+        v_meas = statistics.mean(mt) / 1e3 / wm["flips"] * 1e12
+        with_meas = {"workload": wm["name"], "value": v_meas, "unit": UNIT, "steps": 2,
+                     "measurement_share": 1.0 - value / v_meas}
 
     # roofline of the dominant kernel (the fused sweep kernel: one launch per step)
     peaks = measured_peaks()
@@ -349,11 +521,7 @@ def main():
                   h_in["metro"], h_in["swapt"], wl["sweeps"], wl["swap_every"],
                   measure_from=wl["measure_from"], measure_every=wl["measure_every"],
                   want_spins=True, want_qhist=True, want_esum=True, host_out=h_out, stream=stream)
-    t_e2e = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = reduce_max((time.perf_counter() - t0) / e2e_steps, world)
     h2d = sum(v.nbytes for v in h_in.values())
     d2h = sum(v.nbytes for v in h_out.values())
 
@@ -369,7 +537,7 @@ def main():
                        "kernel_launches_per_step": launches / args.steps},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                          "frac": achieved / peak_tops, "traffic": recorded_traffic(wl["key"]),
-                         "traffic_source_hash": kernel_source_hash(),
+                         "traffic_source_hash": kernel_source_hash(wl["key"]),
                          "peak_basis": f"{sms} SMs x {ALU_LANES_PER_CLK_PER_SM} int-ALU lanes/clk x "
                                        f"{mhz:.0f} MHz (max SM clock of measured peaks file)",
                          "alg_ops_per_site_word": ALG_OPS_PER_SITE_WORD},
@@ -379,6 +547,11 @@ def main():
             "clocks": clocks,
             "flips_per_step": wl["flips"] * world,
         }
+        if with_meas is not None:
+            line["with_measurement"] = with_meas
+        if world == 1 and not args.no_extras:
+            line["batched"] = bench_batched(ea, torch)
+            line["served"] = bench_served(ea, args.served_requests)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)
