@@ -136,18 +136,35 @@ std::vector<BPlan> batch_candidates(const ea_ctx *c, size_t optin)
     return out;
 }
 
-// Default: the candidate within `maxt` threads that keeps most threads busy;
-// ties go to the specialised kernel, then the unit body, then chunks.
+// Default: among the candidates within `maxt` threads that keep at least
+// three quarters of the CTA busy (else among those keeping the most busy):
+// the specialised kernel on 384-thread CTAs (where it runs without spills),
+// else the fewest threads per lattice (more work per thread); ties go to more
+// busy threads, then unit bodies before chunks.
 int default_candidate(const std::vector<BPlan> &cands, int maxt)
 {
+    int most = 0;
+    for (const BPlan &p : cands)
+        if (p.threads <= maxt && p.threads > most) most = p.threads;
+    const int floor_threads = most * 4 >= maxt * 3 ? (maxt * 3 + 3) / 4 : most;
+    auto rank = [](const BPlan &p) { return p.form == kBFast ? 1 : p.form == kBUnit ? 2 : 0; };
+    auto tpl = [](const BPlan &p) { return p.form == kBFast ? 2 * p.p1 : p.p1; };
     int best = -1;
-    auto rank = [](const BPlan &p) { return p.form == kBFast ? 2 : p.form == kBUnit ? 1 : 0; };
     for (int i = 0; i < (int)cands.size(); ++i) {
         const BPlan &p = cands[(size_t)i];
-        if (p.threads > maxt) continue;
+        if (p.threads > maxt || p.threads < floor_threads) continue;
         if (best < 0) { best = i; continue; }
         const BPlan &q = cands[(size_t)best];
-        if (p.threads > q.threads || (p.threads == q.threads && rank(p) > rank(q))) best = i;
+        const bool pf = p.form == kBFast && maxt <= 384, qf = q.form == kBFast && maxt <= 384;
+        if (pf != qf) {
+            if (pf) best = i;
+        } else if (tpl(p) != tpl(q)) {
+            if (tpl(p) < tpl(q)) best = i;
+        } else if (p.threads != q.threads) {
+            if (p.threads > q.threads) best = i;
+        } else if (rank(p) > rank(q)) {
+            best = i;
+        }
     }
     return best;
 }
@@ -220,6 +237,7 @@ cudaError_t grow_host(T **p, size_t *cap, size_t need)
 }
 
 // Width of the batch kernel: forced, else 384 if every member's plan fits.
+// (Automatic defaults are chosen for 512; explicit choices may all fit 384.)
 int kernel_width(const ea_batch *b, const std::vector<int> &resolved)
 {
     if (b->force_threads) return b->force_threads;
@@ -229,17 +247,21 @@ int kernel_width(const ea_batch *b, const std::vector<int> &resolved)
 }
 
 // Candidate index each member runs under: its explicit choice, else the
-// default for the forced width (or 384, then 512).  -1 if none fits.
+// default for the forced width; with the width automatic, the defaults for
+// 512 threads, or those for 384 when every member fits 384 threads anyway.
 std::vector<int> resolve(const ea_batch *b)
 {
-    std::vector<int> r(b->ctxs.size(), -1);
-    for (size_t i = 0; i < b->ctxs.size(); ++i) {
-        if (b->choice[i] >= 0) { r[i] = b->choice[i]; continue; }
-        const int w = b->force_threads ? b->force_threads : ea::kBatchSmallThreads;
-        r[i] = ea::default_candidate(b->cands[i], w);
-        if (r[i] < 0 && !b->force_threads) r[i] = ea::default_candidate(b->cands[i], ea::kBatchMaxThreads);
-    }
-    return r;
+    auto pick = [&](int w) {
+        std::vector<int> r(b->ctxs.size(), -1);
+        for (size_t i = 0; i < b->ctxs.size(); ++i)
+            r[i] = b->choice[i] >= 0 ? b->choice[i] : ea::default_candidate(b->cands[i], w);
+        return r;
+    };
+    if (b->force_threads) return pick(b->force_threads);
+    std::vector<int> r = pick(ea::kBatchMaxThreads);
+    for (size_t i = 0; i < r.size(); ++i)
+        if (r[i] >= 0 && b->cands[i][(size_t)r[i]].threads > ea::kBatchSmallThreads) return r;
+    return pick(ea::kBatchSmallThreads);
 }
 
 int wait_pending(ea_batch *b)
