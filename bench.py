@@ -10,7 +10,8 @@ paper's own figure (Sec. 3):
     t = T / (sweeps * N * NT * C * realizations).
 The same workload with the energy / overlap-q histogram measurement after every
 sweep of the second half is reported beside it ("with_measurement"), and at
-N = 1 the batched mixed-size form and the served trace ("batched", "served").
+N = 1 samples of the L=16 / L=32 ensembles ("large"), the batched mixed-size
+form and the served trace ("batched", "served").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch under torch.distributed.run; each rank runs its own ensemble
@@ -296,6 +297,42 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
     }
 
 
+def bench_large(ea, torch, peak_tops, sweeps=200):
+    """The L=16 and L=32 ensembles of the largest configuration (10^5 sweeps each,
+    swap every 10), timed on a sample of `sweeps` sweeps from warm state with L2
+    flushed, with the integer-ALU roofline fraction of the whole step."""
+    out = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    for key in ("large16", "large32"):
+        wl = workload(key, sweeps)
+        inst = wl["inst"]
+        inp = W.draw_inputs(inst)
+        metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+        ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
+                          metro, swapt)
+        ens.sweep(wl["sweeps"], wl["swap_every"])            # warm
+        flush.fill_(2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ens.launches
+        a.record()
+        ens.sweep(wl["sweeps"], wl["swap_every"])
+        b.record()
+        b.synchronize()
+        t = a.elapsed_time(b) / 1e3
+        site_words = wl["sweeps"] * inst.N * inst.NT * inst.C * inst.G
+        achieved = site_words * ALG_OPS_PER_SITE_WORD / t / 1e12
+        plan = ens.plans()[ens.plan]
+        out[key] = {"workload": wl["name"].replace(f"{sweeps} sweeps", f"{sweeps} of 100000 sweeps (sample)"),
+                    "value": t / wl["flips"] * 1e12, "unit": UNIT,
+                    "roofline_frac": achieved / peak_tops, "achieved_tops": achieved,
+                    "gpu_launches": ens.launches - l0,
+                    "plan": f"{plan['form']} t{plan['threads']} g{plan['group_threads']} "
+                            f"n{plan['lattices_per_cta']}"}
+        ens.close()
+        del ens
+    return out
+
+
 def bench_served(ea, n_requests=32, round_ms=20):
     """Poisson-arriving requests (200/s) replayed in real time through the server,
     against serving them one at a time with plain launches (arrival order); the
@@ -550,6 +587,7 @@ def main():
         if with_meas is not None:
             line["with_measurement"] = with_meas
         if world == 1 and not args.no_extras:
+            line["large"] = bench_large(ea, torch, peak_tops)
             line["batched"] = bench_batched(ea, torch)
             line["served"] = bench_served(ea, args.served_requests)
         if not args.no_cpu_baseline:
