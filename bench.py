@@ -238,7 +238,7 @@ def _flips(inst, sweeps):
     return sweeps * inst.N * inst.NT * inst.C * 32 * inst.G
 
 
-def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVERY):
+def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVERY, autotune=True):
     """The mixed ensemble (L in {4..16}, uneven sizes and ladders) advanced by one
     persistent batched launch, against the same instances launched one after
     another; both sides autotuned, both timed from warm state with L2 flushed."""
@@ -261,8 +261,9 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
         b.synchronize()
         return a.elapsed_time(b) / 1e3
 
-    for e in ens:
-        e.autotune(probe_sweeps=200, swap_every=swap_every)
+    if autotune:
+        for e in ens:
+            e.autotune(probe_sweeps=200, swap_every=swap_every)
 
     def plain():
         for e in ens:
@@ -274,7 +275,8 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
     t_plain = timed(plain)
     plain_launches = sum(e.launches for e in ens) - l1
     batch = ea.Batch(ens)
-    batch.autotune(probe_sweeps=200, swap_every=swap_every)
+    if autotune:
+        batch.autotune(probe_sweeps=200, swap_every=swap_every)
 
     def batched():
         batch.sweep(sweeps, swap_every)
@@ -333,11 +335,17 @@ def bench_large(ea, torch, peak_tops, sweeps=200):
     return out
 
 
-def bench_served(ea, n_requests=32, round_ms=20):
+def bench_served(ea, n_requests=32, round_ms=20, load=None, rate_flips_s=None):
     """Poisson-arriving requests (200/s) replayed in real time through the server,
     against serving them one at a time with plain launches (arrival order); the
-    results of the two are compared bit for bit."""
+    results of the two are compared bit for bit.  With `load`, arrival times are
+    stretched so that the offered work is that fraction of `rate_flips_s`."""
     trace = W.served_trace(n_requests)
+    scale = 1.0
+    if load:
+        work = sum(_flips(r["inst"], r["sweeps"]) for r in trace)
+        scale = work / rate_flips_s / load / max(trace[-1]["arrival_s"], 1e-9)
+        trace = [dict(r, arrival_s=r["arrival_s"] * scale) for r in trace]
     data = []
     for r in trace:
         inst = r["inst"]
@@ -375,8 +383,9 @@ def bench_served(ea, n_requests=32, round_ms=20):
     lat.sort()
     rank = lambda q: lat[max(0, int(np.ceil(q * len(lat))) - 1)]
     return {
-        "workload": f"first {n_requests} requests of the served trace: Poisson arrivals at 200/s, "
-                    "L in {6..16}, 32-2048 realizations, 16-32 temps in [0.8,2.0], 10^3-10^5 "
+        "workload": f"first {n_requests} requests of the served trace: Poisson arrivals at "
+                    f"{200.0 / scale:.3g}/s" + (f" (offered load {load:.0%} of the served rate)" if load else "")
+                    + ", L in {6..16}, 32-2048 realizations, 16-32 temps in [0.8,2.0], 10^3-10^5 "
                     "sweeps log-uniform, swap every 10",
         "value": st["span_s"] / st["flip_attempts"] * 1e12, "unit": UNIT,
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "rounds": st["rounds"],
@@ -446,7 +455,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-mix and served-trace measurements (N=1 only)")
     ap.add_argument("--served-requests", type=int, default=32)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched mix with default plans (--sweeps sweeps) and print its object")
     args = ap.parse_args()
+    if args.batched_only:
+        import torch
+        import paper_1311_5582_gb300 as ea
+        print(json.dumps(bench_batched(ea, torch, sweeps=args.sweeps or W.BATCH_SWEEPS, autotune=False)))
+        return 0
     wl = workload(args.workload, args.sweeps)
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -590,6 +606,8 @@ def main():
             line["large"] = bench_large(ea, torch, peak_tops)
             line["batched"] = bench_batched(ea, torch)
             line["served"] = bench_served(ea, args.served_requests)
+            line["served_load70"] = bench_served(ea, 16, load=0.7,
+                                                 rate_flips_s=1e12 / line["served"]["value"])
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line), flush=True)

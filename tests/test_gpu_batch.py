@@ -202,3 +202,45 @@ def test_empty_batch_and_zero_sweeps_are_no_ops():
     assert gpu.counters == (0, 0)
     np.testing.assert_array_equal(gpu.read_spins().cpu().numpy().view(np.uint32), inp["spins"])
     assert batch.launches == 0
+
+
+def test_large_lattices_in_a_batch():
+    """Chunked members of the largest sizes (L = 20, 24, 32) beside small unit members."""
+    insts = instances([(20, 1, 6, 2), (24, 1, 4, 1), (32, 1, 3, 2), (4, 2, 8, 2), (14, 1, 12, 2)], 2500)
+    members = [make(i) for i in insts]
+    batch = ea.Batch([m[0] for m in members])
+    schedule = [(7, 2), (5, 3)]
+    for n, k in schedule:
+        batch.sweep(n, k)
+    batch.sync()
+    for inst, (gpu, inp, metro, swapt) in zip(insts, members):
+        sp, en, ctr = state(gpu)
+        sp_a, en_a, ctr_a = run_alone(inst, schedule)
+        tag = f"L={inst.L} NT={inst.NT} C={inst.C}"
+        np.testing.assert_array_equal(sp, sp_a, err_msg=tag)
+        np.testing.assert_array_equal(en, en_a, err_msg=tag)
+        assert ctr == ctr_a, tag
+        if inst.L <= 24:
+            sim = oracle.OracleSim(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"],
+                                   inp["spins"], metro, swapt)
+            for n, k in schedule:
+                sim.sweep(n, k, threads=8)
+            np.testing.assert_array_equal(sp, sim.spins(), err_msg="oracle " + tag)
+
+
+def test_per_member_sweeps_and_schedules():
+    """ea_batch_sweep_each: members advance by their own counts and swap periods (0: not this call)."""
+    insts = instances([(6, 2, 8, 2), (8, 1, 24, 2), (16, 1, 32, 1)], 2700)
+    members = [make(i) for i in insts]
+    batch = ea.Batch([m[0] for m in members])
+    calls = [([13, 0, 9], [3, 1, 10]), ([4, 21, 17], [1, 5, 4]), ([0, 6, 0], [2, 2, 2])]
+    for n, k in calls:
+        batch.sweep_each(n, k)
+    batch.sync()
+    for i, (inst, (gpu, *_rest)) in enumerate(zip(insts, members)):
+        sp, en, ctr = state(gpu)
+        sched = [(n[i], k[i]) for n, k in calls if n[i] > 0]
+        sp_a, en_a, ctr_a = run_alone(inst, sched)
+        np.testing.assert_array_equal(sp, sp_a, err_msg=f"member {i}")
+        np.testing.assert_array_equal(en, en_a)
+        assert ctr == ctr_a
