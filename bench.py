@@ -238,6 +238,12 @@ def _flips(inst, sweeps):
     return sweeps * inst.N * inst.NT * inst.C * 32 * inst.G
 
 
+def _alu_peak_tops(torch):
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * ALU_LANES_PER_CLK_PER_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
 def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVERY, autotune=True):
     """The mixed ensemble (L in {4..16}, uneven sizes and ladders) advanced by one
     persistent batched launch, against the same instances launched one after
@@ -292,6 +298,7 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
             f"L={i.L} {32 * i.G} realizations x {i.NT} temps" for i in insts)
             + f" (C=2, ladders geometric in [0.8,2.0]), {sweeps} sweeps, swap every {swap_every}",
         "value": t_batch / flips * 1e12, "unit": UNIT, "plain_value": t_plain / flips * 1e12,
+        "roofline_frac": flips / 32 * ALG_OPS_PER_SITE_WORD / t_batch / 1e12 / _alu_peak_tops(torch),
         "speedup_vs_plain": t_plain / t_batch, "gpu_launches": batch.launches - b0,
         "plain_gpu_launches": plain_launches, "flips": flips,
         "plans": [f"{p['form']} t{p['threads']} g{p['group_threads']} u{p['units_per_cta']}"
@@ -388,6 +395,8 @@ def bench_served(ea, n_requests=32, round_ms=20, load=None, rate_flips_s=None):
                     + ", L in {6..16}, 32-2048 realizations, 16-32 temps in [0.8,2.0], 10^3-10^5 "
                     "sweeps log-uniform, swap every 10",
         "value": st["span_s"] / st["flip_attempts"] * 1e12, "unit": UNIT,
+        "roofline_frac": (st["flip_attempts"] / 32 * ALG_OPS_PER_SITE_WORD / st["span_s"] / 1e12
+                          / _alu_peak_tops(__import__("torch"))),
         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "rounds": st["rounds"],
         "peak_bytes": st["peak_bytes"], "round_ms": round_ms,
         "plain_value": span / flips * 1e12, "plain_p50_ms": rank(0.5), "plain_p99_ms": rank(0.99),
