@@ -234,10 +234,14 @@ void ea_batch_destroy(ea_batch *batch);
 
 /* Serving loop: a server accepts simulation requests from any thread, admits
  * them in arrival order while their device memory fits its budget, keeps
- * their state resident, and advances all resident requests together in
- * rounds of one batched launch (ea_batch_sweep_each), each by up to the
- * number of sweeps that makes the round last about round_ms; requests that
- * arrive meanwhile join at the next round (continuous batching).  Each
+ * their state resident, and advances resident requests together in rounds
+ * of one batched launch (ea_batch_sweep_each), each by up to the number of
+ * sweeps that makes the round last about round_ms; requests that arrive
+ * meanwhile join at the next round (continuous batching).  A round takes the
+ * requests with the least work left, in that order, until their (group,
+ * copy) units give about two tasks per SM (shortest remaining work first
+ * while the GPU stays full); a request left out of 64 consecutive rounds
+ * goes first.  Each
  * result is exactly what ea_create + ea_sweep would give alone.  The paper
  * runs one simulation at a time (Sec. 3); serving is this library's own
  * addition.  One worker thread per server owns its GPU work; the server uses

@@ -3,9 +3,12 @@
 // in rounds of one persistent batched launch (continuous batching).
 //
 // One worker thread owns the GPU work.  Each round it
-//   1. launches one batched call (ea_batch_sweep_each) in which every resident
-//      request advances by min(q, sweeps left) sweeps, q sized so that the
-//      round lasts about round_ms at the measured rate;
+//   1. launches one batched call (ea_batch_sweep_each) in which the resident
+//      requests with the least work left -- as many as give about two
+//      (group, copy) units per SM -- advance by min(q, sweeps left) sweeps, q
+//      sized so that the round lasts about round_ms at the measured rate
+//      (shortest remaining work first, which minimises mean latency when
+//      requests queue, while keeping the GPU full);
 //   2. while that runs, admits queued requests in arrival order as long as
 //      their device bytes fit the budget (contexts are created on a second
 //      stream from a stream-ordered memory pool, so nothing waits for the
@@ -52,12 +55,16 @@ struct Request {
     ea_ctx *ctx = nullptr;
     uint32_t left = 0;                            // sweeps still to run
     uint64_t words = 0;                           // site-words of one sweep (N * NT * C * G)
+    uint32_t waited = 0;                          // consecutive rounds left out
 };
+
+// A request left out of this many consecutive rounds goes first in the next.
+constexpr uint32_t kAgeRounds = 64;
 
 }  // namespace
 
 struct ea_server {
-    int device = 0;
+    int device = 0, sms = 1;
     size_t budget = 0, used = 0, peak = 0;
     uint32_t max_live = 256;
     double round_ms = 20.0;
@@ -213,8 +220,27 @@ void run_round(ea_server *s)
         complete(s, done);
         return;
     }
+    // Shortest remaining work first, as far as the GPU stays full: the requests
+    // with the least work left join this round, in that order, until their
+    // (group, copy) units give about two tasks per SM; the rest wait a round.
+    std::vector<size_t> order(n);
+    for (size_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        const Request &a = *s->live[x], &b = *s->live[y];
+        const bool aged_a = a.waited >= kAgeRounds, aged_b = b.waited >= kAgeRounds;
+        if (aged_a != aged_b) return aged_a;      // starved requests first
+        return (double)a.left * (double)a.words < (double)b.left * (double)b.words;
+    });
+    std::vector<char> in_round(n, 0);
     double words = 0.0;
-    for (size_t i = 0; i < n; ++i) words += (double)s->live[i]->words;
+    uint64_t units = 0;
+    for (size_t j = 0; j < n; ++j) {
+        const Request &r = *s->live[order[j]];
+        if (units >= 2ull * (uint64_t)s->sms && j > 0) break;
+        in_round[order[j]] = 1;
+        words += (double)r.words;
+        units += (uint64_t)r.ctx->G * r.ctx->C;
+    }
     double qd = s->round_ms * s->rate / (words > 0 ? words : 1.0);
     const uint32_t q = (uint32_t)std::max(1.0, std::min(qd, 1048576.0));
     ea_batch_clear(s->batch);
@@ -223,7 +249,8 @@ void run_round(ea_server *s)
     for (size_t i = 0; i < n && rc == EA_OK; ++i) {
         Request &r = *s->live[i];
         rc = ea_batch_add(s->batch, r.ctx);
-        nsw[i] = std::min(q, r.left);
+        nsw[i] = in_round[i] ? std::min(q, r.left) : 0u;
+        r.waited = in_round[i] ? 0u : r.waited + 1u;
         kev[i] = r.swap_every;
     }
     double work = 0.0;
@@ -323,6 +350,7 @@ int ea_server_create(const ea_server_opts *opts, ea_server **out)
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     const size_t cap = free_b / 10 * 9;
     s->budget = (opts && opts->mem_budget) ? std::min((size_t)opts->mem_budget, cap) : cap / 10 * 9;
     if (opts && opts->max_live) s->max_live = opts->max_live;
