@@ -215,6 +215,16 @@ int ea_batch_set_plan(ea_batch *batch, uint32_t member, int plan_index);
  * unless a chosen plan needs more).  Plans wider than the width fail the
  * next ea_batch_sweep with EA_EUNSUPPORTED. */
 int ea_batch_set_width(ea_batch *batch, int threads);
+/* How long a CTA of the batch kernel waits for its next task before it
+ * raises the batch's error flag (in naps of ~256 ns; 0 = the default, tens
+ * of seconds).  A call whose wait runs out ends with every CTA returned and
+ * ea_batch_sync reporting EA_ETIMEOUT; the members' state is then partly
+ * advanced and must be rewritten (ea_write_spins) or discarded.  Correct
+ * calls never wait that long. */
+int ea_batch_set_wait_limit(ea_batch *batch, uint32_t naps);
+/* Test hook for that path: the next ea_batch_sweep queues one task that is
+ * never published, so one CTA's wait runs out (no fault, no trap). */
+int ea_batch_inject_stall(ea_batch *batch);
 /* Work of one unit task in site-word updates (sweeps x N x NT x units); 0 = default. */
 int ea_batch_set_segment(ea_batch *batch, uint32_t site_words);
 int ea_batch_sweep(ea_batch *batch, uint32_t n_sweeps, uint32_t swap_every);

@@ -79,7 +79,8 @@ EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_s
            "ea_get_counters", "ea_sync", "ea_launch_count", "ea_plan_count", "ea_plan_current",
            "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_batch_create", "ea_batch_add",
            "ea_batch_clear", "ea_batch_plan_count", "ea_batch_plan_info", "ea_batch_plan_current",
-           "ea_batch_set_plan", "ea_batch_set_width", "ea_batch_set_segment", "ea_batch_sweep",
+           "ea_batch_set_plan", "ea_batch_set_width", "ea_batch_set_wait_limit", "ea_batch_inject_stall",
+           "ea_batch_set_segment", "ea_batch_sweep",
            "ea_batch_sweep_each", "ea_batch_sync", "ea_batch_autotune", "ea_batch_launch_count", "ea_batch_destroy",
            "ea_server_create", "ea_submit", "ea_poll", "ea_server_stats_get", "ea_server_destroy",
            "ea_run",
@@ -131,6 +132,8 @@ def load_library(path: str | None = None):
     lib.ea_batch_plan_current.argtypes = [vp, u32]
     lib.ea_batch_set_plan.argtypes = [vp, u32, i32]
     lib.ea_batch_set_width.argtypes = [vp, i32]
+    lib.ea_batch_set_wait_limit.argtypes = [vp, u32]
+    lib.ea_batch_inject_stall.argtypes = [vp]
     lib.ea_batch_autotune.argtypes = [vp, u32, u32, ctypes.POINTER(ctypes.c_float)]
     lib.ea_batch_set_segment.argtypes = [vp, u32]
     lib.ea_batch_sweep.argtypes = [vp, u32, u32]
@@ -156,7 +159,8 @@ def load_library(path: str | None = None):
                  "ea_batch_create", "ea_batch_add", "ea_batch_clear", "ea_batch_set_plan",
                  "ea_batch_set_segment", "ea_batch_sweep", "ea_batch_sync", "ea_batch_plan_count",
                  "ea_batch_plan_info", "ea_batch_plan_current", "ea_batch_set_width",
-                 "ea_batch_autotune", "ea_batch_sweep_each", "ea_server_create", "ea_submit",
+                 "ea_batch_autotune", "ea_batch_sweep_each", "ea_batch_set_wait_limit",
+                 "ea_batch_inject_stall", "ea_server_create", "ea_submit",
                  "ea_poll", "ea_server_stats_get"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
@@ -399,6 +403,12 @@ class Batch:
 
     def set_plan(self, member: int, plan_index: int):
         _check(self.lib.ea_batch_set_plan(self.b, int(member), int(plan_index)), "ea_batch_set_plan")
+
+    def set_wait_limit(self, naps: int):
+        _check(self.lib.ea_batch_set_wait_limit(self.b, int(naps)), "ea_batch_set_wait_limit")
+
+    def inject_stall(self):
+        _check(self.lib.ea_batch_inject_stall(self.b), "ea_batch_inject_stall")
 
     def set_width(self, threads: int):
         _check(self.lib.ea_batch_set_width(self.b, int(threads)), "ea_batch_set_width")

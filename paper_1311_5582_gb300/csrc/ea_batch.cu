@@ -181,6 +181,8 @@ struct ea_batch {
     std::vector<int> choice;                    // per member: candidate index, -1 automatic
     int force_threads;                          // 0, or the batch kernel's width (384 / 512)
     uint32_t seg_target;                        // site-words per unit piece (0: default)
+    uint32_t wait_limit;                        // naps before a waiting CTA gives up (0: default)
+    bool stall_next;                            // test hook: next call gets a task never published
     // device buffers: upload area (header + instance table), task queue, flags, joins
     unsigned char *d_up;
     ea::BatchTask *d_tasks;
@@ -373,6 +375,20 @@ int ea_batch_set_width(ea_batch *b, int threads)
     return EA_OK;
 }
 
+int ea_batch_set_wait_limit(ea_batch *b, uint32_t naps)
+{
+    if (!b) return EA_EINVAL;
+    b->wait_limit = naps;
+    return EA_OK;
+}
+
+int ea_batch_inject_stall(ea_batch *b)
+{
+    if (!b) return EA_EINVAL;
+    b->stall_next = true;
+    return EA_OK;
+}
+
 int ea_batch_set_segment(ea_batch *b, uint32_t site_words)
 {
     if (!b) return EA_EINVAL;
@@ -473,6 +489,9 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
         }
         if (p.smem > smem) smem = p.smem;
     }
+    // test hook: one more task than will ever be published, so that the CTA
+    // that takes its index waits until its limit runs out
+    if (b->stall_next) total += 1;
     if (total > 0xFFFFFFF0ull) return EA_EINVAL;
     // longest unit first
     std::vector<size_t> order(init.size());
@@ -485,6 +504,8 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
     hdr->epoch = b->epoch;
     hdr->ninit = (uint32_t)init.size();
     hdr->ninst = (uint32_t)ninst;
+    hdr->spin_limit = b->wait_limit ? b->wait_limit : kSpinLimit;
+    b->stall_next = false;
 
     const void *kern = threads == kBatchSmallThreads ? batch_kernel_384() : batch_kernel_512();
     const BatchShape shape{ninst, init.size(), total, smem, threads};

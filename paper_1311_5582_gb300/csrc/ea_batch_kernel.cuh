@@ -11,7 +11,7 @@
 namespace ea {
 
 constexpr int kBatchMaxThreads = 512;
-constexpr uint32_t kSpinLimit = 1u << 26;   // ~ tens of seconds of 256 ns naps
+constexpr uint32_t kSpinLimit = 1u << 26;   // default wait: ~ tens of seconds of 256 ns naps
 
 enum BatchForm { kBUnit = 0, kBFast = 1, kBChunk = 2 };
 
@@ -45,6 +45,8 @@ struct BatchHdr {
     uint32_t epoch;         // ready[i] == epoch: task i is published
     uint32_t ninit;         // initial tasks, already in tasks[0 .. ninit)
     uint32_t ninst;
+    uint32_t spin_limit;    // naps a CTA waits for a task before raising the error flag
+    uint32_t pad[3];
 };
 
 __host__ __device__ inline uint64_t swaps_between(uint64_t a, uint64_t b, uint32_t k)
@@ -139,7 +141,7 @@ k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tas
         uint32_t *join, BatchCtl *ctl)
 {
     extern __shared__ uint4 smem_u4[];
-    const uint32_t total = hdr->total, epoch = hdr->epoch;
+    const uint32_t total = hdr->total, epoch = hdr->epoch, spin_limit = hdr->spin_limit;
     uint32_t *base = reinterpret_cast<uint32_t *>(smem_u4);
     __shared__ SweepLaunch s_a;
     __shared__ BatchTask s_t;
@@ -156,7 +158,7 @@ k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tas
                 cuda::atomic_ref<int32_t, cuda::thread_scope_device> er(ctl->err);
                 uint32_t n = 0;
                 while (r.load(cuda::memory_order_acquire) != epoch) {
-                    if (++n > kSpinLimit || er.load(cuda::memory_order_relaxed) != 0) {
+                    if (++n > spin_limit || er.load(cuda::memory_order_relaxed) != 0) {
                         er.store(1, cuda::memory_order_relaxed);
                         state = 1;
                         break;

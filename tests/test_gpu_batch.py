@@ -244,3 +244,33 @@ def test_per_member_sweeps_and_schedules():
         np.testing.assert_array_equal(sp, sp_a, err_msg=f"member {i}")
         np.testing.assert_array_equal(en, en_a)
         assert ctr == ctr_a
+
+
+def test_a_wait_that_runs_out_reports_timeout_and_the_batch_recovers():
+    """Failure path without a fault: one queued task is never published, the CTA
+    waiting for it gives up after a short limit, every CTA returns, ea_batch_sync
+    reports EA_ETIMEOUT, and the same batch object then runs correctly."""
+    insts = instances([(4, 1, 4, 2), (8, 1, 8, 2)], 3100)
+    members = [make(i) for i in insts]
+    batch = ea.Batch([m[0] for m in members])
+    batch.set_wait_limit(4096)                  # ~1 ms of naps
+    batch.inject_stall()
+    batch.sweep(20, 5)
+    with pytest.raises(ea.EAError) as ei:
+        batch.sync()
+    assert ei.value.code == -4                  # EA_ETIMEOUT
+    torch.cuda.synchronize()                    # the context is healthy
+    # fresh members through the same batch object, default wait limit
+    batch.set_wait_limit(0)
+    batch.clear()
+    fresh = [make(i) for i in insts]
+    for m in fresh:
+        batch.add(m[0])
+    batch.sweep(20, 5)
+    batch.sync()
+    for inst, (gpu, *_rest) in zip(insts, fresh):
+        sp, en, ctr = state(gpu)
+        sp_a, en_a, ctr_a = run_alone(inst, [(20, 5)])
+        np.testing.assert_array_equal(sp, sp_a)
+        np.testing.assert_array_equal(en, en_a)
+        assert ctr == ctr_a
