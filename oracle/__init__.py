@@ -63,6 +63,8 @@ def _bind(lib):
     lib.or_energies_recompute.restype = None
     lib.or_overlaps.argtypes = [vp, _u32p]
     lib.or_overlaps.restype = ctypes.c_int
+    lib.or_plane_counts.argtypes = [vp, ctypes.c_int, _u32p]
+    lib.or_plane_counts.restype = ctypes.c_int
     lib.or_read_spins.argtypes = [vp, _u32p]
     lib.or_read_spins.restype = None
     lib.or_sweep_index.argtypes = [vp]
@@ -209,6 +211,15 @@ class OracleSim:
         out = np.zeros((self.G, self.NT, 32), np.uint32)
         if self.lib.or_overlaps(self.h, out) != 0:
             raise ValueError("overlaps need two copies")
+        return out
+
+    def plane_counts(self, mode: int) -> np.ndarray:
+        """Per-plane counts (or_plane_counts): mode 0 differing sites between the
+        copies [G][NT][3][L][32]; mode 1 up spins [G][NT][C][3][L][32]."""
+        shape = (self.G, self.NT, 3, self.L, 32) if mode == 0 else (self.G, self.NT, self.C, 3, self.L, 32)
+        out = np.zeros(shape, np.uint32)
+        if self.lib.or_plane_counts(self.h, int(mode), out) != 0:
+            raise ValueError("invalid mode (mode 0 needs two copies)")
         return out
 
     def spins(self) -> np.ndarray:

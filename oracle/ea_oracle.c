@@ -527,6 +527,45 @@ int or_overlaps(const or_sim *m, uint32_t *out)
     return 0;
 }
 
+/* Plane counts for Fourier-mode observables (Sec. 5: the spin-glass
+ * correlation length from the overlap, the ferromagnet's from the
+ * magnetisation).  Site i = x + L(y + Lz); plane (axis a, index p) holds the
+ * L^2 sites whose a-th coordinate is p.  mode 0: number of sites of the plane
+ * where the two copies of slot t differ, out [G][NT][3][L][32] (needs C = 2);
+ * mode 1: number of up spins of copy c in the plane, out [G][NT][C][3][L][32].
+ * Returns 0, or -1 for an invalid mode. */
+int or_plane_counts(const or_sim *m, int mode, uint32_t *out)
+{
+    const int L = m->L;
+    if (mode == 0 && m->C != 2) return -1;
+    if (mode != 0 && mode != 1) return -1;
+    const int ncopy = mode == 0 ? 1 : m->C;
+    for (int g = 0; g < m->G; ++g)
+        for (int t = 0; t < m->NT; ++t)
+            for (int c = 0; c < ncopy; ++c)
+                for (int b = 0; b < OR_LANES; ++b) {
+                    const int8_t *s0 = sig(m, g, c, b, lab(m, g, c, b)[t]);
+                    const int8_t *s1 = mode == 0 ? sig(m, g, 1, b, lab(m, g, 1, b)[t]) : 0;
+                    for (int a = 0; a < 3; ++a)
+                        for (int p = 0; p < L; ++p) {
+                            uint32_t n = 0;
+                            for (int u = 0; u < L; ++u)
+                                for (int v = 0; v < L; ++v) {
+                                    const int x = a == 0 ? p : u;
+                                    const int y = a == 1 ? p : (a == 0 ? u : v);
+                                    const int z = a == 2 ? p : v;
+                                    const int i = x + L * (y + L * z);
+                                    if (mode == 0) n += s0[i] != s1[i];
+                                    else n += s0[i] > 0;
+                                }
+                            const size_t row = mode == 0 ? (((size_t)g * m->NT + t) * 3 + a) * L + p
+                                                         : ((((size_t)g * m->NT + t) * m->C + c) * 3 + a) * L + p;
+                            out[row * OR_LANES + b] = n;
+                        }
+                }
+    return 0;
+}
+
 /* Spins packed back to words, by slot: out [G][NT][C][N]. */
 void or_read_spins(const or_sim *m, uint32_t *out)
 {
