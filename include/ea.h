@@ -130,6 +130,17 @@ int ea_pt_swap(ea_ctx *ctx, uint32_t *masks);
  * count per (g, b), or NULL (needs C == 2).  Asynchronous. */
 int ea_measure(ea_ctx *ctx, int32_t *energies, uint32_t *ndiff, uint64_t *qhist);
 
+/* Per-plane counts for Fourier-mode observables (Sec. 5: the spin-glass
+ * correlation length from the overlap, the ferromagnet's from the
+ * magnetisation).  Site i = x + L(y + Lz); plane (axis a, index p) holds the
+ * L^2 sites whose a-th coordinate (x, y, z for a = 0, 1, 2) is p.
+ * mode 0: sites of each plane where the two copies of a slot differ,
+ *         out = DEVICE int32 [G][NT][3][L][32] (needs n_copies == 2);
+ * mode 1: up spins of each plane per copy, out = DEVICE int32 [G][NT][C][3][L][32].
+ * Asynchronous on the context's stream; EA_EINVAL for another mode or mode 0
+ * with one copy. */
+int ea_measure_planes(ea_ctx *ctx, int mode, int32_t *out);
+
 /* Spins by slot into DEVICE dst [G][NT][C][N].  Asynchronous. */
 int ea_read_spins(ea_ctx *ctx, uint32_t *dst);
 

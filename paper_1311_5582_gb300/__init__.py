@@ -75,7 +75,7 @@ class _PlanDesc(ctypes.Structure):
 PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked"}
 
 EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_sweep",
-           "ea_pt_swap", "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
+           "ea_pt_swap", "ea_measure", "ea_measure_planes", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
            "ea_get_counters", "ea_sync", "ea_launch_count", "ea_plan_count", "ea_plan_current",
            "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_batch_create", "ea_batch_add",
            "ea_batch_clear", "ea_batch_plan_count", "ea_batch_plan_info", "ea_batch_plan_current",
@@ -110,6 +110,7 @@ def load_library(path: str | None = None):
     lib.ea_sweep.argtypes = [vp, ctypes.POINTER(_SweepArgs)]
     lib.ea_pt_swap.argtypes = [vp, vp]
     lib.ea_measure.argtypes = [vp, vp, vp, vp]
+    lib.ea_measure_planes.argtypes = [vp, i32, vp]
     lib.ea_read_spins.argtypes = [vp, vp]
     lib.ea_read_spins_host.argtypes = [vp, vp]
     lib.ea_write_spins.argtypes = [vp, vp, u64, u64]
@@ -153,6 +154,7 @@ def load_library(path: str | None = None):
     lib.ea_strerror.argtypes = [i32]
     lib.ea_strerror.restype = ctypes.c_char_p
     for name in ("ea_build_tables", "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
+                 "ea_measure_planes",
                  "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
                  "ea_get_counters", "ea_sync", "ea_run", "ea_plan_count", "ea_plan_current",
                  "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_pt_swap_static",
@@ -314,6 +316,16 @@ class Ensemble:
         nd = self._empty((self.G, self.NT, 32), torch.int32) if ndiff else None
         _check(self.lib.ea_measure(self.ctx, _ptr(e), _ptr(nd), _ptr(qhist)), "ea_measure")
         return e, nd
+
+    def measure_planes(self, mode: int):
+        """Per-plane counts (ea_measure_planes): mode 0 -> int32 [G][NT][3][L][32] of
+        sites where the copies differ; mode 1 -> [G][NT][C][3][L][32] of up spins."""
+        import torch
+        shape = ((self.G, self.NT, 3, self.L, 32) if mode == 0
+                 else (self.G, self.NT, self.C, 3, self.L, 32))
+        out = self._empty(shape, torch.int32)
+        _check(self.lib.ea_measure_planes(self.ctx, int(mode), _ptr(out)), "ea_measure_planes")
+        return out
 
     def read_spins(self, out=None):
         import torch

@@ -481,6 +481,15 @@ int ea_measure(ea_ctx *c, int32_t *energies, uint32_t *ndiff, uint64_t *qhist)
     return EA_OK;
 }
 
+int ea_measure_planes(ea_ctx *c, int mode, int32_t *out)
+{
+    if (!c || !out || (mode != 0 && mode != 1)) return EA_EINVAL;
+    if (mode == 0 && c->C != 2) return EA_EINVAL;
+    EA_TRY(ea::launch_measure_planes(c->d_spins, (int)c->L, c->G, c->NT, c->C, mode, out, c->stream,
+                                     &c->launches));
+    return EA_OK;
+}
+
 int ea_read_spins(ea_ctx *c, uint32_t *dst)
 {
     if (!c || !dst) return EA_EINVAL;

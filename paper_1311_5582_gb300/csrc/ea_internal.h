@@ -100,6 +100,9 @@ cudaError_t launch_sweep_chunk(const SweepLaunch &a, int L, const Plan &plan, cu
                                uint64_t *launches);
 cudaError_t launch_swap_global(const SweepLaunch &a, int L, uint64_t P, uint32_t *masks,
                                int32_t *energy_log_row, cudaStream_t st, uint64_t *launches);
+// Per-plane counts (k_measure_planes); L <= 32.
+cudaError_t launch_measure_planes(const uint32_t *spins, int L, uint32_t G, uint32_t NT, uint32_t C,
+                                  int mode, int32_t *out, cudaStream_t st, uint64_t *launches);
 cudaError_t launch_energy(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, int L,
                           uint32_t G, uint32_t NT, uint32_t C, cudaStream_t st,
                           uint64_t *launches);

@@ -200,6 +200,55 @@ __global__ void k_import_spins(const uint32_t *api, uint32_t *dev, int L, uint32
     }
 }
 
+// Per-plane counts for Fourier-mode observables (Sec. 5): one warp per plane
+// (axis blockIdx.y, index = warp), one block per unit.  mode 0: unit (g, t),
+// sites of the plane where the two copies differ; mode 1: unit (g, t, c), up
+// spins of the plane.  out [unit][3][L][32] in API order.  Each lane adds its
+// words into a bit-sliced counter; a 32 x 32 transpose gives each lane its
+// realization's count.
+__global__ void k_measure_planes(const uint32_t *spins, int L, uint32_t NT, uint32_t C, int mode,
+                                 int32_t *out)
+{
+    const int N = L * L * L, H = N / 2;
+    const uint32_t unit = blockIdx.x;
+    const int a = (int)blockIdx.y, plane = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    uint32_t g, t, c;
+    if (mode == 0) {
+        g = unit / NT;
+        t = unit % NT;
+        c = 0;
+    } else {
+        g = unit / (NT * C);
+        t = (unit / C) % NT;
+        c = unit % C;
+    }
+    const uint32_t *A = spins + (((size_t)g * C + c) * NT + t) * N;
+    const uint32_t *B = spins + (((size_t)g * C + (C - 1)) * NT + t) * N;
+    uint32_t acc[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) acc[q] = 0;
+    // per lane at most ceil(L^2 / 32) <= 32 words: the 8-plane counter cannot overflow
+    for (int j = lane; j < L * L; j += 32) {
+        const int u = j % L, v = j / L;
+        const int x = a == 0 ? plane : u;
+        const int y = a == 1 ? plane : (a == 0 ? u : v);
+        const int z = a == 2 ? plane : v;
+        const int i = x + L * (y + L * z);
+        const int w = ((x + y + z) & 1) * H + (i >> 1);
+        uint32_t cy = mode == 0 ? (A[w] ^ B[w]) : A[w];
+#pragma unroll
+        for (int q = 0; q < kPlanes; ++q) {
+            const uint32_t t2 = acc[q] & cy;
+            acc[q] ^= cy;
+            cy = t2;
+        }
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) cnt += __popc(warp_transpose(acc[q], lane)) << q;
+    out[(((size_t)unit * 3 + a) * L + plane) * kLanes + lane] = cnt;
+}
+
 __global__ void k_export_spins(const uint32_t *dev, uint32_t *api, int L, uint32_t G, uint32_t NT,
                                uint32_t C)
 {
@@ -466,6 +515,15 @@ cudaError_t launch_import_spins(const uint32_t *api_spins, uint32_t *spins, int 
 {
     const size_t N = (size_t)L * L * L;
     k_import_spins<<<grid_for(G * C * NT * N, 256), 256, 0, st>>>(api_spins, spins, L, G, NT, C);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure_planes(const uint32_t *spins, int L, uint32_t G, uint32_t NT, uint32_t C,
+                                  int mode, int32_t *out, cudaStream_t st, uint64_t *launches)
+{
+    const uint32_t units = mode == 0 ? G * NT : G * NT * C;
+    k_measure_planes<<<dim3(units, 3), 32 * L, 0, st>>>(spins, L, NT, C, mode, out);
     *launches += 1;
     return cudaGetLastError();
 }
