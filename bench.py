@@ -308,8 +308,9 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
 
 def bench_large(ea, torch, peak_tops, sweeps=200):
     """The L=16 and L=32 ensembles of the largest configuration (10^5 sweeps each,
-    swap every 10), timed on a sample of `sweeps` sweeps from warm state with L2
-    flushed, with the integer-ALU roofline fraction of the whole step."""
+    swap every 10), each under the plan its autotuner picks, timed on a sample of
+    `sweeps` sweeps from warm state with L2 flushed, with the integer-ALU
+    roofline fraction of the whole step."""
     out = {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     for key in ("large16", "large32"):
@@ -319,6 +320,7 @@ def bench_large(ea, torch, peak_tops, sweeps=200):
         metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
         ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
                           metro, swapt)
+        ens.autotune(probe_sweeps=60, swap_every=wl["swap_every"])
         ens.sweep(wl["sweeps"], wl["swap_every"])            # warm
         flush.fill_(2)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

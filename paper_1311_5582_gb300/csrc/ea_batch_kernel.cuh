@@ -97,10 +97,10 @@ __device__ __forceinline__ void run_unit(int L, uint32_t *base, const SweepLaunc
 __device__ __forceinline__ void run_fast(int L, int HP, uint32_t *base, const SweepLaunch &a,
                                          uint32_t unit, int swap_smem)
 {
-    if (L == 8 && HP == 4) unit_fast_body<8, 4>(base, a, unit, 0, swap_smem, 0, 0);
-    else if (L == 8 && HP == 8) unit_fast_body<8, 8>(base, a, unit, 0, swap_smem, 0, 0);
-    else if (L == 16 && HP == 32) unit_fast_body<16, 32>(base, a, unit, 0, swap_smem, 0, 0);
-    else if (L == 16 && HP == 64) unit_fast_body<16, 64>(base, a, unit, 0, swap_smem, 0, 0);
+    if (L == 8 && HP == 4) unit_fast_body<8, 4, false>(base, a, unit, 0, swap_smem, 0, 0);
+    else if (L == 8 && HP == 8) unit_fast_body<8, 8, false>(base, a, unit, 0, swap_smem, 0, 0);
+    else if (L == 16 && HP == 32) unit_fast_body<16, 32, false>(base, a, unit, 0, swap_smem, 0, 0);
+    else if (L == 16 && HP == 64) unit_fast_body<16, 64, false>(base, a, unit, 0, swap_smem, 0, 0);
 }
 
 __device__ __forceinline__ void run_chunk(int L, int j_smem, uint32_t *base, const SweepLaunch &a,

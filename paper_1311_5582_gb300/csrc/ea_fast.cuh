@@ -327,11 +327,19 @@ __device__ __forceinline__ void warp_sum_to_lanes(const uint32_t (&acc)[PL], int
     out[lane] = (int)warp_transpose(x, lane);
 }
 
-template <int L, int HP>
+// MEAS = false compiles the body without the measurement and log paths
+// (launches that measure and log nothing); the flags then must be 0 and the
+// log pointers null.
+template <int L, int HP, bool MEAS = true>
 __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const SweepLaunch &a, uint32_t unit,
-                                               int cluster_measure, int swap_in_smem, int snap_mode,
-                                               int hist_smem)
+                                               int cluster_measure_arg, int swap_in_smem, int snap_mode_arg,
+                                               int hist_smem_arg)
 {
+    const int cluster_measure = MEAS ? cluster_measure_arg : 0;
+    const int snap_mode = MEAS ? snap_mode_arg : 0;
+    const int hist_smem = MEAS ? hist_smem_arg : 0;
+    int32_t *const energy_log = MEAS ? a.energy_log : nullptr;
+    uint32_t *const swap_log = MEAS ? a.swap_log : nullptr;
     using Gm = Geo<L>;
     using Mp = FastMap<HP>;
     constexpr int N = Gm::N;
@@ -441,8 +449,8 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
     for (uint32_t n = 0; n < a.n_sweeps; ++n) {
         const uint64_t s = a.s0 + n;
         const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
-        const bool meas = measured(s, a.measure_from, a.measure_every);
-        const bool needE = swap_now || a.energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
+        const bool meas = MEAS && measured(s, a.measure_from, a.measure_every);
+        const bool needE = swap_now || energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
         uint32_t acc[PL];
 #pragma unroll
         for (int p = 0; p < PL; ++p) acc[p] = 0;
@@ -537,20 +545,20 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
                 }
                 dst[(size_t)(NT - 1) * RW] = x;
             }
-            if (a.swap_log != nullptr)
+            if (swap_log != nullptr)
                 for (int p = tid; p + 1 < NT; p += nthr)
-                    a.swap_log[(((size_t)pass_local * a.G + g) * a.C + c) * (NT - 1) + p] = msk[p];
+                    swap_log[(((size_t)pass_local * a.G + g) * a.C + c) * (NT - 1) + p] = msk[p];
             __syncthreads();
         }
         if (swap_after(s, a.swap_every)) {
             ++P;
             ++pass_local;
         }
-        if (a.energy_log != nullptr) {
+        if (energy_log != nullptr) {
             const size_t row = (size_t)(s - a.log_s0);
             for (int i = tid; i < NT * kLanes; i += nthr) {
                 const int t = i >> 5, b = i & 31;
-                a.energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = E[i];
+                energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = E[i];
             }
         }
         if (meas) {

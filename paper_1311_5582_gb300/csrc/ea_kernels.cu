@@ -483,7 +483,7 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
     // chunked form: always possible when one lattice fits
     {
         const int caps[] = {0, 1, 2, 4};
-        const int prefs[] = {0, 128, 256};
+        const int prefs[] = {0, 64, 128, 256};
         for (int cap : caps)
             for (int tp : prefs) {
                 Plan p;

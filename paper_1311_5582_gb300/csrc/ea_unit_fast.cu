@@ -4,21 +4,23 @@
 
 namespace ea {
 namespace {
-template <int L, int HP, int MAXT>
+template <int L, int HP, int MAXT, bool MEAS>
 __global__ void __launch_bounds__(MAXT, 1)
 k_sweep_unit_fast(const __grid_constant__ SweepLaunch a, int cluster_measure, int swap_in_smem,
                   int snap_mode, int hist_smem)
 {
     extern __shared__ uint4 smem_u4[];
-    unit_fast_body<L, HP>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, cluster_measure,
-                          swap_in_smem, snap_mode, hist_smem);
+    unit_fast_body<L, HP, MEAS>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, cluster_measure,
+                                swap_in_smem, snap_mode, hist_smem);
 }
 
 template <int L, int HP, int MAXT>
 cudaError_t launch_fast(const SweepLaunch &a, size_t smem, bool swap_in_smem, bool cluster_measure,
                         bool snap_mode, bool hist_smem, cudaStream_t st)
 {
-    auto kern = k_sweep_unit_fast<L, HP, MAXT>;
+    // launches that measure and log nothing run the body compiled without those paths
+    const bool meas = a.measure_every != 0 || a.energy_log != nullptr || a.swap_log != nullptr;
+    auto kern = meas ? k_sweep_unit_fast<L, HP, MAXT, true> : k_sweep_unit_fast<L, HP, MAXT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
