@@ -87,7 +87,7 @@ __device__ __forceinline__ void run_unit(int L, uint32_t *base, const SweepLaunc
                                          int tpl, int swap_smem, int m)
 {
     switch (L) {
-#define EA_U(X) case X: unit_body<X>(base, a, unit, tpl, 0, swap_smem, m); break;
+#define EA_U(X) case X: unit_body<X, false>(base, a, unit, tpl, 0, swap_smem, m); break;
         EA_U(4) EA_U(6) EA_U(8) EA_U(10) EA_U(12) EA_U(14) EA_U(16) EA_U(20) EA_U(24) EA_U(32)
 #undef EA_U
     default: break;
@@ -109,8 +109,8 @@ __device__ __forceinline__ void run_chunk(int L, int j_smem, uint32_t *base, con
     switch (L) {
 #define EA_C(X)                                                                          \
     case X:                                                                              \
-        if (j_smem) chunk_body<X, true>(base, a, unit, chunk, tpl, nlat);                \
-        else chunk_body<X, false>(base, a, unit, chunk, tpl, nlat);                      \
+        if (j_smem) chunk_body<X, true, false>(base, a, unit, chunk, tpl, nlat);         \
+        else chunk_body<X, false, false>(base, a, unit, chunk, tpl, nlat);               \
         break;
         EA_C(4) EA_C(6) EA_C(8) EA_C(10) EA_C(12) EA_C(14) EA_C(16) EA_C(20) EA_C(24) EA_C(32)
 #undef EA_C

@@ -21,10 +21,15 @@ namespace {
 // ensemble (m * NT <= 64), run in lockstep: slot l of the CTA is slot l % NT
 // of unit unit0 + l / NT.  Measurements and the cluster form need m = 1.
 
-template <int L>
+// MEAS = false compiles the body without the measurement, cluster and log
+// paths (launches that use none of them; cluster_measure must then be 0).
+template <int L, bool MEAS = true>
 __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, uint32_t unit0, int tpl,
-                                          int cluster_measure, int swap_in_smem, int m = 1)
+                                          int cluster_measure_arg, int swap_in_smem, int m = 1)
 {
+    const int cluster_measure = MEAS ? cluster_measure_arg : 0;
+    int32_t *const energy_log = MEAS ? a.energy_log : nullptr;
+    uint32_t *const swap_log = MEAS ? a.swap_log : nullptr;
     using Gm = Geo<L>;
     constexpr int N = Gm::N;
     const int NT = (int)a.NT;
@@ -70,8 +75,8 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
     for (uint32_t n = 0; n < a.n_sweeps; ++n) {
         const uint64_t s = a.s0 + n;
         const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
-        const bool meas = measured(s, a.measure_from, a.measure_every);
-        const bool needE = swap_now || a.energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
+        const bool meas = MEAS && measured(s, a.measure_from, a.measure_every);
+        const bool needE = swap_now || energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
         uint32_t acc[kPlanes];
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
@@ -143,11 +148,11 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
                 }
                 reinterpret_cast<uint2 *>(Su + (size_t)(NT - 1) * N)[w] = x;
             }
-            if (a.swap_log != nullptr)
+            if (swap_log != nullptr)
                 for (int i = tid; i < m * (NT - 1); i += nthr) {
                     const int ub = i / (NT - 1), p = i - ub * (NT - 1);
                     const uint32_t un = unit0 + (uint32_t)ub;
-                    a.swap_log[(((size_t)pass_local * a.G + un / a.C) * a.C + un % a.C) * (NT - 1) + p] =
+                    swap_log[(((size_t)pass_local * a.G + un / a.C) * a.C + un % a.C) * (NT - 1) + p] =
                         msk[i];
                 }
             __syncthreads();
@@ -156,13 +161,13 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
             ++P;
             ++pass_local;
         }
-        if (a.energy_log != nullptr) {
+        if (energy_log != nullptr) {
             const size_t row = (size_t)(s - a.log_s0);
             for (int i = tid; i < MT * kLanes; i += nthr) {
                 const int lf2 = i >> 5, b = i & 31;
                 const int ub = lf2 / NT, t = lf2 - ub * NT;
                 const uint32_t un = unit0 + (uint32_t)ub;
-                a.energy_log[(((row * a.G + un / a.C) * NT + t) * a.C + un % a.C) * kLanes + b] = E[i];
+                energy_log[(((row * a.G + un / a.C) * NT + t) * a.C + un % a.C) * kLanes + b] = E[i];
             }
         }
         if (meas) {
@@ -217,10 +222,13 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
 // lattices [t0, t0 + nlat) of one unit, runs the sweeps up to the next swap
 // point, and writes them back; the swap pass runs as its own kernels.
 
-template <int L, bool J_SMEM>
+// LOG = false compiles the body without the energy-log path (energy_log must
+// then be null).
+template <int L, bool J_SMEM, bool LOG = true>
 __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a, uint32_t unit,
                                            int chunk, int tpl, int nlat)
 {
+    int32_t *const energy_log = LOG ? a.energy_log : nullptr;
     using Gm = Geo<L>;
     constexpr int N = Gm::N;
     uint32_t *S = base;                                                   // [nlat][2][H]
@@ -256,7 +264,7 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
     for (uint32_t n = 0; n < a.n_sweeps; ++n) {
         const uint64_t s = a.s0 + n;
         const bool last = n + 1 == a.n_sweeps;
-        const bool needE = a.energy_log != nullptr || (last && a.compute_energy_last);
+        const bool needE = energy_log != nullptr || (last && a.compute_energy_last);
         uint32_t acc[kPlanes];
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
@@ -275,9 +283,9 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
             for (int i = tid; i < nl_here * kLanes; i += nthr) {
                 const int e = E[i];
                 const int t = tbase + (i >> 5), b = i & 31;
-                if (a.energy_log != nullptr) {
+                if (energy_log != nullptr) {
                     const size_t row = (size_t)(s - a.log_s0);
-                    a.energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = e;
+                    energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = e;
                 }
                 if (last) a.energy[((size_t)unit * NT + t) * kLanes + b] = e;
             }

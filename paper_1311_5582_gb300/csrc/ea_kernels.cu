@@ -7,22 +7,22 @@
 namespace ea {
 
 namespace {
-template <int L>
+template <int L, bool MEAS>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 k_sweep_unit(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure, int swap_in_smem)
 {
     extern __shared__ uint4 smem_u4[];
-    unit_body<L>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, tpl, cluster_measure,
-                 swap_in_smem);
+    unit_body<L, MEAS>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, tpl, cluster_measure,
+                       swap_in_smem);
 }
 
-template <int L, bool J_SMEM>
+template <int L, bool J_SMEM, bool LOG>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 k_sweep_chunk(const __grid_constant__ SweepLaunch a, int tpl, int nlat)
 {
     extern __shared__ uint4 smem_u4[];
-    chunk_body<L, J_SMEM>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, (int)blockIdx.y, tpl,
-                          nlat);
+    chunk_body<L, J_SMEM, LOG>(reinterpret_cast<uint32_t *>(smem_u4), a, blockIdx.x, (int)blockIdx.y,
+                               tpl, nlat);
 }
 
 // Swap decision of one pass for every unit: one CTA per unit.  Reads the
@@ -290,7 +290,9 @@ template <int L>
 cudaError_t launch_unit_L(const SweepLaunch &a, const Plan &plan, bool cluster_measure,
                           cudaStream_t st)
 {
-    auto kern = k_sweep_unit<L>;
+    // launches that measure and log nothing run the body compiled without those paths
+    const bool full = a.measure_every != 0 || a.energy_log != nullptr || a.swap_log != nullptr;
+    auto kern = full ? k_sweep_unit<L, true> : k_sweep_unit<L, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)plan.smem);
     if (e != cudaSuccess) return e;
@@ -319,14 +321,15 @@ cudaError_t launch_chunk_L(const SweepLaunch &a, const Plan &plan, cudaStream_t 
 {
     const int nchunks = ((int)a.NT + plan.lattices_per_cta - 1) / plan.lattices_per_cta;
     dim3 grid(a.G * a.C, nchunks);
+    const bool log = a.energy_log != nullptr;
     if (plan.j_in_smem) {
-        auto kern = k_sweep_chunk<L, true>;
+        auto kern = log ? k_sweep_chunk<L, true, true> : k_sweep_chunk<L, true, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)plan.smem);
         if (e != cudaSuccess) return e;
         kern<<<grid, plan.threads, plan.smem, st>>>(a, plan.threads_per_lattice, plan.lattices_per_cta);
     } else {
-        auto kern = k_sweep_chunk<L, false>;
+        auto kern = log ? k_sweep_chunk<L, false, true> : k_sweep_chunk<L, false, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)plan.smem);
         if (e != cudaSuccess) return e;
