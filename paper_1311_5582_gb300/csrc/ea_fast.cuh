@@ -327,6 +327,18 @@ __device__ __forceinline__ void warp_sum_to_lanes(const uint32_t (&acc)[PL], int
     out[lane] = (int)warp_transpose(x, lane);
 }
 
+// Named CTA barriers (ids 1..15; 0 is __syncthreads): the producer warp
+// arrives without waiting, the consumer warps wait until `count` threads have
+// arrived.  Both order the shared-memory accesses made before them.
+__device__ __forceinline__ void named_arrive(int id, int count)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // MEAS = false compiles the body without the measurement and log paths
 // (launches that measure and log nothing); the flags then must be 0 and the
 // log pointers null.
@@ -480,6 +492,17 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
         __syncthreads();
         if (swap_now) {
             const int *bnd = (P & 1) ? bnd1 : bnd0;
+            // Pipelined exchange (L = 8, 16 threads per lattice, at least 12 warps):
+            // warp 0 releases each batch of eight decided pairs through named
+            // barrier 1 + batch; warps 1..4 (two 8-byte columns of the lattices
+            // each) exchange that batch meanwhile; the remaining warps (at least
+            // seven: one item each) compute the next pass's bounds.  Every thread
+            // of warps 0..4 passes each of the batch barriers exactly once (160
+            // threads).
+            constexpr int kXW = 4;                     // exchange warps
+            bool pipe = false;
+            if constexpr (L == 8 && HP == 8) pipe = nthr >= 32 * (kXW + 8);
+            const int kPipeThreads = 32 * (kXW + 1);
             if (warp == 0) {
                 // Sequential pairs (0,1), (1,2), ... per realization lane.  The
                 // configuration carried upward has energy `cur`; pair p accepts iff
@@ -509,14 +532,54 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
                             if (lane == 0) msk[p] = m;
                         }
                     }
+                    if (pipe) {
+                        __syncwarp();
+                        named_arrive(1 + p0 / 8, kPipeThreads);   // masks of this batch are final
+                    }
                 }
                 E[(NT - 1) * kLanes + lane] = cur;
+            } else if (pipe && warp <= kXW) {
+                if constexpr (L == 8 && HP == 8) {
+                    constexpr int RW = N / 2;                     // 256 columns, two a thread
+                    constexpr int CW = 32 * kXW;                  // column stride between them
+                    const int w = tid - 32;
+                    const uint2 *src = reinterpret_cast<const uint2 *>(S) + w;
+                    uint2 *dst = reinterpret_cast<uint2 *>(S) + w;
+                    uint2 x0 = src[0], x1 = src[CW];
+                    for (int p0 = 0; p0 + 1 < NT; p0 += 8) {
+                        uint2 y0[8], y1[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const bool in = p0 + q + 1 < NT;
+                            y0[q] = in ? src[(size_t)(p0 + 1 + q) * RW] : make_uint2(0u, 0u);
+                            y1[q] = in ? src[(size_t)(p0 + 1 + q) * RW + CW] : make_uint2(0u, 0u);
+                        }
+                        named_sync(1 + p0 / 8, kPipeThreads);     // wait for this batch's masks
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            if (p0 + q + 1 < NT) {
+                                const uint32_t m = msk[p0 + q];
+                                const uint32_t a0 = (x0.x ^ y0[q].x) & m, b0 = (x0.y ^ y0[q].y) & m;
+                                const uint32_t a1 = (x1.x ^ y1[q].x) & m, b1 = (x1.y ^ y1[q].y) & m;
+                                dst[(size_t)(p0 + q) * RW] = make_uint2(x0.x ^ a0, x0.y ^ b0);
+                                dst[(size_t)(p0 + q) * RW + CW] = make_uint2(x1.x ^ a1, x1.y ^ b1);
+                                x0 = make_uint2(y0[q].x ^ a0, y0[q].y ^ b0);
+                                x1 = make_uint2(y1[q].x ^ a1, y1[q].y ^ b1);
+                            }
+                        }
+                    }
+                    dst[(size_t)(NT - 1) * RW] = x0;
+                    dst[(size_t)(NT - 1) * RW + CW] = x1;
+                }
+            } else if (pipe) {
+                if constexpr (L == 8 && HP == 8)
+                    bounds(P + 1, (P & 1) ? bnd0 : bnd1, tid - kPipeThreads, nthr - kPipeThreads);
             } else {
                 // meanwhile: bounds of the next pass (other buffer)
                 bounds(P + 1, (P & 1) ? bnd0 : bnd1, tid - 32, nthr - 32);
             }
             __syncthreads();
-            for (int w = tid; w < N / 2; w += nthr) {
+            for (int w = tid; !pipe && w < N / 2; w += nthr) {
                 // masked exchange chain; the words of eight slots are loaded before
                 // any of them is stored (slot rows never alias)
                 const uint2 *src = reinterpret_cast<const uint2 *>(S) + w;
