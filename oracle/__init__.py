@@ -26,6 +26,7 @@ _lib = None
 _u32p = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
 
 
 def build(src: str = _SRC, out: str = _LIB_PATH, extra_flags: tuple = ()) -> str:
@@ -47,6 +48,17 @@ def _bind(lib):
     lib.or_metro_table.restype = ctypes.c_int
     lib.or_swap_table.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, _u32p]
     lib.or_swap_table.restype = ctypes.c_int
+    lib.or_metro_table_field.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u64p]
+    lib.or_metro_table_field.restype = ctypes.c_int
+    lib.or_swap_table_field.argtypes = [_f64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        _u32p]
+    lib.or_swap_table_field.restype = ctypes.c_int
+    lib.or_field_step.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.or_field_step.restype = ctypes.c_int
+    lib.or_set_field.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    lib.or_set_field.restype = ctypes.c_int
+    lib.or_magnetisations.argtypes = [vp, _i32p]
+    lib.or_magnetisations.restype = None
     lib.or_create.argtypes = [ctypes.c_int] * 4 + [ctypes.c_uint64, _u32p, _u32p, _u32p, vp,
                                                   ctypes.c_int, ctypes.c_int]
     lib.or_create.restype = vp
@@ -123,13 +135,44 @@ def swap_table_trimmed(betas, n_sites: int) -> np.ndarray:
     return np.ascontiguousarray(full[:, :length])
 
 
+def metro_table_field(betas, h_num: int, h_den: int) -> np.ndarray:
+    """Field Metropolis table [NT][2][7] of 64-bit thresholds (2^32 = always)."""
+    betas = np.ascontiguousarray(betas, np.float64)
+    out = np.zeros((len(betas), 2, 7), np.uint64)
+    if load().or_metro_table_field(betas, len(betas), int(h_num), int(h_den), out) != 0:
+        raise ValueError("invalid temperatures or field")
+    return out
+
+
+def field_step(h_num: int, h_den: int) -> int:
+    """Step of differences of Et = h_den E - h_num M."""
+    return int(load().or_field_step(int(h_num), int(h_den)))
+
+
+def swap_table_field_trimmed(betas, n_sites: int, h_num: int, h_den: int) -> np.ndarray:
+    """Field swap table over k = 1..kmax (Et_p - Et_{p+1} = -k step), trailing zeros removed."""
+    betas = np.ascontiguousarray(betas, np.float64)
+    step = field_step(h_num, h_den)
+    kmax = (6 * n_sites * int(h_den) + 2 * n_sites * abs(int(h_num))) // step
+    out = np.zeros((max(len(betas) - 1, 0), kmax), np.uint32)
+    if load().or_swap_table_field(betas, len(betas), int(h_num), int(h_den), kmax, out) != 0:
+        raise ValueError("invalid temperatures or field")
+    if out.size == 0:
+        return out[:, :0]
+    nz = np.nonzero(out.any(axis=0))[0]
+    length = int(nz[-1]) + 1 if len(nz) else 0
+    return np.ascontiguousarray(out[:, :length])
+
+
 class OracleSim:
     """Scalar simulation state; mirrors the product's create/sweep/swap/measure calls."""
 
-    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, group_base=0):
+    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, group_base=0, field=None):
         """group_base: global index of the first group passed (the random-number
         counters use global group indices, so a subset of groups reproduces the
-        same trajectories as the full ensemble)."""
+        same trajectories as the full ensemble).  field: (h_num, h_den, metro_f)
+        with metro_f from metro_table_field and swapt from swap_table_field_trimmed
+        (metro is then unused)."""
         self.lib = load()
         self.L, self.G, self.NT, self.C = int(L), int(G), int(NT), int(C)
         self.N = self.L ** 3
@@ -147,6 +190,12 @@ class OracleSim:
                                     swap_len, int(group_base))
         if not self.h:
             raise ValueError("oracle rejected the configuration")
+        if field is not None:
+            h_num, h_den, metro_f = field
+            self._metro_f = np.ascontiguousarray(metro_f, np.uint64)
+            if self.lib.or_set_field(self.h, int(h_num), int(h_den),
+                                     self._metro_f.ctypes.data if int(h_num) else None) != 0:
+                raise ValueError("oracle rejected the field")
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -200,6 +249,11 @@ class OracleSim:
     def energies(self) -> np.ndarray:
         out = np.zeros((self.G, self.NT, self.C, 32), np.int32)
         self.lib.or_energies(self.h, out)
+        return out
+
+    def magnetisations(self) -> np.ndarray:
+        out = np.zeros((self.G, self.NT, self.C, 32), np.int32)
+        self.lib.or_magnetisations(self.h, out)
         return out
 
     def energies_recomputed(self) -> np.ndarray:

@@ -25,6 +25,14 @@
  *    Accepted swaps exchange the configurations between temperature slots
  *    (the paper swaps probability-table rows, Sec. 4.3.1; here each slot keeps
  *    a label of the stored configuration it currently holds).
+ *  - External field (Eq. 1 with h != 0, the paper's field runs of Sec. 5):
+ *        H = - sum J S S' - h sum_i S_i,  h = h_num / h_den rational,
+ *    tracked exactly as Et = h_den * E_bond - h_num * M (M = sum_i S_i).  A flip
+ *    of S changes Et by h_den (12 - 4u) + 2 h_num S (u = unsatisfied bonds):
+ *    accepted iff that is <= 0 or r < metro_f[t][S>0][u] (a 64-bit threshold,
+ *    2^32 = always).  Swaps compare Et_p - Et_{p+1}, a multiple of
+ *    step = gcd(4 h_den, 2 |h_num|), with swapt[p][k-1] for Et_p - Et_{p+1} =
+ *    -k step.  h_num = 0, h_den = 1 is exactly the field-free method.
  *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11; the generator family
  *    the paper evaluates in Sec. 4.3.2), one 32-bit output per
  *    (word-group, temperature slot, copy, sweep, site), shared by the 32
@@ -124,6 +132,53 @@ int or_swap_table(const double *beta, int nt, int len, uint32_t *swapt)
     return 0;
 }
 
+/* Field tables (see the header).  metro_f[t][sp][u], sp = 1 for S = +1, is
+ * floor(exp(-beta dE) 2^32) for dE = 12 - 4u + 2 h S > 0 (clamped below 2^32),
+ * and 2^32 (always) for dE <= 0.  Returns 0, or -1 for beta < 0 or h_den < 1. */
+int or_metro_table_field(const double *beta, int nt, int h_num, int h_den, uint64_t *metro_f)
+{
+    if (h_den < 1) return -1;
+    const double h = (double)h_num / (double)h_den;
+    for (int t = 0; t < nt; ++t) {
+        if (!(beta[t] >= 0.0)) return -1;
+        for (int sp = 0; sp < 2; ++sp)
+            for (int u = 0; u <= 6; ++u) {
+                const int S = sp ? 1 : -1;
+                const long long dEt = (long long)h_den * (12 - 4 * u) + 2LL * h_num * S;
+                uint64_t v = 4294967296ull;
+                if (dEt > 0) v = or_prob_to_u32(exp(-beta[t] * (12.0 - 4.0 * u + 2.0 * h * S)));
+                metro_f[((size_t)t * 2 + sp) * 7 + u] = v;
+            }
+    }
+    return 0;
+}
+
+static int or_gcd(int a, int b)
+{
+    if (a < 0) a = -a;
+    if (b < 0) b = -b;
+    while (b) { int t = a % b; a = b; b = t; }
+    return a;
+}
+
+/* Step of Et differences: gcd(4 h_den, 2 |h_num|). */
+int or_field_step(int h_num, int h_den) { return or_gcd(4 * h_den, 2 * h_num); }
+
+/* swapt[p][k-1] = floor(exp(-(beta_p - beta_{p+1}) k step / h_den) 2^32), the
+ * threshold for Et_p - Et_{p+1} = -k step.  Returns 0 or -1. */
+int or_swap_table_field(const double *beta, int nt, int h_num, int h_den, int len, uint32_t *swapt)
+{
+    if (h_den < 1) return -1;
+    const double step = (double)or_field_step(h_num, h_den);
+    for (int p = 0; p + 1 < nt; ++p) {
+        double db = beta[p] - beta[p + 1];
+        if (!(db >= 0.0)) return -1;
+        for (int k = 1; k <= len; ++k)
+            swapt[(size_t)p * len + (k - 1)] = or_prob_to_u32(exp(-db * step * k / h_den));
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------ simulation */
 
 typedef struct {
@@ -139,6 +194,9 @@ typedef struct {
     int64_t *E;      /* [G][C][32][NT]     energy of stored configuration r */
     uint32_t *metro; /* [NT][3] */
     uint32_t *swapt; /* [NT-1][swap_len] */
+    int h_num, h_den, step;  /* field h = h_num / h_den; step of Et differences */
+    uint64_t *metro_f;       /* [NT][2][7] when h_num != 0, else NULL */
+    int64_t *M;      /* [G][C][32][NT]     magnetisation of stored configuration r */
     uint64_t sweep;  /* global sweep index s of the next sweep */
     uint64_t pass;   /* global index P of the next swap pass */
 } or_sim;
@@ -158,6 +216,10 @@ static int *lab(const or_sim *m, int g, int c, int b)
 static int64_t *en(const or_sim *m, int g, int c, int b)
 {
     return m->E + (((size_t)g * m->C + c) * OR_LANES + b) * m->NT;
+}
+static int64_t *mg(const or_sim *m, int g, int c, int b)
+{
+    return m->M + (((size_t)g * m->C + c) * OR_LANES + b) * m->NT;
 }
 
 /* Site index of (x, y, z) with periodic wrap. */
@@ -213,6 +275,7 @@ void or_destroy(or_sim *m)
 {
     if (!m) return;
     free(m->sigma); free(m->J); free(m->label); free(m->E); free(m->metro); free(m->swapt);
+    free(m->metro_f); free(m->M);
     free(m->nbr); free(m->colour);
     free(m);
 }
@@ -234,11 +297,13 @@ or_sim *or_create(int L, int G, int NT, int C, uint64_t seed,
     m->J = (int8_t *)malloc((size_t)G * OR_LANES * 3 * N);
     m->label = (int *)malloc(sizeof(int) * (size_t)G * C * OR_LANES * NT);
     m->E = (int64_t *)malloc(sizeof(int64_t) * (size_t)G * C * OR_LANES * NT);
+    m->M = (int64_t *)malloc(sizeof(int64_t) * (size_t)G * C * OR_LANES * NT);
+    m->h_num = 0; m->h_den = 1; m->step = 4; m->metro_f = NULL;
     m->metro = (uint32_t *)malloc(sizeof(uint32_t) * 3 * (size_t)NT);
     m->nbr = (int *)malloc(sizeof(int) * 6 * N);
     m->colour = (int8_t *)malloc(N);
     m->swapt = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)(NT > 1 ? NT - 1 : 0) * swap_len + 1));
-    if (!m->sigma || !m->J || !m->label || !m->E || !m->metro || !m->swapt || !m->nbr ||
+    if (!m->sigma || !m->J || !m->label || !m->E || !m->M || !m->metro || !m->swapt || !m->nbr ||
         !m->colour) {
         or_destroy(m);
         return NULL;
@@ -271,10 +336,39 @@ or_sim *or_create(int L, int G, int NT, int C, uint64_t seed,
                     }
                     lab(m, g, c, b)[t] = t;
                     en(m, g, c, b)[t] = or_config_energy(m, s, g, b);
+                    int64_t mm = 0;
+                    for (size_t i = 0; i < N; ++i) mm += s[i];
+                    mg(m, g, c, b)[t] = mm;
                 }
     return m;
 }
 
+
+/* Switches on the external field h = h_num / h_den with its Metropolis table
+ * metro_f [NT][2][7] (or_metro_table_field) and the swap table given at
+ * creation (built by or_swap_table_field for the same h).  Returns 0, or -1
+ * for h_den < 1 or a missing table. */
+int or_set_field(or_sim *m, int h_num, int h_den, const uint64_t *metro_f)
+{
+    if (h_den < 1 || (h_num != 0 && !metro_f)) return -1;
+    m->h_num = h_num;
+    m->h_den = h_den;
+    m->step = or_field_step(h_num, h_den);
+    free(m->metro_f);
+    m->metro_f = NULL;
+    if (h_num != 0) {
+        m->metro_f = (uint64_t *)malloc(sizeof(uint64_t) * 14 * (size_t)m->NT);
+        if (!m->metro_f) return -1;
+        memcpy(m->metro_f, metro_f, sizeof(uint64_t) * 14 * (size_t)m->NT);
+    }
+    return 0;
+}
+
+/* Et = h_den E - h_num M of stored configuration r. */
+static int64_t et_of(const or_sim *m, int g, int c, int b, int r)
+{
+    return (int64_t)m->h_den * en(m, g, c, b)[r] - (int64_t)m->h_num * mg(m, g, c, b)[r];
+}
 
 /* One checkerboard sweep of the configuration held by slot t of (g, c), all
  * 32 realizations, global sweep index s (Sec. 2.3, Sec. 3.1). */
@@ -292,9 +386,17 @@ static void sweep_slot(or_sim *m, int g, int c, int t, uint64_t s)
                 int8_t *sp = sig(m, g, c, b, rr);
                 int dE = 2 * sp[i] * local_field(m, sp, g, b, i);
                 int accept;
-                if (dE <= 0) accept = 1;
-                else accept = r < m->metro[t * 3 + (12 - dE) / 4];
+                if (m->h_num == 0) {
+                    if (dE <= 0) accept = 1;
+                    else accept = r < m->metro[t * 3 + (12 - dE) / 4];
+                } else {
+                    /* Et changes by h_den dE - h_num (M' - M) = h_den dE + 2 h_num S */
+                    const long long dEt = (long long)m->h_den * dE + 2LL * m->h_num * sp[i];
+                    if (dEt <= 0) accept = 1;
+                    else accept = (uint64_t)r < m->metro_f[((size_t)t * 2 + (sp[i] > 0)) * 7 + (12 - dE) / 4];
+                }
                 if (accept) {
+                    mg(m, g, c, b)[rr] -= 2 * sp[i];
                     sp[i] = (int8_t)-sp[i];
                     en(m, g, c, b)[rr] += dE;
                 }
@@ -312,7 +414,8 @@ static void swap_pass(or_sim *m, int g, int c, uint64_t P, uint32_t *mask)
         int *l = lab(m, g, c, b);
         int64_t *e = en(m, g, c, b);
         for (int p = 0; p + 1 < m->NT; ++p) {
-            int64_t delta = e[l[p]] - e[l[p + 1]];
+            int64_t delta = m->h_num == 0 ? e[l[p]] - e[l[p + 1]]
+                                          : et_of(m, g, c, b, l[p]) - et_of(m, g, c, b, l[p + 1]);
             uint32_t r = or_uniform(m->seed, ((uint32_t)p << 3) | ((uint32_t)b >> 2),
                                     (1u << 24) | ((uint32_t)c << 8), (uint32_t)P,
                                     (uint32_t)(m->group_base + g), b & 3);
@@ -320,7 +423,7 @@ static void swap_pass(or_sim *m, int g, int c, uint64_t P, uint32_t *mask)
             if (delta >= 0) {
                 accept = 1;
             } else {
-                int64_t k = -delta / 4;
+                int64_t k = -delta / m->step;
                 accept = (k <= m->swap_len) && (r < m->swapt[(size_t)p * m->swap_len + (k - 1)]);
             }
             if (accept) {
@@ -389,9 +492,13 @@ static void *or_worker(void *arg)
             if (w->check) {
                 for (int c = 0; c < C; ++c)
                     for (int b = 0; b < OR_LANES; ++b)
-                        for (int r = 0; r < NT; ++r)
-                            if (or_config_energy(m, sig(m, g, c, b, r), g, b) != en(m, g, c, b)[r])
-                                w->failed = 1;
+                        for (int r = 0; r < NT; ++r) {
+                            const int8_t *sr = sig(m, g, c, b, r);
+                            if (or_config_energy(m, sr, g, b) != en(m, g, c, b)[r]) w->failed = 1;
+                            int64_t mm = 0;
+                            for (int i = 0; i < m->N; ++i) mm += sr[i];
+                            if (mm != mg(m, g, c, b)[r]) w->failed = 1;
+                        }
             }
             if (w->energy_log)
                 for (int t = 0; t < NT; ++t)
@@ -514,6 +621,17 @@ void or_energies_recompute(const or_sim *m, int32_t *out)
                 for (int b = 0; b < OR_LANES; ++b)
                     out[(((size_t)g * m->NT + t) * m->C + c) * OR_LANES + b] = (int32_t)
                         or_config_energy(m, sig(m, g, c, b, lab(m, g, c, b)[t]), g, b);
+}
+
+/* Magnetisations M = sum_i S_i by slot: out [G][NT][C][32]. */
+void or_magnetisations(const or_sim *m, int32_t *out)
+{
+    for (int g = 0; g < m->G; ++g)
+        for (int t = 0; t < m->NT; ++t)
+            for (int c = 0; c < m->C; ++c)
+                for (int b = 0; b < OR_LANES; ++b)
+                    out[(((size_t)g * m->NT + t) * m->C + c) * OR_LANES + b] =
+                        (int32_t)mg(m, g, c, b)[lab(m, g, c, b)[t]];
 }
 
 /* Overlap counts n_diff by slot: out [G][NT][32] (requires C == 2). */

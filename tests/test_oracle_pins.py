@@ -412,7 +412,8 @@ MUTANTS = {
     "dE_sign": ("int dE = 2 * sp[i] * local_field(m, sp, g, b, i);",
                 "int dE = -2 * sp[i] * local_field(m, sp, g, b, i);"),
     "threshold_index": ("m->metro[t * 3 + (12 - dE) / 4]", "m->metro[t * 3 + 2 - (12 - dE) / 4]"),
-    "swap_sign": ("int64_t delta = e[l[p]] - e[l[p + 1]];", "int64_t delta = e[l[p + 1]] - e[l[p]];"),
+    "swap_sign": ("int64_t delta = m->h_num == 0 ? e[l[p]] - e[l[p + 1]]",
+                  "int64_t delta = m->h_num == 0 ? e[l[p + 1]] - e[l[p]]"),
     "minus_bond_J": ("h += jb(m, g, b, d)[im] * s[im];", "h += jb(m, g, b, d)[i] * s[im];"),
     "colour_order": ("for (int colour = 0; colour < 2; ++colour) {",
                      "for (int colour = 1; colour >= 0; --colour) {"),
