@@ -353,7 +353,8 @@ int or_set_field(or_sim *m, int h_num, int h_den, const uint64_t *metro_f)
     if (h_den < 1 || (h_num != 0 && !metro_f)) return -1;
     m->h_num = h_num;
     m->h_den = h_den;
-    m->step = or_field_step(h_num, h_den);
+    /* with h_num = 0 the method is the field-free one: decisions on E, step 4 */
+    m->step = h_num == 0 ? 4 : or_field_step(h_num, h_den);
     free(m->metro_f);
     m->metro_f = NULL;
     if (h_num != 0) {

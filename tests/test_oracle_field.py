@@ -72,9 +72,12 @@ def test_zero_field_tables_reduce_to_the_field_free_ones():
                                   oracle.swap_table_trimmed(betas, 64))
 
 
-def test_zero_field_trajectory_equals_the_field_free_oracle():
+@pytest.mark.parametrize("h_den", [1, 3])
+def test_zero_field_trajectory_equals_the_field_free_oracle(h_den):
+    """h = 0 / h_den is no field whatever h_den: Et = h_den E, whose differences
+    are multiples of 4 h_den, so the swap index is still (E_{p+1} - E_p) / 4."""
     inst, inp = inputs(4, 2, 6, 2, 41, 42)
-    sim_f, _, _ = field_sim(inst, inp, 0, 1)
+    sim_f, _, _ = field_sim(inst, inp, 0, h_den)
     sim_0 = oracle.OracleSim(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
                              oracle.metro_table(inp["betas"]),
                              oracle.swap_table_trimmed(inp["betas"], inst.N))
