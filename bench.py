@@ -344,6 +344,56 @@ def bench_large(ea, torch, peak_tops, sweeps=200):
     return out
 
 
+def bench_field(ea, torch, sweeps=200, h=(1, 2)):
+    """The headline ensemble in the external field h = h_num / h_den (Eq. 1 with
+    h != 0; generic unit and chunked kernels), autotuned and timed like the
+    headline from warm state with L2 flushed, beside the same ensemble at h = 0
+    restricted to the same generic plans (the cost of the field itself)."""
+    wl = workload("scale", sweeps)
+    inst = wl["inst"]
+    inp = W.draw_inputs(inst)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def timed(ens):
+        ens.sweep(wl["sweeps"], wl["swap_every"])            # warm
+        flush.fill_(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ens.launches
+        a.record()
+        ens.sweep(wl["sweeps"], wl["swap_every"])
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3 / wl["flips"] * 1e12, ens.launches - l0
+
+    def plan_text(ens):
+        p = ens.plans()[ens.plan]
+        return f"{p['form']} t{p['threads']} g{p['group_threads']} n{p['lattices_per_cta']}"
+
+    mf, sw = ea.ea_build_tables_field(inp["betas"], inst.N, *h)
+    ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], None, sw,
+                      field=(h[0], h[1], mf))
+    ens.autotune(probe_sweeps=60, swap_every=wl["swap_every"])
+    v_field, launches = timed(ens)
+    out = {"workload": wl["name"] + f", field h = {h[0]}/{h[1]}", "value": v_field, "unit": UNIT,
+           "plan": plan_text(ens), "gpu_launches": launches}
+    ens.close()
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
+    best = None
+    for i, p in enumerate(ens.plans()):
+        if p["form"] == "unit-fast":
+            continue
+        ens.select_plan(i)
+        v, _ = timed(ens)
+        if best is None or v < best[0]:
+            best = (v, plan_text(ens))
+    ens.close()
+    if best is not None:
+        out["h0_same_kernel_family"] = {"value": best[0], "unit": UNIT, "plan": best[1]}
+        out["field_cost"] = v_field / best[0]
+    return out
+
+
 def bench_served(ea, n_requests=32, round_ms=20, load=None, rate_flips_s=None):
     """Poisson-arriving requests (200/s) replayed in real time through the server,
     against serving them one at a time with plain launches (arrival order); the
@@ -615,6 +665,7 @@ def main():
             line["with_measurement"] = with_meas
         if world == 1 and not args.no_extras:
             line["large"] = bench_large(ea, torch, peak_tops)
+            line["field"] = bench_field(ea, torch)
             line["batched"] = bench_batched(ea, torch)
             line["served"] = bench_served(ea, args.served_requests)
             line["served_load70"] = bench_served(ea, 16, load=0.7,

@@ -116,6 +116,47 @@ int ea_create(const ea_config *cfg, void *stream, ea_ctx **out);
 /* Frees the context's device memory after its stream has drained.  NULL is a no-op. */
 void ea_destroy(ea_ctx *ctx);
 
+/* External field h = h_num / h_den: the Hamiltonian of Eq. 1 with the term
+ * -h sum_i S_i (the field runs of Sec. 5).  With M = sum_i S_i, the method
+ * works on Et = h_den (E - h M) = h_den E - h_num M, an integer:
+ *   Metropolis: a flip of spin S with u unsatisfied bonds changes Et by
+ *     h_den (12 - 4u) + 2 h_num S; it is accepted iff r < metro[t][S > 0][u]
+ *     (uint64; 2^32 = always, the value where that change is <= 0).
+ *   Swap pass: Et differences are multiples of step = gcd(4 h_den, 2|h_num|);
+ *     pair p is accepted iff Et_p - Et_{p+1} >= 0 or r < swapt[p][k-1],
+ *     k = (Et_{p+1} - Et_p) / step <= swap_len (cfg->swapt, cfg->swap_len
+ *     are read in these units; cfg->metro is ignored and may be NULL).
+ * Energies reported by the library stay E (bonds only, Eq. 1 at h = 0); the
+ * field term is -h M with M from ea_magnetisations.  Requires h_den >= 1 and
+ * (3 h_den + |h_num|) < 2^15 (Et differences fit int32 for N <= 32768).
+ * h_num == 0 gives exactly the field-free method (metro[t][sp][u] must then
+ * equal the field-free table for u < 3 and 2^32 above). */
+typedef struct {
+    int32_t h_num;
+    int32_t h_den;
+    const uint64_t *metro;    /* host [NT][2][7], each [t][sp] row non-decreasing in u, <= 2^32 */
+} ea_field;
+
+/* Field tables in FP64 (Sec. 4.3.1, 4.3.2 with the field term):
+ * metro_out[t][sp][u] = floor(exp(-beta_t (12 - 4u + 2 h S)) 2^32) (clamped
+ * below 2^32) where that energy change is > 0, else 2^32; S = +1 for sp = 1.
+ * swap columns k = 1..(6N h_den + 2N |h_num|) / step hold
+ * floor(exp(-(beta_p - beta_{p+1}) k step / h_den) 2^32) with trailing zero
+ * columns dropped; *swap_len_out, swap_cap and swap_out as ea_build_tables.
+ * Host-only. */
+int ea_build_tables_field(const double *beta, uint32_t n_temps, uint32_t n_sites, int32_t h_num,
+                          int32_t h_den, uint64_t *metro_out, uint32_t *swap_out, uint32_t swap_cap,
+                          uint32_t *swap_len_out);
+
+/* ea_create in the field `field` (NULL: none, as ea_create).  Contexts with a
+ * field run the generic unit and chunked kernel forms; batches and the server
+ * do not take them (EA_EINVAL). */
+int ea_create_field(const ea_config *cfg, const ea_field *field, void *stream, ea_ctx **out);
+
+/* Magnetisations M = sum_i S_i of every lattice by slot, recomputed from the
+ * spins: DEVICE int32 [G][NT][C][32].  Any context.  Asynchronous. */
+int ea_magnetisations(ea_ctx *ctx, int32_t *out);
+
 /* Runs args->n_sweeps checkerboard sweeps with the swap passes and
  * measurements the arguments ask for; asynchronous on the context's stream. */
 int ea_sweep(ea_ctx *ctx, const ea_sweep_args *args);

@@ -72,9 +72,14 @@ class _PlanDesc(ctypes.Structure):
                 ("smem_bytes", ctypes.c_uint64), ("units_per_cta", ctypes.c_int32)]
 
 
+class _Field(ctypes.Structure):
+    _fields_ = [("h_num", ctypes.c_int32), ("h_den", ctypes.c_int32), ("metro", ctypes.c_void_p)]
+
+
 PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked"}
 
-EXPORTS = ["ea_build_tables", "ea_supported_L", "ea_create", "ea_destroy", "ea_sweep",
+EXPORTS = ["ea_build_tables", "ea_build_tables_field", "ea_supported_L", "ea_create",
+           "ea_create_field", "ea_magnetisations", "ea_destroy", "ea_sweep",
            "ea_pt_swap", "ea_measure", "ea_measure_planes", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
            "ea_get_counters", "ea_sync", "ea_launch_count", "ea_plan_count", "ea_plan_current",
            "ea_plan_info", "ea_plan_select", "ea_autotune", "ea_batch_create", "ea_batch_add",
@@ -105,6 +110,11 @@ def load_library(path: str | None = None):
     lib.ea_build_tables.argtypes = [vp, u32, u32, vp, vp, u32, ctypes.POINTER(u32)]
     lib.ea_supported_L.argtypes = [u32]
     lib.ea_create.argtypes = [ctypes.POINTER(_Config), vp, ctypes.POINTER(vp)]
+    lib.ea_build_tables_field.argtypes = [vp, u32, u32, ctypes.c_int32, ctypes.c_int32, vp, vp, u32,
+                                          ctypes.POINTER(u32)]
+    lib.ea_create_field.argtypes = [ctypes.POINTER(_Config), ctypes.POINTER(_Field), vp,
+                                    ctypes.POINTER(vp)]
+    lib.ea_magnetisations.argtypes = [vp, vp]
     lib.ea_destroy.argtypes = [vp]
     lib.ea_destroy.restype = None
     lib.ea_sweep.argtypes = [vp, ctypes.POINTER(_SweepArgs)]
@@ -153,7 +163,8 @@ def load_library(path: str | None = None):
     lib.ea_server_destroy.restype = None
     lib.ea_strerror.argtypes = [i32]
     lib.ea_strerror.restype = ctypes.c_char_p
-    for name in ("ea_build_tables", "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
+    for name in ("ea_build_tables", "ea_build_tables_field", "ea_create_field", "ea_magnetisations",
+                 "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
                  "ea_measure_planes",
                  "ea_measure", "ea_read_spins", "ea_read_spins_host", "ea_write_spins",
                  "ea_get_counters", "ea_sync", "ea_run", "ea_plan_count", "ea_plan_current",
@@ -208,16 +219,36 @@ def ea_build_tables(betas, n_sites: int):
     return metro, swapt
 
 
+def ea_build_tables_field(betas, n_sites: int, h_num: int, h_den: int):
+    """Field tables for h = h_num / h_den: metro [NT][2][7] uint64 (2^32 = always) and
+    swapt [NT-1][swap_len] uint32 in steps of gcd(4 h_den, 2 |h_num|) of Et."""
+    lib = load_library()
+    betas = np.ascontiguousarray(betas, np.float64)
+    nt = len(betas)
+    metro = np.zeros((nt, 2, 7), np.uint64)
+    ln = ctypes.c_uint32(0)
+    _check(lib.ea_build_tables_field(betas.ctypes.data, nt, n_sites, int(h_num), int(h_den),
+                                     metro.ctypes.data, None, 0, ctypes.byref(ln)), "ea_build_tables_field")
+    swapt = np.zeros((max(nt - 1, 0), ln.value), np.uint32)
+    if swapt.size:
+        _check(lib.ea_build_tables_field(betas.ctypes.data, nt, n_sites, int(h_num), int(h_den), None,
+                                         swapt.ctypes.data, ln.value, ctypes.byref(ln)),
+               "ea_build_tables_field")
+    return metro, swapt
+
+
 def ea_supported_L(L: int) -> bool:
     return bool(load_library().ea_supported_L(L))
 
 
 def _config(L, G, NT, C, seed, bonds, spins, metro, swapt):
+    if metro is None:   # field ensembles: the field carries the Metropolis table
+        metro = np.zeros((0, 3), np.uint32)
     keep = [np.ascontiguousarray(a, np.uint32) for a in (bonds, spins, metro, swapt)]
     b, s, m, w = keep
     N = L ** 3
-    assert b.shape == (G, 3, N) and s.shape == (G, NT, C, N) and m.shape == (NT, 3)
-    cfg = _Config(L, G, NT, C, int(seed), b.ctypes.data, s.ctypes.data, m.ctypes.data,
+    assert b.shape == (G, 3, N) and s.shape == (G, NT, C, N) and m.shape in ((NT, 3), (0, 3))
+    cfg = _Config(L, G, NT, C, int(seed), b.ctypes.data, s.ctypes.data, m.ctypes.data if m.size else None,
                   w.ctypes.data if w.size else None, w.shape[1] if w.ndim == 2 else 0)
     return cfg, keep
 
@@ -230,9 +261,12 @@ def _stream_handle(stream):
 
 
 class Ensemble:
-    """One simulated ensemble (an ea_ctx): G word-groups x NT slots x C copies of an L^3 lattice."""
+    """One simulated ensemble (an ea_ctx): G word-groups x NT slots x C copies of an L^3 lattice.
 
-    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, stream=None):
+    field=(h_num, h_den, metro_field) runs it in the external field h = h_num / h_den
+    (ea_create_field); metro is then unused and swapt is the field swap table."""
+
+    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, stream=None, field=None):
         import torch
         self.lib = load_library()
         self.L, self.G, self.NT, self.C = int(L), int(G), int(NT), int(C)
@@ -242,7 +276,15 @@ class Ensemble:
         cfg, _keep = _config(self.L, self.G, self.NT, self.C, seed, bonds, spins, metro, swapt)
         self.swap_len = cfg.swap_len
         h = ctypes.c_void_p(None)
-        _check(self.lib.ea_create(ctypes.byref(cfg), self.handle, ctypes.byref(h)), "ea_create")
+        if field is None:
+            _check(self.lib.ea_create(ctypes.byref(cfg), self.handle, ctypes.byref(h)), "ea_create")
+        else:
+            h_num, h_den, mf = field
+            mf = np.ascontiguousarray(mf, np.uint64)
+            assert mf.shape == (self.NT, 2, 7)
+            fld = _Field(int(h_num), int(h_den), mf.ctypes.data)
+            _check(self.lib.ea_create_field(ctypes.byref(cfg), ctypes.byref(fld), self.handle,
+                                            ctypes.byref(h)), "ea_create_field")
         self.ctx = h
 
     def close(self):
@@ -325,6 +367,13 @@ class Ensemble:
                  else (self.G, self.NT, self.C, 3, self.L, 32))
         out = self._empty(shape, torch.int32)
         _check(self.lib.ea_measure_planes(self.ctx, int(mode), _ptr(out)), "ea_measure_planes")
+        return out
+
+    def magnetisations(self):
+        """M = sum_i S_i of every lattice by slot (ea_magnetisations): int32 [G][NT][C][32]."""
+        import torch
+        out = self._empty((self.G, self.NT, self.C, 32), torch.int32)
+        _check(self.lib.ea_magnetisations(self.ctx, _ptr(out)), "ea_magnetisations")
         return out
 
     def read_spins(self, out=None):

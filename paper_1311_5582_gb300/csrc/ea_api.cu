@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <numeric>
 #include <new>
 #include <vector>
 
@@ -41,7 +42,7 @@ bool measured(uint64_t s, uint64_t from, uint32_t every)
 
 int validate_tables(const uint32_t *metro, const uint32_t *swapt, uint32_t NT, uint32_t len)
 {
-    for (uint32_t t = 0; t < NT; ++t)
+    for (uint32_t t = 0; metro && t < NT; ++t)
         if (metro[t * 3] > metro[t * 3 + 1] || metro[t * 3 + 1] > metro[t * 3 + 2]) return EA_EINVAL;
     if (NT > 1 && len > 0) {
         if (!swapt) return EA_EINVAL;
@@ -67,6 +68,11 @@ ea::SweepLaunch base_launch(ea_ctx *c)
     a.C = c->C;
     a.rk = c->rk;
     a.err = c->d_err;
+    a.metro_f = c->d_metro_f;
+    a.mag = c->d_mag;
+    a.h_num = c->h_num;
+    a.h_den = c->h_den;
+    a.step = c->step;
     return a;
 }
 
@@ -95,6 +101,8 @@ void free_ctx(ea_ctx *c, cudaStream_t st)
     ctx_free(c, c->d_masks, st);
     ctx_free(c, c->d_energy, st);
     ctx_free(c, c->d_err, st);
+    ctx_free(c, c->d_metro_f, st);
+    ctx_free(c, c->d_mag, st);
     delete c;
 }
 
@@ -169,9 +177,61 @@ int ea_build_tables(const double *beta, uint32_t n_temps, uint32_t n_sites, uint
     return EA_OK;
 }
 
+int ea_build_tables_field(const double *beta, uint32_t n_temps, uint32_t n_sites, int32_t h_num,
+                          int32_t h_den, uint64_t *metro_out, uint32_t *swap_out, uint32_t swap_cap,
+                          uint32_t *swap_len_out)
+{
+    if (!beta || n_temps == 0 || n_sites == 0 || !swap_len_out || h_den < 1) return EA_EINVAL;
+    if (3LL * h_den + std::llabs((long long)h_num) >= (1LL << 15)) return EA_EINVAL;
+    for (uint32_t t = 0; t < n_temps; ++t) {
+        if (!(beta[t] >= 0.0) || !std::isfinite(beta[t])) return EA_EINVAL;
+        if (t > 0 && !(beta[t] <= beta[t - 1])) return EA_EINVAL;
+    }
+    const double h = (double)h_num / (double)h_den;
+    if (metro_out)
+        for (uint32_t t = 0; t < n_temps; ++t)
+            for (int sp = 0; sp < 2; ++sp) {
+                const int S = sp ? 1 : -1;
+                for (int u = 0; u < 7; ++u) {
+                    // the change of Et = h_den E - h_num M; accepted always where <= 0
+                    const long long d = (long long)h_den * (12 - 4 * u) + 2LL * h_num * S;
+                    metro_out[((size_t)t * 2 + sp) * 7 + u] =
+                        d <= 0 ? (1ull << 32)
+                               : prob_to_u32(std::exp(-beta[t] * (12.0 - 4.0 * u + 2.0 * h * S)));
+                }
+            }
+    const long long step = std::gcd(4LL * h_den, 2LL * std::llabs((long long)h_num));
+    const uint64_t kmax = (uint64_t)((6LL * n_sites * h_den + 2LL * n_sites * std::llabs((long long)h_num)) / step);
+    const double stepd = (double)step;
+    uint64_t len = 0;
+    for (uint32_t p = 0; p + 1 < n_temps; ++p) {
+        const double db = beta[p] - beta[p + 1];
+        uint64_t lo = 0, hi = kmax;   // entry lo non-zero (lo = 0: none known); entries decrease in k
+        while (lo < hi) {
+            const uint64_t mid = lo + (hi - lo + 1) / 2;
+            if (prob_to_u32(std::exp(-db * stepd * (double)mid / h_den)) != 0) lo = mid; else hi = mid - 1;
+        }
+        if (lo > len) len = lo;
+    }
+    if (len > 0xFFFFFFFFull) return EA_EINVAL;
+    *swap_len_out = (uint32_t)len;
+    if (swap_out && swap_cap >= len && len > 0)
+        for (uint32_t p = 0; p + 1 < n_temps; ++p) {
+            const double db = beta[p] - beta[p + 1];
+            for (uint64_t k = 1; k <= len; ++k)
+                swap_out[(size_t)p * swap_cap + (k - 1)] = prob_to_u32(std::exp(-db * stepd * (double)k / h_den));
+        }
+    return EA_OK;
+}
+
 int ea_create(const ea_config *cfg, void *stream, ea_ctx **out)
 {
     return ea::create_ctx(cfg, (cudaStream_t)stream, nullptr, out);
+}
+
+int ea_create_field(const ea_config *cfg, const ea_field *field, void *stream, ea_ctx **out)
+{
+    return ea::create_ctx(cfg, (cudaStream_t)stream, nullptr, out, field);
 }
 
 void ea_destroy(ea_ctx *ctx)
@@ -185,17 +245,57 @@ void ea_destroy(ea_ctx *ctx)
 
 namespace ea {
 
-int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea_ctx **out)
+// Checks a field's tables.  h_num == 0: the field-free method; its
+// thresholds are written to metro0 [NT][3].
+int validate_field(const ea_field *f, uint32_t NT, uint32_t *metro0)
 {
-    if (!cfg || !out) return EA_EINVAL;
+    if (!f->metro || f->h_den < 1) return EA_EINVAL;
+    if (3LL * f->h_den + std::llabs((long long)f->h_num) >= (1LL << 15)) return EA_EINVAL;
+    for (uint32_t t = 0; t < NT; ++t)
+        for (int sp = 0; sp < 2; ++sp) {
+            const uint64_t *row = f->metro + ((size_t)t * 2 + sp) * 7;
+            for (int u = 0; u < 7; ++u) {
+                if (row[u] > (1ull << 32)) return EA_EINVAL;
+                if (u > 0 && row[u] < row[u - 1]) return EA_EINVAL;
+            }
+            if (f->h_num == 0)
+                for (int u = 0; u < 7; ++u) {
+                    const uint64_t other = f->metro[((size_t)t * 2 + (1 - sp)) * 7 + u];
+                    if (row[u] != other || (u < 3 && row[u] >= (1ull << 32)) ||
+                        (u >= 3 && row[u] != (1ull << 32)))
+                        return EA_EINVAL;
+                    if (u < 3) metro0[t * 3 + u] = (uint32_t)row[u];
+                }
+        }
+    return EA_OK;
+}
+
+int create_ctx(const ea_config *cfg_in, cudaStream_t stream, cudaMemPool_t pool, ea_ctx **out,
+               const ea_field *field)
+{
+    if (!cfg_in || !out) return EA_EINVAL;
     *out = nullptr;
+    ea_config cfg_copy = *cfg_in;
+    const ea_config *cfg = &cfg_copy;
+    uint32_t metro0[kMaxTemps * 3];
+    if (field) {
+        if (cfg->n_temps == 0 || cfg->n_temps > (uint32_t)kMaxTemps) return EA_EINVAL;
+        const int rc = validate_field(field, cfg->n_temps, metro0);
+        if (rc != EA_OK) return rc;
+        if (field->h_num == 0) {   // exactly the field-free method
+            cfg_copy.metro = metro0;
+            field = nullptr;
+        } else {
+            cfg_copy.metro = nullptr;
+        }
+    }
     const uint32_t L = cfg->L;
     if (L < 4 || (L & 1u)) return EA_EINVAL;
     if (!ea::supported_L((int)L)) return EA_EUNSUPPORTED;
     if (cfg->n_groups == 0 || cfg->n_temps == 0 || cfg->n_temps > (uint32_t)ea::kMaxTemps)
         return EA_EINVAL;
     if (cfg->n_copies < 1 || cfg->n_copies > 2) return EA_EINVAL;
-    if (!cfg->bonds || !cfg->spins0 || !cfg->metro) return EA_EINVAL;
+    if (!cfg->bonds || !cfg->spins0 || (!cfg->metro && !field)) return EA_EINVAL;
     if (cfg->n_temps > 1 && cfg->swap_len > 0 && !cfg->swapt) return EA_EINVAL;
     int rc = validate_tables(cfg->metro, cfg->swapt, cfg->n_temps, cfg->swap_len);
     if (rc != EA_OK) return rc;
@@ -212,6 +312,9 @@ int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea
     c->stream = stream;
     c->pool = pool;
     c->rk = ea::make_round_keys(cfg->seed);
+    c->h_num = field ? field->h_num : 0;
+    c->h_den = field ? field->h_den : 1;
+    c->step = field ? std::gcd(4 * field->h_den, 2 * std::abs(field->h_num)) : 4;
 
     cudaError_t e = cudaGetDevice(&c->device);
     int optin = 0;
@@ -219,7 +322,7 @@ int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (e != cudaSuccess) { delete c; return cuda_fail(e); }
     c->smem_optin = (size_t)optin;
-    c->plans = ea::make_plans((int)L, (int)c->NT, (int)c->C, c->swap_len, c->smem_optin);
+    c->plans = ea::make_plans((int)L, (int)c->NT, (int)c->C, c->swap_len, c->smem_optin, field != nullptr);
     if (c->plans.empty()) {
         delete c;
         return EA_EUNSUPPORTED;
@@ -242,7 +345,10 @@ int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea
     auto alloc = [&](auto **p, size_t bytes) { return ctx_alloc(c, reinterpret_cast<void **>(p), bytes, st); };
     if ((e = alloc(&c->d_spins, n_spin * 4)) != cudaSuccess) return fail(e);
     if ((e = alloc(&c->d_bonds, n_bond * 4)) != cudaSuccess) return fail(e);
-    if ((e = alloc(&c->d_metro, (size_t)c->NT * 3 * 4)) != cudaSuccess) return fail(e);
+    if (!field && (e = alloc(&c->d_metro, (size_t)c->NT * 3 * 4)) != cudaSuccess) return fail(e);
+    if (field && (e = alloc(&c->d_metro_f, (size_t)c->NT * 14 * 8)) != cudaSuccess) return fail(e);
+    if (field && (e = alloc(&c->d_mag, (size_t)c->G * c->C * c->NT * ea::kLanes * 4)) != cudaSuccess)
+        return fail(e);
     if ((e = alloc(&c->d_swapt, (n_swap ? n_swap : 1) * 4)) != cudaSuccess) return fail(e);
     if ((e = alloc(&c->d_masks, (size_t)c->G * c->C * ea::kMaxTemps * 4)) != cudaSuccess)
         return fail(e);
@@ -256,7 +362,11 @@ int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea
         return fail(e);
     if ((e = cudaMemcpyAsync(stage_b, cfg->bonds, n_bond * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return fail(e);
-    if ((e = cudaMemcpyAsync(c->d_metro, cfg->metro, (size_t)c->NT * 3 * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    if (!field &&
+        (e = cudaMemcpyAsync(c->d_metro, cfg->metro, (size_t)c->NT * 3 * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return fail(e);
+    if (field && (e = cudaMemcpyAsync(c->d_metro_f, field->metro, (size_t)c->NT * 14 * 8,
+                                      cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return fail(e);
     if (n_swap &&
         (e = cudaMemcpyAsync(c->d_swapt, cfg->swapt, n_swap * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -265,7 +375,7 @@ int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea
                                &c->launches)) != cudaSuccess)
         return fail(e);
     if ((e = ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)L, c->G, c->NT, c->C, st,
-                               &c->launches)) != cudaSuccess)
+                               &c->launches, c->d_mag)) != cudaSuccess)
         return fail(e);
     if (pool) {
         // stream-ordered: the staging buffers are released after the import
@@ -419,6 +529,10 @@ int ea_autotune(ea_ctx *c, uint32_t probe_sweeps, uint32_t swap_every, float *ms
     if (e == cudaSuccess) e = cudaEventCreate(&ev1);
     if (e == cudaSuccess) e = cudaMemcpyAsync(save_s, c->d_spins, n_spin * 4, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(save_e, c->d_energy, n_e * 4, cudaMemcpyDeviceToDevice, c->stream);
+    int32_t *save_m = nullptr;
+    if (e == cudaSuccess && c->d_mag) e = cudaMalloc(&save_m, n_e * 4);
+    if (e == cudaSuccess && c->d_mag)
+        e = cudaMemcpyAsync(save_m, c->d_mag, n_e * 4, cudaMemcpyDeviceToDevice, c->stream);
     int best = c->plan_idx, rc = EA_OK;
     float best_ms = 0.f;
     ea_sweep_args args;
@@ -438,6 +552,8 @@ int ea_autotune(ea_ctx *c, uint32_t probe_sweeps, uint32_t swap_every, float *ms
                 e = cudaMemcpyAsync(c->d_spins, save_s, n_spin * 4, cudaMemcpyDeviceToDevice, c->stream);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(c->d_energy, save_e, n_e * 4, cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess && save_m)
+                e = cudaMemcpyAsync(c->d_mag, save_m, n_e * 4, cudaMemcpyDeviceToDevice, c->stream);
         }
         if (ms_out) ms_out[i] = ms;
         if (e == cudaSuccess && rc == EA_OK && (i == 0 || ms < best_ms)) {
@@ -448,6 +564,7 @@ int ea_autotune(ea_ctx *c, uint32_t probe_sweeps, uint32_t swap_every, float *ms
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(save_s);
     cudaFree(save_e);
+    cudaFree(save_m);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (rc != EA_OK) return rc;
@@ -460,7 +577,7 @@ int ea_pt_swap(ea_ctx *c, uint32_t *masks)
     if (!c) return EA_EINVAL;
     cudaStream_t st = c->stream;
     EA_TRY(ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)c->L, c->G, c->NT, c->C, st,
-                             &c->launches));
+                             &c->launches, c->d_mag));
     ea::SweepLaunch a = base_launch(c);
     a.swap_log = masks;   // row 0 of a one-pass log
     a.pass_local0 = 0;
@@ -475,7 +592,7 @@ int ea_measure(ea_ctx *c, int32_t *energies, uint32_t *ndiff, uint64_t *qhist)
     if ((ndiff || qhist) && c->C != 2) return EA_EINVAL;
     cudaStream_t st = c->stream;
     EA_TRY(ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)c->L, c->G, c->NT, c->C, st,
-                             &c->launches));
+                             &c->launches, c->d_mag));
     EA_TRY(ea::launch_measure(c->d_spins, c->d_energy, (int)c->L, c->G, c->NT, c->C, energies, ndiff,
                               qhist, nullptr, st, &c->launches));
     return EA_OK;
@@ -487,6 +604,14 @@ int ea_measure_planes(ea_ctx *c, int mode, int32_t *out)
     if (mode == 0 && c->C != 2) return EA_EINVAL;
     EA_TRY(ea::launch_measure_planes(c->d_spins, (int)c->L, c->G, c->NT, c->C, mode, out, c->stream,
                                      &c->launches));
+    return EA_OK;
+}
+
+int ea_magnetisations(ea_ctx *c, int32_t *out)
+{
+    if (!c || !out) return EA_EINVAL;
+    EA_TRY(ea::launch_magnetisation(c->d_spins, (int)c->L, c->G, c->NT, c->C, out, c->stream,
+                                    &c->launches));
     return EA_OK;
 }
 
@@ -517,7 +642,7 @@ int ea_write_spins(ea_ctx *c, const uint32_t *src, uint64_t sweep_index, uint64_
     EA_TRY(ea::launch_import_spins(src, c->d_spins, (int)c->L, c->G, c->NT, c->C, c->stream,
                                    &c->launches));
     EA_TRY(ea::launch_energy(c->d_spins, c->d_bonds, c->d_energy, (int)c->L, c->G, c->NT, c->C,
-                             c->stream, &c->launches));
+                             c->stream, &c->launches, c->d_mag));
     c->sweep = sweep_index;
     c->pass = pass_index;
     return EA_OK;

@@ -313,6 +313,7 @@ int ea_batch_add(ea_batch *b, ea_ctx *ctx)
 {
     if (!b || !ctx) return EA_EINVAL;
     if (ctx->device != b->device) return EA_EINVAL;
+    if (ctx->h_num != 0) return EA_EINVAL;   // the batch kernel runs the field-free bodies
     for (const ea_ctx *m : b->ctxs)
         if (m == ctx) return EA_EINVAL;      // a member runs once per call
     std::vector<ea::BPlan> c = ea::batch_candidates(ctx, b->optin);

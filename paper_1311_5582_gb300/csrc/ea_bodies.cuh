@@ -23,7 +23,10 @@ namespace {
 
 // MEAS = false compiles the body without the measurement, cluster and log
 // paths (launches that use none of them; cluster_measure must then be 0).
-template <int L, bool MEAS = true>
+// FIELD = true runs the method in an external field (ea_device.cuh): field
+// flips, magnetisations counted with the energies, decisions on Et; it needs
+// kMaxTemps x 32 more words of shared memory (after the masks).
+template <int L, bool MEAS = true, bool FIELD = false>
 __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, uint32_t unit0, int tpl,
                                           int cluster_measure_arg, int swap_in_smem, int m = 1)
 {
@@ -40,7 +43,8 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
     int *bnd = E + kMaxTemps * kLanes;                        // [64][32] swap accept bounds
     int *nd = bnd + kMaxTemps * kLanes;                       // [64][32] overlap counts
     uint32_t *msk = reinterpret_cast<uint32_t *>(nd + kMaxTemps * kLanes);  // [64]
-    uint32_t *Tsw = msk + kMaxTemps;                          // [NT-1][swap_len] if swap_in_smem
+    int *Mv = reinterpret_cast<int *>(msk + kMaxTemps);       // [64][32] magnetisations (FIELD)
+    uint32_t *Tsw = msk + kMaxTemps + (FIELD ? kMaxTemps * kLanes : 0);  // [NT-1][swap_len]
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const bool act = tid < tpl * MT;                    // threads beyond the units' groups idle
@@ -65,7 +69,16 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
         for (int w = tid; w < nsw; w += nthr) Tsw[w] = a.swapt[w];
         swt = Tsw;
     }
-    const uint32_t t0 = a.metro[l * 3 + 0], t1 = a.metro[l * 3 + 1], t2 = a.metro[l * 3 + 2];
+    uint32_t t0 = 0, t1 = 0, t2 = 0;
+    uint64_t T[14];
+    if constexpr (FIELD) {
+#pragma unroll
+        for (int k = 0; k < 14; ++k) T[k] = a.metro_f[(size_t)l * 14 + k];
+    } else {
+        t0 = a.metro[l * 3 + 0];
+        t1 = a.metro[l * 3 + 1];
+        t2 = a.metro[l * 3 + 2];
+    }
     uint32_t *mine = S + (size_t)lf * N;
     const uint32_t *myJ = Js + (size_t)ui * 3 * N;
     __syncthreads();
@@ -77,11 +90,13 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
         const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
         const bool meas = MEAS && measured(s, a.measure_from, a.measure_every);
         const bool needE = swap_now || energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
-        uint32_t acc[kPlanes];
+        uint32_t acc[kPlanes], accM[kPlanes];
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
+        for (int p = 0; p < kPlanes; ++p) acc[p] = accM[p] = 0;
         if (needE)   // counters add 2 per unsatisfied bond: E = 2U - 3N
             for (int i = tid; i < MT * kLanes; i += nthr) E[i] = -3 * N;
+        if (FIELD && needE)   // and 2 per up spin: M = 2 up - N
+            for (int i = tid; i < MT * kLanes; i += nthr) Mv[i] = -N;
         if (swap_now) {
             // Swap acceptance bounds depend only on the pass index: compute them
             // now; they are read after the half-sweeps' barriers.  Row
@@ -91,21 +106,43 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
                 const int ub = row / (NT - 1), p = row - ub * (NT - 1);
                 const uint32_t un = unit0 + (uint32_t)ub;
                 const uint32_t r = swap_uniform(a.rk, p, b, P, un / a.C, (int)(un % a.C));
-                bnd[i] = accept_bound(swt + (size_t)p * a.swap_len, a.swap_len, r);
+                const int b4 = accept_bound(swt + (size_t)p * a.swap_len, a.swap_len, r);
+                bnd[i] = FIELD ? (b4 / 4) * a.step : b4;      // -K x the step of Et
             }
         }
-        if (act)
-            half_sweep<L, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g,
-                                 (0u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
-        __syncthreads();
-        if (needE) {
+        const uint32_t tag0 = (0u << 16) | ((uint32_t)c << 8) | (uint32_t)l;
+        const uint32_t tag1 = (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l;
+        if constexpr (FIELD) {
+            if (act) {
+                if (needE)
+                    half_sweep_field<L, false, true>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, T,
+                                                     acc, accM);
+                else
+                    half_sweep_field<L, false, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk,
+                                                      T, acc, accM);
+            }
+            __syncthreads();
+            if (needE) {
+                if (act)
+                    half_sweep_field<L, true, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, T,
+                                                    acc, accM);
+                reduce_counters(acc, tpl, E, lane, warp, 2, MT);
+                reduce_counters(accM, tpl, Mv, lane, warp, 2, MT);
+            } else if (act) {
+                half_sweep_field<L, false, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, T,
+                                                  acc, accM);
+            }
+        } else {
             if (act)
-                half_sweep<L, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g,
-                                    (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
-            reduce_counters(acc, tpl, E, lane, warp, 2, MT);
-        } else if (act) {
-            half_sweep<L, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g,
-                                 (1u << 16) | ((uint32_t)c << 8) | (uint32_t)l, a.rk, t0, t1, t2, acc);
+                half_sweep<L, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, t0, t1, t2, acc);
+            __syncthreads();
+            if (needE) {
+                if (act)
+                    half_sweep<L, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                reduce_counters(acc, tpl, E, lane, warp, 2, MT);
+            } else if (act) {
+                half_sweep<L, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+            }
         }
         __syncthreads();
         if (swap_now) {
@@ -116,6 +153,25 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
                 int *Eu = E + uw * NT * kLanes;
                 const int *bu = bnd + uw * (NT - 1) * kLanes;
                 uint32_t *mu = msk + uw * (NT - 1);
+                if constexpr (FIELD) {
+                    // decisions on Et = h_den E - h_num M; E and M travel together
+                    int *Mu = Mv + uw * NT * kLanes;
+                    int ce = Eu[lane], cm = Mu[lane];
+                    for (int p = 0; p + 1 < NT; ++p) {
+                        const int ne = Eu[(p + 1) * kLanes + lane], nm = Mu[(p + 1) * kLanes + lane];
+                        const int xc = a.h_den * ce - a.h_num * cm, xn = a.h_den * ne - a.h_num * nm;
+                        const bool ok = (xc - xn) >= bu[p * kLanes + lane];
+                        const uint32_t msk_p = __ballot_sync(kFull, ok);
+                        Eu[p * kLanes + lane] = ok ? ne : ce;
+                        Mu[p * kLanes + lane] = ok ? nm : cm;
+                        ce = ok ? ce : ne;
+                        cm = ok ? cm : nm;
+                        if (lane == 0) mu[p] = msk_p;
+                    }
+                    Eu[(NT - 1) * kLanes + lane] = ce;
+                    Mu[(NT - 1) * kLanes + lane] = cm;
+                    continue;
+                }
                 int cur = Eu[lane];
                 int nxt = Eu[kLanes + lane];
                 int bb = bu[lane];
@@ -213,6 +269,8 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
     }
     // energies of the final state, spins back to global memory
     for (int i = tid; i < MT * kLanes; i += nthr) a.energy[(size_t)unit0 * NT * kLanes + i] = E[i];
+    if constexpr (FIELD)
+        for (int i = tid; i < MT * kLanes; i += nthr) a.mag[(size_t)unit0 * NT * kLanes + i] = Mv[i];
     for (int w = tid; w < MT * N / 4; w += nthr)
         reinterpret_cast<uint4 *>(gS)[w] = reinterpret_cast<const uint4 *>(S)[w];
 }
@@ -223,8 +281,10 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
 // point, and writes them back; the swap pass runs as its own kernels.
 
 // LOG = false compiles the body without the energy-log path (energy_log must
-// then be null).
-template <int L, bool J_SMEM, bool LOG = true>
+// then be null).  FIELD = true: field flips (ea_device.cuh), and the
+// magnetisations after the last sweep go to a.mag with the energies; needs
+// kMaxTemps x 32 more words of shared memory after the energies.
+template <int L, bool J_SMEM, bool LOG = true, bool FIELD = false>
 __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a, uint32_t unit,
                                            int chunk, int tpl, int nlat)
 {
@@ -234,6 +294,7 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
     uint32_t *S = base;                                                   // [nlat][2][H]
     uint32_t *Js = S + (size_t)nlat * N;                                 // [3][2][H] if J_SMEM
     int *E = reinterpret_cast<int *>(Js + (J_SMEM ? 3 * N : 0));         // [64][32]
+    int *Mv = E + kMaxTemps * kLanes;                                    // [64][32] if FIELD
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int c = (int)(unit % a.C);
@@ -257,7 +318,13 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
         J = Js;
     }
     uint32_t t0 = 0, t1 = 0, t2 = 0;
-    if (active) { t0 = a.metro[slot * 3]; t1 = a.metro[slot * 3 + 1]; t2 = a.metro[slot * 3 + 2]; }
+    uint64_t T[14];
+    if constexpr (FIELD) {
+#pragma unroll
+        for (int k = 0; k < 14; ++k) T[k] = active ? a.metro_f[(size_t)slot * 14 + k] : 0;
+    } else if (active) {
+        t0 = a.metro[slot * 3]; t1 = a.metro[slot * 3 + 1]; t2 = a.metro[slot * 3 + 2];
+    }
     uint32_t *mine = S + (size_t)l * N;
     __syncthreads();
 
@@ -265,20 +332,44 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
         const uint64_t s = a.s0 + n;
         const bool last = n + 1 == a.n_sweeps;
         const bool needE = energy_log != nullptr || (last && a.compute_energy_last);
-        uint32_t acc[kPlanes];
+        uint32_t acc[kPlanes], accM[kPlanes];
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
+        for (int p = 0; p < kPlanes; ++p) acc[p] = accM[p] = 0;
         if (needE)
             for (int i = tid; i < kMaxTemps * kLanes; i += nthr) E[i] = -3 * N;
-        if (active)
-            half_sweep<L, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g,
-                                 (0u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
+        const bool needM = FIELD && last && a.compute_energy_last;
+        if (needM)
+            for (int i = tid; i < kMaxTemps * kLanes; i += nthr) Mv[i] = -N;
+        const uint32_t tag0 = (0u << 16) | ((uint32_t)c << 8) | (uint32_t)slot;
+        const uint32_t tag1 = (1u << 16) | ((uint32_t)c << 8) | (uint32_t)slot;
+        if (active) {
+            if constexpr (FIELD) {
+                if (needM)
+                    half_sweep_field<L, false, true>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, T,
+                                                     acc, accM);
+                else
+                    half_sweep_field<L, false, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, T,
+                                                      acc, accM);
+            } else {
+                half_sweep<L, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, t0, t1, t2, acc);
+            }
+        }
         __syncthreads();
         if (needE) {
-            if (active)
-                half_sweep<L, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g,
-                                    (1u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
+            if (active) {
+                if constexpr (FIELD) {
+                    if (needM)
+                        half_sweep_field<L, true, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk,
+                                                        T, acc, accM);
+                    else
+                        half_sweep_field<L, true, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk,
+                                                         T, acc, accM);
+                } else {
+                    half_sweep<L, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                }
+            }
             reduce_counters(acc, tpl, E, lane, warp, 2, nlat);
+            if (needM) reduce_counters(accM, tpl, Mv, lane, warp, 2, nlat);
             __syncthreads();
             for (int i = tid; i < nl_here * kLanes; i += nthr) {
                 const int e = E[i];
@@ -288,10 +379,14 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
                     energy_log[(((row * a.G + g) * NT + t) * a.C + c) * kLanes + b] = e;
                 }
                 if (last) a.energy[((size_t)unit * NT + t) * kLanes + b] = e;
+                if (needM) a.mag[((size_t)unit * NT + t) * kLanes + b] = Mv[i];
             }
         } else if (active) {
-            half_sweep<L, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g,
-                                 (1u << 16) | ((uint32_t)c << 8) | (uint32_t)slot, a.rk, t0, t1, t2, acc);
+            if constexpr (FIELD)
+                half_sweep_field<L, false, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, T, acc,
+                                                  accM);
+            else
+                half_sweep<L, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
         }
         __syncthreads();
     }

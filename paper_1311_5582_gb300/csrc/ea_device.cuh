@@ -336,6 +336,92 @@ __device__ __forceinline__ void half_sweep(uint32_t *S, const uint32_t *J, int c
     }
 }
 
+// ------------------------------------------------------------ external field
+// With h = h_num / h_den != 0 (Eq. 1) a flip of spin S with u unsatisfied
+// bonds changes Et = h_den E - h_num M by h_den (12 - 4u) + 2 h_num S; it is
+// accepted iff r < T[S > 0][u], with T[sp][u] = 2^32 (always) where that change
+// is <= 0.  For each spin value the accepted u form a suffix (the table grows
+// with u), so the flip mask is [u >= m_S] with m_S the number of thresholds r
+// does not beat.
+
+// Bit-sliced u >= m for a value m in 0..7 common to all lanes (u <= 6).
+__device__ __forceinline__ uint32_t ge_scalar(uint32_t u0, uint32_t u1, uint32_t u2, int m)
+{
+    const uint32_t M2 = (m & 4) ? kFull : 0u, M1 = (m & 2) ? kFull : 0u, M0 = (m & 1) ? kFull : 0u;
+    const uint32_t gt2 = u2 & ~M2, eq2 = ~(u2 ^ M2);
+    const uint32_t gt1 = u1 & ~M1, eq1 = ~(u1 ^ M1);
+    const uint32_t ge0 = u0 | ~M0;
+    return gt2 | (eq2 & (gt1 | (eq1 & ge0)));
+}
+
+// Flip mask in a field: s the spin word, T the slot's 14 thresholds [sp][u].
+__device__ __forceinline__ uint32_t flip_mask_field(uint32_t s, uint32_t u0, uint32_t u1, uint32_t u2,
+                                                    uint32_t r, const uint64_t (&T)[14])
+{
+    int m0 = 0, m1 = 0;
+#pragma unroll
+    for (int u = 0; u < 7; ++u) {
+        m0 += (uint64_t)r >= T[u] ? 1 : 0;
+        m1 += (uint64_t)r >= T[7 + u] ? 1 : 0;
+    }
+    const uint32_t f0 = ge_scalar(u0, u1, u2, m0), f1 = ge_scalar(u0, u1, u2, m1);
+    return (s & f1) | (~s & f0);
+}
+
+// Adds one word to a bit-sliced per-lane counter.
+__device__ __forceinline__ void acc_add_word(uint32_t (&acc)[kPlanes], uint32_t w)
+{
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) {
+        const uint32_t c = acc[p] & w;
+        acc[p] ^= w;
+        w = c;
+    }
+}
+
+// half_sweep in a field: WITH_E as there; WITH_M counts the up spins of the
+// updated sites into accM.
+template <int L, bool WITH_E, bool WITH_M>
+__device__ __forceinline__ void half_sweep_field(uint32_t *S, const uint32_t *J, int col, int tl, int tpl,
+                                                 int qper, uint32_t s, uint32_t g, uint32_t ctag,
+                                                 const RoundKeys &rk, const uint64_t (&T)[14],
+                                                 uint32_t (&acc)[kPlanes], uint32_t (&accM)[kPlanes])
+{
+    using Gm = Geo<L>;
+    uint32_t *Sc = S + col * Gm::H;
+    for (int j = 0; j < qper; ++j) {
+        const int q = tl + j * tpl;
+        if (q >= Gm::Q) break;
+        Quad o;
+        load_quad<L>(S, J, col, q, o);
+        const uint4 r = philox((uint32_t)q, ctag, s, g, rk);
+        const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+        uint32_t x0[4], x1[4], x2[4], ns[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint32_t u0, u1, u2;
+            unsat_count(o.s[i], o.nb, o.jb, i, u0, u1, u2);
+            const uint32_t f = flip_mask_field(o.s[i], u0, u1, u2, rr[i], T);
+            ns[i] = o.s[i] ^ f;
+            if constexpr (WITH_E) {
+                x0[i] = u0;
+                x1[i] = u1 ^ (f & ~u0);
+                x2[i] = u2 ^ (f & ~(u0 & u1));
+            }
+        }
+        *reinterpret_cast<uint4 *>(Sc + 4 * q) = make_uint4(ns[0], ns[1], ns[2], ns[3]);
+        if constexpr (WITH_E) {
+            uint32_t A[5];
+            quad_sum(x0, x1, x2, A);
+            acc_add5(acc, A);
+        }
+        if constexpr (WITH_M) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc_add_word(accM, ns[i]);
+        }
+    }
+}
+
 __device__ __forceinline__ bool swap_after(uint64_t s, uint32_t swap_every)
 {
     return swap_every != 0 && ((s + 1) % swap_every) == 0;

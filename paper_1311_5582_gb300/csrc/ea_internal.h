@@ -56,6 +56,10 @@ struct SweepLaunch {
     // chunked form: lattices [t0, t0 + nlat) of each unit per CTA
     uint32_t t_per_cta;
     int compute_energy_last;        // chunked form: energies after the last sweep
+    // external field h = h_num / h_den (h_num == 0: none); see ea_device.cuh
+    const uint64_t *metro_f;        // [NT][2][7] thresholds, 2^32 = always
+    int32_t *mag;                   // [G][C][NT][32] magnetisations by slot
+    int32_t h_num, h_den, step;     // step of Et = h_den E - h_num M differences
 };
 
 enum PlanForm { kFormUnit = 0, kFormUnitFast = 1, kFormChunked = 2 };
@@ -75,7 +79,9 @@ struct Plan {
 bool supported_L(int L);
 // Every kernel plan that can run (L, NT) within the device's opt-in shared
 // memory, best guess first.  Empty if none.
-std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin);
+// field: plans for the external-field kernels (generic unit and chunked forms).
+std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin,
+                             bool field = false);
 
 int fast_unit_threads(int L, int HP, int NT);
 // Dynamic shared memory of the specialised unit kernel (with or without the
@@ -103,9 +109,18 @@ cudaError_t launch_swap_global(const SweepLaunch &a, int L, uint64_t P, uint32_t
 // Per-plane counts (k_measure_planes); L <= 32.
 cudaError_t launch_measure_planes(const uint32_t *spins, int L, uint32_t G, uint32_t NT, uint32_t C,
                                   int mode, int32_t *out, cudaStream_t st, uint64_t *launches);
+// With mag != null also the magnetisations [G][C][NT][32].
 cudaError_t launch_energy(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, int L,
                           uint32_t G, uint32_t NT, uint32_t C, cudaStream_t st,
-                          uint64_t *launches);
+                          uint64_t *launches, int32_t *mag = nullptr);
+// Magnetisations of every lattice, out = DEVICE int32 [G][NT][C][32].
+cudaError_t launch_magnetisation(const uint32_t *spins, int L, uint32_t G, uint32_t NT, uint32_t C,
+                                 int32_t *out, cudaStream_t st, uint64_t *launches);
+// External-field sweep kernels (ea_field.cu); called by launch_sweep_unit /
+// launch_sweep_chunk when a.h_num != 0.
+cudaError_t launch_sweep_unit_field(const SweepLaunch &a, int L, const Plan &plan, bool cluster_measure,
+                                    cudaStream_t st);
+cudaError_t launch_sweep_chunk_field(const SweepLaunch &a, int L, const Plan &plan, cudaStream_t st);
 cudaError_t launch_measure(const uint32_t *spins, const int32_t *energy, int L, uint32_t G,
                            uint32_t NT, uint32_t C, int32_t *energies_out, uint32_t *ndiff_out,
                            uint64_t *qhist, int64_t *esum, cudaStream_t st, uint64_t *launches);
@@ -123,6 +138,10 @@ struct ea_ctx {
     uint32_t *d_spins, *d_bonds, *d_metro, *d_swapt, *d_masks;
     int32_t *d_energy;
     int *d_err;
+    // external field h = h_num / h_den (h_num == 0: none, the pointers null)
+    int32_t h_num, h_den, step;
+    uint64_t *d_metro_f;           // [NT][2][7]
+    int32_t *d_mag;                // [G][C][NT][32] magnetisations by slot
     uint64_t sweep, pass;
     uint64_t launches;
     std::vector<ea::Plan> plans;   // every kernel plan that can run this ensemble
@@ -134,7 +153,9 @@ struct ea_ctx {
 namespace ea {
 // Creates a context (ea_create with an optional memory pool: with a pool every
 // allocation is stream-ordered on `stream` and nothing waits on the host).
-int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea_ctx **out);
+// field: NULL, or the external field (ea_create_field).
+int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea_ctx **out,
+               const ea_field *field = nullptr);
 // Releases a context's device memory (stream-ordered on `st` for pooled
 // contexts) and the context itself.  The caller has ordered its last use.
 void destroy_ctx(ea_ctx *c, cudaStream_t st);

@@ -43,7 +43,31 @@ k_swap_decide(const __grid_constant__ SweepLaunch a, uint64_t P, uint32_t *masks
                               swap_uniform(a.rk, p, b, P, g, c));
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && a.h_num != 0) {
+        // field: bounds in steps of Et = h_den E - h_num M; E and M travel together
+        int32_t *E = a.energy + (size_t)unit * NT * kLanes;
+        int32_t *M = a.mag + (size_t)unit * NT * kLanes;
+        int ce = E[lane], cm = M[lane];
+        for (int p = 0; p + 1 < NT; ++p) {
+            const int ne = E[(p + 1) * kLanes + lane], nm = M[(p + 1) * kLanes + lane];
+            const int xc = a.h_den * ce - a.h_num * cm, xn = a.h_den * ne - a.h_num * nm;
+            const bool ok = (xc - xn) >= (bnd[p * kLanes + lane] / 4) * a.step;
+            const uint32_t m = __ballot_sync(kFull, ok);
+            E[p * kLanes + lane] = ok ? ne : ce;
+            M[p * kLanes + lane] = ok ? nm : cm;
+            ce = ok ? ce : ne;
+            cm = ok ? cm : nm;
+            if (lane == 0) {
+                masks_out[(size_t)unit * (NT - 1) + p] = m;
+                if (swap_log_row) swap_log_row[(size_t)unit * (NT - 1) + p] = m;
+            }
+        }
+        E[(NT - 1) * kLanes + lane] = ce;
+        M[(NT - 1) * kLanes + lane] = cm;
+        if (energy_log_row)
+            for (int t = 0; t < NT; ++t)
+                energy_log_row[(((size_t)g * NT + t) * a.C + c) * kLanes + lane] = E[t * kLanes + lane];
+    } else if (warp == 0) {
         int32_t *E = a.energy + (size_t)unit * NT * kLanes;
         int cur = E[lane];
         for (int p = 0; p + 1 < NT; ++p) {
@@ -83,21 +107,38 @@ k_swap_apply(uint32_t *spins, const uint32_t *masks, int N, int NT)
     S[(size_t)(NT - 1) * N + w] = x;
 }
 
-// Energies recomputed from the spins: one CTA per lattice.
+// Energies (and, with mag != null, magnetisations M = 2 up - N) recomputed
+// from the spins: one CTA per lattice.
 template <int L>
 __global__ void __launch_bounds__(kMaxThreads)
-k_energy(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, uint32_t NT, uint32_t C)
+k_energy(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, int32_t *mag, uint32_t NT,
+         uint32_t C)
 {
     using Gm = Geo<L>;
-    __shared__ int U[kLanes];
+    __shared__ int U[kLanes], Up[kLanes];
     const size_t lat = blockIdx.x;              // (unit, t)
     const uint32_t unit = (uint32_t)(lat / NT);
     const uint32_t g = unit / C;
     const uint32_t *S = spins + lat * Gm::N;
     const uint32_t *J = bonds + (size_t)g * 3 * Gm::N;
     const int tid = threadIdx.x, tpl = blockDim.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < kLanes) U[tid] = 0;
+    if (tid < kLanes) U[tid] = Up[tid] = 0;
     __syncthreads();
+    if (mag != nullptr) {
+        // per-thread count <= 4 x 2 x kMaxQuadsPerThread = 80 (N / 4 vectors, 2Q)
+        uint32_t accM[kPlanes];
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) accM[p] = 0;
+        const uint4 *S4 = reinterpret_cast<const uint4 *>(S);
+        for (int w = tid; w < Gm::N / 4; w += tpl) {
+            const uint4 x = S4[w];
+            acc_add_words4(accM, x.x, x.y, x.z, x.w);
+        }
+        int cm = 0;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) cm += __popc(warp_transpose(accM[p], lane)) << p;
+        atomicAdd(&Up[lane], cm);
+    }
     uint32_t acc[kPlanes];
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
@@ -122,6 +163,36 @@ k_energy(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, uint32_t
     atomicAdd(&U[lane], cnt);
     __syncthreads();
     if (tid < kLanes) energy[lat * kLanes + tid] = 2 * U[tid] - 3 * Gm::N;
+    if (mag != nullptr && tid < kLanes) mag[lat * kLanes + tid] = 2 * Up[tid] - Gm::N;
+}
+
+// Magnetisations M = 2 up - N of every lattice in API order [G][NT][C][32]:
+// one CTA per lattice (g, c, t).
+__global__ void __launch_bounds__(256)
+k_magnetisation(const uint32_t *spins, int N, uint32_t NT, uint32_t C, int32_t *out)
+{
+    __shared__ int up[kLanes];
+    const size_t lat = blockIdx.x;              // device order (g, c, t)
+    const uint32_t t = (uint32_t)(lat % NT), gc = (uint32_t)(lat / NT);
+    const uint32_t c = gc % C, g = gc / C;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < kLanes) up[tid] = 0;
+    __syncthreads();
+    // per-thread count <= 4 x ceil(N / 1024) <= 128 for N <= 32768
+    uint32_t acc[kPlanes];
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
+    const uint4 *S4 = reinterpret_cast<const uint4 *>(spins + lat * N);
+    for (int w = tid; w < N / 4; w += blockDim.x) {
+        const uint4 x = S4[w];
+        acc_add_words4(acc, x.x, x.y, x.z, x.w);
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int p = 0; p < kPlanes; ++p) cnt += __popc(warp_transpose(acc[p], lane)) << p;
+    atomicAdd(&up[lane], cnt);
+    __syncthreads();
+    if (tid < kLanes) out[(((size_t)g * NT + t) * C + c) * kLanes + tid] = 2 * up[tid] - N;
 }
 
 // Measurement pass: per (group, slot) overlap counts between the two copies,
@@ -339,13 +410,13 @@ cudaError_t launch_chunk_L(const SweepLaunch &a, const Plan &plan, cudaStream_t 
 }
 
 template <int L>
-cudaError_t launch_energy_L(const uint32_t *spins, const uint32_t *bonds, int32_t *energy,
+cudaError_t launch_energy_L(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, int32_t *mag,
                             uint32_t G, uint32_t NT, uint32_t C, cudaStream_t st)
 {
     constexpr int Q = Geo<L>::Q;
     int threads = 32;
     while (threads < kMaxThreads && (Q + threads - 1) / threads > kMaxQuadsPerThread) threads *= 2;
-    k_energy<L><<<(unsigned)((size_t)G * C * NT), threads, 0, st>>>(spins, bonds, energy, NT, C);
+    k_energy<L><<<(unsigned)((size_t)G * C * NT), threads, 0, st>>>(spins, bonds, energy, mag, NT, C);
     return cudaGetLastError();
 }
 
@@ -384,7 +455,7 @@ static int pow2_at_least(int x)
 }
 
 static bool unit_generic_plan(int L, int NT, uint32_t swap_len, size_t smem_optin, int tpl_pref,
-                              Plan *plan)
+                              bool field, Plan *plan)
 {
     const int N = L * L * L, Q = N / 8;
     const int tpl_min = pow2_at_least((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
@@ -393,7 +464,7 @@ static bool unit_generic_plan(int L, int NT, uint32_t swap_len, size_t smem_opti
     // whole warps only: shuffles in the energy reduction use full masks
     while ((tpl * NT) % 32 != 0) tpl *= 2;
     while (tpl * NT > kMaxThreads && tpl / 2 >= tpl_min && ((tpl / 2) * NT) % 32 == 0) tpl /= 2;
-    size_t smem = UnitSmem::base_bytes(N, NT);
+    size_t smem = UnitSmem::base_bytes(N, NT) + (field ? (size_t)kMaxTemps * kLanes * 4 : 0);
     const size_t sw = UnitSmem::swap_bytes(NT, swap_len);
     const bool sw_smem = smem + sw <= smem_optin;
     if (sw_smem) smem += sw;
@@ -410,12 +481,13 @@ static bool unit_generic_plan(int L, int NT, uint32_t swap_len, size_t smem_opti
     return true;
 }
 
-static bool chunk_plan(int L, int NT, size_t smem_optin, int tpl_pref, int nlat_cap, Plan *plan)
+static bool chunk_plan(int L, int NT, size_t smem_optin, int tpl_pref, int nlat_cap, bool field,
+                       Plan *plan)
 {
     const int N = L * L * L, Q = N / 8;
     const int tpl_min = pow2_at_least((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
     const size_t lat_bytes = (size_t)N * 4, j_bytes = (size_t)3 * N * 4;
-    const size_t e_bytes = (size_t)kMaxTemps * kLanes * 4;
+    const size_t e_bytes = (size_t)kMaxTemps * kLanes * 4 * (field ? 2 : 1);
     const bool j_smem = j_bytes + lat_bytes + e_bytes <= smem_optin;
     const size_t budget = smem_optin - (j_smem ? j_bytes : 0) - e_bytes;
     int nlat = (int)(budget / lat_bytes);
@@ -444,14 +516,14 @@ static bool chunk_plan(int L, int NT, size_t smem_optin, int tpl_pref, int nlat_
     return true;
 }
 
-std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin)
+std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin, bool field)
 {
     (void)C;
     std::vector<Plan> out;
     if (NT < 1 || NT > kMaxTemps || !supported_L(L)) return out;
     const int N = L * L * L;
-    // fast unit form (L % 8 == 0): best first
-    {
+    // fast unit form (L % 8 == 0): best first; field-free only
+    if (!field) {
         const bool sw_smem = fast_unit_smem(L, NT, swap_len, true, false, false) <= smem_optin;
         const size_t smem = fast_unit_smem(L, NT, swap_len, sw_smem, false, false);
         const int hps[] = {8, 16, 4, 64, 32};
@@ -476,7 +548,7 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
         const int prefs[] = {0, 8, 16, 32, 64, 128};
         for (int tp : prefs) {
             Plan p;
-            if (!unit_generic_plan(L, NT, swap_len, smem_optin, tp, &p)) continue;
+            if (!unit_generic_plan(L, NT, swap_len, smem_optin, tp, field, &p)) continue;
             bool dup = false;
             for (const Plan &q : out)
                 if (q.form == p.form && q.threads_per_lattice == p.threads_per_lattice) dup = true;
@@ -490,7 +562,7 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
         for (int cap : caps)
             for (int tp : prefs) {
                 Plan p;
-                if (!chunk_plan(L, NT, smem_optin, tp, cap, &p)) continue;
+                if (!chunk_plan(L, NT, smem_optin, tp, cap, field, &p)) continue;
                 bool dup = false;
                 for (const Plan &q : out)
                     if (q.form == p.form && q.threads_per_lattice == p.threads_per_lattice &&
@@ -544,6 +616,7 @@ cudaError_t launch_sweep_unit(const SweepLaunch &a, int L, const Plan &plan, boo
                               cudaStream_t st, uint64_t *launches)
 {
     *launches += 1;
+    if (a.h_num != 0) return launch_sweep_unit_field(a, L, plan, cluster_measure, st);
     switch (L) {
 #define EA_CASE(X) case X: return launch_unit_L<X>(a, plan, cluster_measure, st);
         EA_FOR_EACH_L(EA_CASE)
@@ -556,6 +629,7 @@ cudaError_t launch_sweep_chunk(const SweepLaunch &a, int L, const Plan &plan, cu
                                uint64_t *launches)
 {
     *launches += 1;
+    if (a.h_num != 0) return launch_sweep_chunk_field(a, L, plan, st);
     switch (L) {
 #define EA_CASE(X) case X: return launch_chunk_L<X>(a, plan, st);
         EA_FOR_EACH_L(EA_CASE)
@@ -579,15 +653,25 @@ cudaError_t launch_swap_global(const SweepLaunch &a, int L, uint64_t P, uint32_t
 }
 
 cudaError_t launch_energy(const uint32_t *spins, const uint32_t *bonds, int32_t *energy, int L,
-                          uint32_t G, uint32_t NT, uint32_t C, cudaStream_t st, uint64_t *launches)
+                          uint32_t G, uint32_t NT, uint32_t C, cudaStream_t st, uint64_t *launches,
+                          int32_t *mag)
 {
     *launches += 1;
     switch (L) {
-#define EA_CASE(X) case X: return launch_energy_L<X>(spins, bonds, energy, G, NT, C, st);
+#define EA_CASE(X) case X: return launch_energy_L<X>(spins, bonds, energy, mag, G, NT, C, st);
         EA_FOR_EACH_L(EA_CASE)
 #undef EA_CASE
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_magnetisation(const uint32_t *spins, int L, uint32_t G, uint32_t NT, uint32_t C,
+                                 int32_t *out, cudaStream_t st, uint64_t *launches)
+{
+    const int N = L * L * L;
+    k_magnetisation<<<G * C * NT, 256, 0, st>>>(spins, N, NT, C, out);
+    *launches += 1;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_measure(const uint32_t *spins, const int32_t *energy, int L, uint32_t G,

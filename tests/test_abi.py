@@ -109,3 +109,37 @@ def test_null_context_calls_fail_cleanly():
     assert lib.ea_measure(None, None, None, None) == -1
     assert lib.ea_sync(None) == -1
     lib.ea_destroy(None)
+
+
+@pytest.mark.parametrize("h_num,h_den,nt,L", [(1, 2, 8, 4), (-3, 4, 16, 8), (7, 1, 12, 6), (5, 3, 32, 16),
+                                              (1, 10, 24, 32), (0, 1, 6, 4)])
+def test_field_tables_match_oracle_bit_for_bit(h_num, h_den, nt, L):
+    betas = W.geometric_ladder(nt, 0.8, 2.0)
+    m, s = ea.ea_build_tables_field(betas, L ** 3, h_num, h_den)
+    np.testing.assert_array_equal(m, oracle.metro_table_field(betas, h_num, h_den))
+    np.testing.assert_array_equal(s, oracle.swap_table_field_trimmed(betas, L ** 3, h_num, h_den))
+
+
+def test_field_builder_and_create_reject_bad_fields():
+    betas = W.geometric_ladder(4, 1.0, 2.0)
+    with pytest.raises(ea.EAError):
+        ea.ea_build_tables_field(betas, 64, 1, 0)              # h_den < 1
+    with pytest.raises(ea.EAError):
+        ea.ea_build_tables_field(betas, 64, 1 << 15, 1)        # Et would overflow int32
+    lib = ea.load_library()
+    cfg, keep = _cfg()
+    mf, sw = ea.ea_build_tables_field(betas, 64, 1, 2)
+
+    def rc(h_num, h_den, table):
+        t = np.ascontiguousarray(table, np.uint64)
+        f = ea._Field(h_num, h_den, t.ctypes.data)
+        h = ctypes.c_void_p(None)
+        return lib.ea_create_field(ctypes.byref(cfg), ctypes.byref(f), None, ctypes.byref(h))
+
+    bad = mf.copy(); bad[1, 0, 2], bad[1, 0, 3] = bad[1, 0, 3], bad[1, 0, 2]   # decreasing in u
+    assert rc(1, 2, bad) == -1
+    big = mf.copy(); big[0, 1, 6] = (1 << 32) + 1                              # above "always"
+    assert rc(1, 2, big) == -1
+    assert rc(1, 0, mf) == -1
+    # h_num = 0 must carry the field-free table: both spin rows equal, 2^32 for u >= 3
+    assert rc(0, 1, mf) == -1
