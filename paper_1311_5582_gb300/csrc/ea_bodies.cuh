@@ -73,7 +73,7 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
     uint64_t T[14];
     if constexpr (FIELD) {
 #pragma unroll
-        for (int k = 0; k < 14; ++k) T[k] = a.metro_f[(size_t)l * 14 + k];
+        for (int k = 0; k < 14; ++k) T[k] = 0ull - a.metro_f[(size_t)l * 14 + k];   // 2^64 - T
     } else {
         t0 = a.metro[l * 3 + 0];
         t1 = a.metro[l * 3 + 1];
@@ -321,7 +321,7 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
     uint64_t T[14];
     if constexpr (FIELD) {
 #pragma unroll
-        for (int k = 0; k < 14; ++k) T[k] = active ? a.metro_f[(size_t)slot * 14 + k] : 0;
+        for (int k = 0; k < 14; ++k) T[k] = active ? 0ull - a.metro_f[(size_t)slot * 14 + k] : 0;   // 2^64 - T
     } else if (active) {
         t0 = a.metro[slot * 3]; t1 = a.metro[slot * 3 + 1]; t2 = a.metro[slot * 3 + 2];
     }

@@ -340,32 +340,36 @@ __device__ __forceinline__ void half_sweep(uint32_t *S, const uint32_t *J, int c
 // With h = h_num / h_den != 0 (Eq. 1) a flip of spin S with u unsatisfied
 // bonds changes Et = h_den E - h_num M by h_den (12 - 4u) + 2 h_num S; it is
 // accepted iff r < T[S > 0][u], with T[sp][u] = 2^32 (always) where that change
-// is <= 0.  For each spin value the accepted u form a suffix (the table grows
-// with u), so the flip mask is [u >= m_S] with m_S the number of thresholds r
-// does not beat.
+// is <= 0.  The kernels hold each threshold as 2^64 - T: the high word of
+// r + 2^64 - T (one wide multiply-add, FMA pipe) is all-ones iff r < T, which
+// also gives "always" for T = 2^32 and "never" for T = 0.
 
-// Bit-sliced u >= m for a value m in 0..7 common to all lanes (u <= 6).
-__device__ __forceinline__ uint32_t ge_scalar(uint32_t u0, uint32_t u1, uint32_t u2, int m)
+__device__ __forceinline__ uint32_t below_field(uint32_t r, uint64_t neg_t)
 {
-    const uint32_t M2 = (m & 4) ? kFull : 0u, M1 = (m & 2) ? kFull : 0u, M0 = (m & 1) ? kFull : 0u;
-    const uint32_t gt2 = u2 & ~M2, eq2 = ~(u2 ^ M2);
-    const uint32_t gt1 = u1 & ~M1, eq1 = ~(u1 ^ M1);
-    const uint32_t ge0 = u0 | ~M0;
-    return gt2 | (eq2 & (gt1 | (eq1 & ge0)));
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, 1, %2;" : "=l"(d) : "r"(r), "l"(neg_t));
+    return (uint32_t)(d >> 32);
 }
 
-// Flip mask in a field: s the spin word, T the slot's 14 thresholds [sp][u].
+// Flip mask in a field: s the spin word, NTh the slot's 14 thresholds [sp][u]
+// as 2^64 - T.  For each spin value the table is non-decreasing in u, so the
+// accepted u form a suffix and the mask is the OR over u of [u_lane >= u] and
+// "r < T[u]".
 __device__ __forceinline__ uint32_t flip_mask_field(uint32_t s, uint32_t u0, uint32_t u1, uint32_t u2,
-                                                    uint32_t r, const uint64_t (&T)[14])
+                                                    uint32_t r, const uint64_t (&NTh)[14])
 {
-    int m0 = 0, m1 = 0;
+    const uint32_t ge2 = u1 | u2, ge1 = ge2 | u0, ge3 = u2 | (u1 & u0);
+    const uint32_t ge4 = u2, ge5 = u2 & (u1 | u0), ge6 = u2 & u1;
+    uint32_t f[2];
 #pragma unroll
-    for (int u = 0; u < 7; ++u) {
-        m0 += (uint64_t)r >= T[u] ? 1 : 0;
-        m1 += (uint64_t)r >= T[7 + u] ? 1 : 0;
+    for (int sp = 0; sp < 2; ++sp) {
+        const int o = 7 * sp;
+        f[sp] = below_field(r, NTh[o]) | (ge1 & below_field(r, NTh[o + 1])) |
+                (ge2 & below_field(r, NTh[o + 2])) | (ge3 & below_field(r, NTh[o + 3])) |
+                (ge4 & below_field(r, NTh[o + 4])) | (ge5 & below_field(r, NTh[o + 5])) |
+                (ge6 & below_field(r, NTh[o + 6]));
     }
-    const uint32_t f0 = ge_scalar(u0, u1, u2, m0), f1 = ge_scalar(u0, u1, u2, m1);
-    return (s & f1) | (~s & f0);
+    return (s & f[1]) | (~s & f[0]);
 }
 
 // Adds one word to a bit-sliced per-lane counter.
@@ -379,12 +383,12 @@ __device__ __forceinline__ void acc_add_word(uint32_t (&acc)[kPlanes], uint32_t 
     }
 }
 
-// half_sweep in a field: WITH_E as there; WITH_M counts the up spins of the
-// updated sites into accM.
+// half_sweep in a field (thresholds as 2^64 - T): WITH_E as there; WITH_M
+// counts the up spins of the updated sites into accM.
 template <int L, bool WITH_E, bool WITH_M>
 __device__ __forceinline__ void half_sweep_field(uint32_t *S, const uint32_t *J, int col, int tl, int tpl,
                                                  int qper, uint32_t s, uint32_t g, uint32_t ctag,
-                                                 const RoundKeys &rk, const uint64_t (&T)[14],
+                                                 const RoundKeys &rk, const uint64_t (&NTh)[14],
                                                  uint32_t (&acc)[kPlanes], uint32_t (&accM)[kPlanes])
 {
     using Gm = Geo<L>;
@@ -401,7 +405,7 @@ __device__ __forceinline__ void half_sweep_field(uint32_t *S, const uint32_t *J,
         for (int i = 0; i < 4; ++i) {
             uint32_t u0, u1, u2;
             unsat_count(o.s[i], o.nb, o.jb, i, u0, u1, u2);
-            const uint32_t f = flip_mask_field(o.s[i], u0, u1, u2, rr[i], T);
+            const uint32_t f = flip_mask_field(o.s[i], u0, u1, u2, rr[i], NTh);
             ns[i] = o.s[i] ^ f;
             if constexpr (WITH_E) {
                 x0[i] = u0;

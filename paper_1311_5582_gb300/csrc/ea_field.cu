@@ -9,7 +9,7 @@ namespace ea {
 namespace {
 
 template <int L>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(field_max_threads(L), 1)
 k_sweep_unit_field(const __grid_constant__ SweepLaunch a, int tpl, int cluster_measure, int swap_in_smem)
 {
     extern __shared__ uint4 smem_u4[];
@@ -18,7 +18,7 @@ k_sweep_unit_field(const __grid_constant__ SweepLaunch a, int tpl, int cluster_m
 }
 
 template <int L, bool J_SMEM>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(field_max_threads(L), 1)
 k_sweep_chunk_field(const __grid_constant__ SweepLaunch a, int tpl, int nlat)
 {
     extern __shared__ uint4 smem_u4[];

@@ -116,6 +116,10 @@ cudaError_t launch_energy(const uint32_t *spins, const uint32_t *bonds, int32_t 
 // Magnetisations of every lattice, out = DEVICE int32 [G][NT][C][32].
 cudaError_t launch_magnetisation(const uint32_t *spins, int L, uint32_t G, uint32_t NT, uint32_t C,
                                  int32_t *out, cudaStream_t st, uint64_t *launches);
+// Most threads a CTA of the external-field kernels has for lattice size L
+// (384, so that a thread holds its 14 thresholds in registers; 512 for L = 32,
+// whose lattices need 512 threads).
+constexpr int field_max_threads(int L) { return L >= 32 ? 512 : 384; }
 // External-field sweep kernels (ea_field.cu); called by launch_sweep_unit /
 // launch_sweep_chunk when a.h_num != 0.
 cudaError_t launch_sweep_unit_field(const SweepLaunch &a, int L, const Plan &plan, bool cluster_measure,

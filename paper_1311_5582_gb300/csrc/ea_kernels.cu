@@ -447,6 +447,10 @@ bool supported_L(int L)
     }
 }
 
+// Threads a CTA of the sweep kernels may have: the field kernels are
+// compiled for at most field_max_threads(L) (more registers a thread).
+static int max_threads(int L, bool field) { return field ? field_max_threads(L) : kMaxThreads; }
+
 static int pow2_at_least(int x)
 {
     int p = 1;
@@ -457,6 +461,7 @@ static int pow2_at_least(int x)
 static bool unit_generic_plan(int L, int NT, uint32_t swap_len, size_t smem_optin, int tpl_pref,
                               bool field, Plan *plan)
 {
+    const int kMaxThreads = max_threads(L, field);
     const int N = L * L * L, Q = N / 8;
     const int tpl_min = pow2_at_least((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
     int tpl = tpl_pref > 0 ? tpl_pref : pow2_at_least((Q + 3) / 4);
@@ -484,6 +489,7 @@ static bool unit_generic_plan(int L, int NT, uint32_t swap_len, size_t smem_opti
 static bool chunk_plan(int L, int NT, size_t smem_optin, int tpl_pref, int nlat_cap, bool field,
                        Plan *plan)
 {
+    const int kMaxThreads = max_threads(L, field);
     const int N = L * L * L, Q = N / 8;
     const int tpl_min = pow2_at_least((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
     const size_t lat_bytes = (size_t)N * 4, j_bytes = (size_t)3 * N * 4;

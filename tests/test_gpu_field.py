@@ -49,7 +49,7 @@ def compare(gpu, sim, n, swap_every, tag):
 
 @pytest.mark.parametrize("L,G,NT,C,h_num,h_den,swap_every", [
     (4, 2, 8, 2, 1, 2, 1), (6, 1, 7, 2, -5, 3, 2), (8, 2, 12, 2, 3, 1, 1), (10, 1, 5, 1, 1, 4, 3),
-    (12, 1, 6, 2, -1, 2, 1), (16, 1, 8, 2, 2, 5, 2),
+    (12, 1, 6, 2, -1, 2, 1), (16, 1, 4, 2, 2, 5, 2),
 ])
 @pytest.mark.parametrize("form", ["unit", "chunked"])
 def test_field_matches_oracle(L, G, NT, C, h_num, h_den, swap_every, form):
