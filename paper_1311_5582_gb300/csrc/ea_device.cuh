@@ -187,15 +187,26 @@ __device__ __forceinline__ void unsat_count(uint32_t s, const uint32_t (&nb)[6][
     full_add(a1, b1, c, u1, u2);
 }
 
+// All-ones iff r < T, for a threshold T <= 2^32 held as 2^64 - T: the high
+// word of r + 2^64 - T, formed by one wide multiply-add that issues to the FMA
+// pipe and leaves the integer ALU pipe to the bit-sliced logic.
+__device__ __forceinline__ uint32_t below_wide(uint32_t r, uint64_t neg_t)
+{
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, 1, %2;" : "=l"(d) : "r"(r), "l"(neg_t));
+    return (uint32_t)(d >> 32);
+}
+
 // Flip mask of a site: all lanes with dE <= 0 (u >= 3), and lanes with
-// u >= m where m counts the thresholds r is not below (t0 <= t1 <= t2).
+// u >= m where m counts the thresholds r is not below (t0 <= t1 <= t2, given
+// as 2^64 - t).
 __device__ __forceinline__ uint32_t flip_mask(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t r,
-                                              uint32_t t0, uint32_t t1, uint32_t t2)
+                                              uint64_t n0, uint64_t n1, uint64_t n2)
 {
     const uint32_t ge2 = u2 | u1;
     const uint32_t ge1 = ge2 | u0;
     const uint32_t ge3 = u2 | (u1 & u0);
-    return (r < t0) ? kFull : (r < t1) ? ge1 : (r < t2) ? ge2 : ge3;
+    return ge3 | (ge2 & below_wide(r, n2)) | (ge1 & below_wide(r, n1)) | below_wide(r, n0);
 }
 
 // Sum of four 3-bit lane values (x2 x1 x0)[j] into a 5-bit value A.
@@ -306,6 +317,7 @@ __device__ __forceinline__ void half_sweep(uint32_t *S, const uint32_t *J, int c
 {
     using Gm = Geo<L>;
     uint32_t *Sc = S + col * Gm::H;
+    const uint64_t n0 = 0ull - (uint64_t)t0, n1 = 0ull - (uint64_t)t1, n2 = 0ull - (uint64_t)t2;
     for (int j = 0; j < qper; ++j) {
         const int q = tl + j * tpl;
         if (q >= Gm::Q) break;
@@ -318,7 +330,7 @@ __device__ __forceinline__ void half_sweep(uint32_t *S, const uint32_t *J, int c
         for (int i = 0; i < 4; ++i) {
             uint32_t u0, u1, u2;
             unsat_count(o.s[i], o.nb, o.jb, i, u0, u1, u2);
-            const uint32_t f = flip_mask(u0, u1, u2, rr[i], t0, t1, t2);
+            const uint32_t f = flip_mask(u0, u1, u2, rr[i], n0, n1, n2);
             ns[i] = o.s[i] ^ f;
             if constexpr (WITH_E) {
                 // after a flip the six bonds change state: u' = 6 - u
@@ -340,16 +352,8 @@ __device__ __forceinline__ void half_sweep(uint32_t *S, const uint32_t *J, int c
 // With h = h_num / h_den != 0 (Eq. 1) a flip of spin S with u unsatisfied
 // bonds changes Et = h_den E - h_num M by h_den (12 - 4u) + 2 h_num S; it is
 // accepted iff r < T[S > 0][u], with T[sp][u] = 2^32 (always) where that change
-// is <= 0.  The kernels hold each threshold as 2^64 - T: the high word of
-// r + 2^64 - T (one wide multiply-add, FMA pipe) is all-ones iff r < T, which
+// is <= 0.  The kernels hold each threshold as 2^64 - T (below_wide), which
 // also gives "always" for T = 2^32 and "never" for T = 0.
-
-__device__ __forceinline__ uint32_t below_field(uint32_t r, uint64_t neg_t)
-{
-    uint64_t d;
-    asm("mad.wide.u32 %0, %1, 1, %2;" : "=l"(d) : "r"(r), "l"(neg_t));
-    return (uint32_t)(d >> 32);
-}
 
 // Flip mask in a field: s the spin word, NTh the slot's 14 thresholds [sp][u]
 // as 2^64 - T.  For each spin value the table is non-decreasing in u, so the
@@ -364,10 +368,10 @@ __device__ __forceinline__ uint32_t flip_mask_field(uint32_t s, uint32_t u0, uin
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
         const int o = 7 * sp;
-        f[sp] = below_field(r, NTh[o]) | (ge1 & below_field(r, NTh[o + 1])) |
-                (ge2 & below_field(r, NTh[o + 2])) | (ge3 & below_field(r, NTh[o + 3])) |
-                (ge4 & below_field(r, NTh[o + 4])) | (ge5 & below_field(r, NTh[o + 5])) |
-                (ge6 & below_field(r, NTh[o + 6]));
+        f[sp] = below_wide(r, NTh[o]) | (ge1 & below_wide(r, NTh[o + 1])) |
+                (ge2 & below_wide(r, NTh[o + 2])) | (ge3 & below_wide(r, NTh[o + 3])) |
+                (ge4 & below_wide(r, NTh[o + 4])) | (ge5 & below_wide(r, NTh[o + 5])) |
+                (ge6 & below_wide(r, NTh[o + 6]));
     }
     return (s & f[1]) | (~s & f[0]);
 }
