@@ -398,6 +398,59 @@ def bench_field(ea, torch, peak_tops, sweeps=200, h=(1, 2)):
     return out
 
 
+# Algorithmic integer ops of the temperature-packed form per flip attempt: a
+# quarter Philox4x32-10 call (one uniform per attempt: 10), three threshold
+# tests and three mask-bit ORs, plus the 24-op bit-sliced update of the site
+# word shared by its NT slots.
+TP_ALG_OPS_PER_FLIP = 16
+
+
+def bench_tpack(ea, torch, peak_tops, sweeps=200):
+    """The temperature-packed form on its workload (few realizations, 32
+    temperatures, one uniform per flip attempt), timed from warm state with L2
+    flushed, beside the realization-packed form computing the same trajectories
+    (realization r as bit 0 of word-group r) per flip of those realizations."""
+    inst = W.TPACK
+    wl = {"sweeps": sweeps, "swap_every": W.TPACK_SWAP_EVERY,
+          "name": (f"EA +-J L={inst.L} ({inst.N} sites), {inst.G} realizations temperature-packed "
+                   f"(one word per realization, copy and site), {inst.NT} temperatures geometric in "
+                   f"[{inst.tmin},{inst.tmax}] x {inst.C} copies, {sweeps} of {W.TPACK_SWEEPS} sweeps "
+                   f"(sample), PT swap every {W.TPACK_SWAP_EVERY} sweeps")}
+    inp = W.draw_tp_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def timed(ens):
+        ens.sweep(wl["sweeps"], wl["swap_every"])            # warm
+        flush.fill_(4)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ens.launches
+        a.record()
+        ens.sweep(wl["sweeps"], wl["swap_every"])
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3, ens.launches - l0
+
+    tp = ea.TPEnsemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
+    t_tp, launches = timed(tp)
+    tp.close()
+    flips = wl["sweeps"] * inst.N * inst.NT * inst.C * inst.G
+    ops = flips * (TP_ALG_OPS_PER_FLIP + 24 / inst.NT)
+    out = {"workload": wl["name"], "value": t_tp / flips * 1e12, "unit": UNIT,
+           "roofline_frac": ops / t_tp / 1e12 / peak_tops, "achieved_tops": ops / t_tp / 1e12,
+           "alg_ops_basis": f"{TP_ALG_OPS_PER_FLIP} per flip attempt + 24 per site-word",
+           "gpu_launches": launches}
+    b, s = W.tp_as_groups(inp["bonds"], inp["spins"], inst.NT)
+    rp = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, b, s, metro, swapt)
+    rp.autotune(probe_sweeps=20, swap_every=wl["swap_every"])
+    t_rp, _ = timed(rp)
+    rp.close()
+    out["packed_form_same_trajectories"] = {"value": t_rp / flips * 1e12, "unit": UNIT,
+                                            "note": "per flip of the same realizations (bit 0 of each group)"}
+    out["speedup_vs_packed_form"] = t_rp / t_tp
+    return out
+
+
 def bench_served(ea, n_requests=32, round_ms=20, load=None, rate_flips_s=None):
     """Poisson-arriving requests (200/s) replayed in real time through the server,
     against serving them one at a time with plain launches (arrival order); the
@@ -670,6 +723,7 @@ def main():
         if world == 1 and not args.no_extras:
             line["large"] = bench_large(ea, torch, peak_tops)
             line["field"] = bench_field(ea, torch, peak_tops)
+            line["tpack"] = bench_tpack(ea, torch, peak_tops)
             line["batched"] = bench_batched(ea, torch)
             line["served"] = bench_served(ea, args.served_requests)
             line["served_load70"] = bench_served(ea, 16, load=0.7,

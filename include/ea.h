@@ -372,6 +372,61 @@ int ea_pt_swap_static(uint32_t *spins, int32_t *energies, const uint32_t *swapt,
                       uint32_t L, uint32_t n_groups, uint32_t n_temps, uint32_t n_copies,
                       uint64_t seed, uint64_t pass_index, uint32_t *masks, void *stream);
 
+/* ---- Temperature-packed form ------------------------------------------------
+ * The word layout of the paper's compact asynchronous multispin coding
+ * (Sec. 3.2 "Map Temperatures Replicas to Bits", Sec. 4.3.3): one 32-bit word
+ * per (realization, copy, site) whose bit t is the spin of temperature slot t,
+ * so the temperature replicas of one realization are updated together and a
+ * replica exchange (Sec. 2.4) permutes bits inside each word.  NT <= 32.
+ *
+ * Random numbers: each realization has its own.  Realization r uses the
+ * counters of word-group r of the realization-packed form above (bit 0 of
+ * that group): Metropolis uniform of (r, slot t, copy c, sweep s, site i) =
+ * output k & 3 of Philox(k >> 2, (colour << 16) | (c << 8) | t, s, r), swap
+ * uniform of pair p in pass P = output 0 of Philox(p << 3, (1 << 24) | (c << 8),
+ * P, r).  Everything else (tables, sweep order, swap rule, energies) is the
+ * method above, so realization r follows exactly the trajectory of realization
+ * 32r of a realization-packed ensemble with the same bonds, spins and tables.
+ * This form spends one uniform per flip attempt instead of one per 32; it
+ * suits ensembles with few realizations and many temperatures.
+ */
+typedef struct ea_tp ea_tp;
+
+typedef struct {
+    uint32_t L;               /* as ea_config (ea_supported_L) */
+    uint32_t n_real;          /* R >= 1 realizations */
+    uint32_t n_temps;         /* 1 <= NT <= 32 */
+    uint32_t n_copies;        /* C in {1, 2} */
+    uint64_t seed;            /* Philox key */
+    const uint8_t *bonds;     /* host [R][3][N]: nonzero <=> J = -1 on bond (i, i + e_d); copied */
+    const uint32_t *spins0;   /* host [R][C][N]: bit t <=> S = +1 in slot t; bits >= NT ignored; copied */
+    const uint32_t *metro;    /* host [NT][3] as ea_config; copied */
+    const uint32_t *swapt;    /* host [NT-1][swap_len] as ea_config; copied */
+    uint32_t swap_len;
+} ea_tp_config;
+
+/* Validates cfg (EA_EINVAL on a bad shape or table, EA_EUNSUPPORTED on L),
+ * allocates the device state, imports the inputs and computes the initial
+ * energies on `stream` (a cudaStream_t, NULL = legacy default stream), and
+ * synchronises that stream once.  *out is owned by the caller until
+ * ea_tp_destroy. */
+int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out);
+/* n_sweeps sweeps, each followed by a swap pass iff swap_every > 0 and
+ * (s + 1) % swap_every == 0 (s global), in one kernel launch.  DEVICE outputs,
+ * each may be NULL: energy_log [n_sweeps][R][NT][C] int32 (energies by slot
+ * after each sweep and its pass), swap_log [passes][R][C] uint32 (bit p =
+ * pair p accepted).  Asynchronous on the context's stream. */
+int ea_tp_sweep(ea_tp *tp, uint32_t n_sweeps, uint32_t swap_every, int32_t *energy_log,
+                uint32_t *swap_log);
+/* Copies the state to DEVICE buffers, each may be NULL: spins [R][C][N] (bit t
+ * = slot t, bits >= NT zero), energies [R][NT][C] int32.  Asynchronous. */
+int ea_tp_read(ea_tp *tp, uint32_t *spins, int32_t *energies);
+/* Global sweep and pass indices and the number of kernels launched so far
+ * (each pointer may be NULL). */
+int ea_tp_info(const ea_tp *tp, uint64_t *sweep_index, uint64_t *pass_index, uint64_t *launches);
+/* Synchronises the context's stream and frees its device memory. */
+void ea_tp_destroy(ea_tp *tp);
+
 /* Static description of an error code. */
 const char *ea_strerror(int code);
 

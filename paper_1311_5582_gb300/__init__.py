@@ -55,6 +55,14 @@ class _Request(ctypes.Structure):
                 ("spins_out", ctypes.c_void_p), ("energies_out", ctypes.c_void_p)]
 
 
+class _TpConfig(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_uint32), ("n_real", ctypes.c_uint32),
+                ("n_temps", ctypes.c_uint32), ("n_copies", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64), ("bonds", ctypes.c_void_p),
+                ("spins0", ctypes.c_void_p), ("metro", ctypes.c_void_p),
+                ("swapt", ctypes.c_void_p), ("swap_len", ctypes.c_uint32)]
+
+
 class _ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
@@ -89,7 +97,8 @@ EXPORTS = ["ea_build_tables", "ea_build_tables_field", "ea_supported_L", "ea_cre
            "ea_batch_sweep_each", "ea_batch_sync", "ea_batch_autotune", "ea_batch_launch_count", "ea_batch_destroy",
            "ea_server_create", "ea_submit", "ea_poll", "ea_server_stats_get", "ea_server_destroy",
            "ea_run",
-           "ea_pt_swap_static", "ea_strerror"]
+           "ea_pt_swap_static", "ea_tp_create", "ea_tp_sweep", "ea_tp_read", "ea_tp_info",
+           "ea_tp_destroy", "ea_strerror"]
 
 
 def load_library(path: str | None = None):
@@ -163,6 +172,12 @@ def load_library(path: str | None = None):
     lib.ea_server_destroy.restype = None
     lib.ea_strerror.argtypes = [i32]
     lib.ea_strerror.restype = ctypes.c_char_p
+    lib.ea_tp_create.argtypes = [ctypes.POINTER(_TpConfig), vp, ctypes.POINTER(vp)]
+    lib.ea_tp_sweep.argtypes = [vp, u32, u32, vp, vp]
+    lib.ea_tp_read.argtypes = [vp, vp, vp]
+    lib.ea_tp_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.ea_tp_destroy.argtypes = [vp]
+    lib.ea_tp_destroy.restype = None
     for name in ("ea_build_tables", "ea_build_tables_field", "ea_create_field", "ea_magnetisations",
                  "ea_supported_L", "ea_create", "ea_sweep", "ea_pt_swap",
                  "ea_measure_planes",
@@ -174,7 +189,8 @@ def load_library(path: str | None = None):
                  "ea_batch_plan_info", "ea_batch_plan_current", "ea_batch_set_width",
                  "ea_batch_autotune", "ea_batch_sweep_each", "ea_batch_set_wait_limit",
                  "ea_batch_inject_stall", "ea_server_create", "ea_submit",
-                 "ea_poll", "ea_server_stats_get"):
+                 "ea_poll", "ea_server_stats_get", "ea_tp_create", "ea_tp_sweep", "ea_tp_read",
+                 "ea_tp_info"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -607,3 +623,93 @@ def ea_pt_swap_static(spins, energies, swapt, L, n_groups, n_temps, n_copies, se
                                  _ptr(swapt) if swap_len else None, swap_len, int(L),
                                  int(n_groups), int(n_temps), int(n_copies), int(seed),
                                  int(pass_index), _ptr(masks), handle), "ea_pt_swap_static")
+
+
+class TPEnsemble:
+    """Temperature-packed ensemble (an ea_tp): R realizations x C copies of an L^3
+    lattice, one word per (realization, copy, site) with bit t = temperature slot t
+    (NT <= 32).  Realization r draws the random numbers of word-group r of the
+    realization-packed form (its bit 0), so it follows the trajectory of
+    realization 32r of an Ensemble with the same inputs.
+
+    bonds: [R][3][N] uint8 (1 <=> J = -1); spins: [R][C][N] uint32 (bit t = slot t)."""
+
+    def __init__(self, L, R, NT, C, seed, bonds, spins, metro, swapt, stream=None):
+        import torch
+        self.lib = load_library()
+        self.L, self.R, self.NT, self.C = int(L), int(R), int(NT), int(C)
+        self.N = self.L ** 3
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.handle, self.stream = _stream_handle(stream)
+        b = np.ascontiguousarray(bonds, np.uint8)
+        sp = np.ascontiguousarray(spins, np.uint32)
+        m = np.ascontiguousarray(metro, np.uint32)
+        w = np.ascontiguousarray(swapt, np.uint32)
+        assert b.shape == (self.R, 3, self.N) and sp.shape == (self.R, self.C, self.N)
+        assert m.shape == (self.NT, 3)
+        self.swap_len = w.shape[1] if w.ndim == 2 else 0
+        cfg = _TpConfig(self.L, self.R, self.NT, self.C, int(seed), b.ctypes.data, sp.ctypes.data,
+                        m.ctypes.data, w.ctypes.data if w.size else None, self.swap_len)
+        h = ctypes.c_void_p(None)
+        _check(self.lib.ea_tp_create(ctypes.byref(cfg), self.handle, ctypes.byref(h)), "ea_tp_create")
+        self.ctx = h
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.ea_tp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _info(self):
+        s, p, n = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        _check(self.lib.ea_tp_info(self.ctx, ctypes.byref(s), ctypes.byref(p), ctypes.byref(n)),
+               "ea_tp_info")
+        return s.value, p.value, n.value
+
+    @property
+    def sweep_index(self) -> int:
+        return self._info()[0]
+
+    @property
+    def pass_index(self) -> int:
+        return self._info()[1]
+
+    @property
+    def launches(self) -> int:
+        return self._info()[2]
+
+    def n_passes(self, n_sweeps: int, swap_every: int) -> int:
+        if swap_every <= 0:
+            return 0
+        s0 = self.sweep_index
+        return (s0 + n_sweeps) // swap_every - s0 // swap_every
+
+    def sweep(self, n_sweeps: int, swap_every: int, energy_log=False, swap_log=False) -> dict:
+        """ea_tp_sweep; returns the requested logs as device tensors:
+        energy_log [n][R][NT][C] int32, swap_log [passes][R][C] int32 (bit p = pair p)."""
+        import torch
+        out = {}
+        el = sl = None
+        if energy_log:
+            el = torch.empty((n_sweeps, self.R, self.NT, self.C), dtype=torch.int32, device=self.device)
+            out["energy_log"] = el
+        if swap_log:
+            sl = torch.zeros((self.n_passes(n_sweeps, swap_every), self.R, self.C), dtype=torch.int32,
+                             device=self.device)
+            out["swap_log"] = sl
+        _check(self.lib.ea_tp_sweep(self.ctx, int(n_sweeps), int(swap_every), _ptr(el),
+                                    _ptr(sl) if sl is not None and sl.numel() else None), "ea_tp_sweep")
+        return out
+
+    def read(self):
+        """(spins [R][C][N] int32 view of the words, energies [R][NT][C] int32), device tensors."""
+        import torch
+        sp = torch.empty((self.R, self.C, self.N), dtype=torch.int32, device=self.device)
+        en = torch.empty((self.R, self.NT, self.C), dtype=torch.int32, device=self.device)
+        _check(self.lib.ea_tp_read(self.ctx, _ptr(sp), _ptr(en)), "ea_tp_read")
+        return sp, en

@@ -143,3 +143,40 @@ def test_field_builder_and_create_reject_bad_fields():
     assert rc(1, 0, mf) == -1
     # h_num = 0 must carry the field-free table: both spin rows equal, 2^32 for u >= 3
     assert rc(0, 1, mf) == -1
+
+
+def _tp_create(L=4, R=2, NT=4, C=2, metro=None, swapt=None, bonds=True, spins=True):
+    lib = ea.load_library()
+    N = L ** 3
+    b = np.zeros((R, 3, N), np.uint8)
+    s = np.zeros((R, C, N), np.uint32)
+    betas = W.geometric_ladder(max(min(NT, 64), 1), 1.0, 2.0)
+    m, w = ea.ea_build_tables(betas, N)
+    m = m if metro is None else metro
+    w = w if swapt is None else swapt
+    cfg = ea._TpConfig(L, R, NT, C, 1, b.ctypes.data if bonds else None, s.ctypes.data if spins else None,
+                       m.ctypes.data, w.ctypes.data if w.size else None, w.shape[1] if w.ndim == 2 else 0)
+    h = ctypes.c_void_p(None)
+    return lib.ea_tp_create(ctypes.byref(cfg), None, ctypes.byref(h)), h
+
+
+def test_tp_create_validates_arguments_before_touching_the_device():
+    """The temperature-packed form rejects bad shapes and tables on the host."""
+    assert _tp_create(NT=33)[0] == -1                    # more slots than bits in a word
+    assert _tp_create(NT=0)[0] == -1
+    assert _tp_create(R=0)[0] == -1
+    assert _tp_create(C=3)[0] == -1
+    assert _tp_create(L=5)[0] == -1                      # odd L
+    assert _tp_create(L=18)[0] == -5                     # even but not compiled
+    assert _tp_create(bonds=False)[0] == -1
+    assert _tp_create(spins=False)[0] == -1
+    bad = np.array([[5, 3, 9]] * 4, np.uint32)           # thresholds must not decrease in u
+    assert _tp_create(metro=bad)[0] == -1
+    w = ea.ea_build_tables(W.geometric_ladder(4, 1.0, 2.0), 64)[1].copy()
+    w[0, :2] = [1, 2]                                    # swap rows must not increase in k
+    assert _tp_create(swapt=w)[0] == -1
+    lib = ea.load_library()
+    assert lib.ea_tp_sweep(None, 1, 1, None, None) == -1
+    assert lib.ea_tp_read(None, None, None) == -1
+    assert lib.ea_tp_info(None, None, None, None) == -1
+    lib.ea_tp_destroy(None)

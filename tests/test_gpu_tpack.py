@@ -1,0 +1,118 @@
+"""GPU parity of the temperature-packed form (ea_tp_*) against the CPU oracle.
+
+Realization r of a temperature-packed ensemble draws the random numbers of
+word-group r of the realization-packed method (its bit 0), so it must follow
+exactly the trajectory the oracle computes for bit 0 of group r when the
+oracle is given the same bonds, spins and tables in its own layout.  Energies,
+swap masks and spins are compared bit for bit (tolerance 0) after every sweep,
+across lattice sizes with ragged quad counts (L = 6, 10, 12, 14), the
+shared-memory and global-memory bond paths (L <= 24, L = 32), one and two
+copies, 1 to 32 temperatures, and calls split at arbitrary sweeps.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1311_5582_gb300 as ea  # noqa: E402
+
+
+def _inputs(L, R, NT, C, seed):
+    inst = W.Instance(L=L, G=R, NT=NT, C=C, seed=seed, tmin=0.8, tmax=2.0, input_seed=900 + L * 37 + NT)
+    inp = W.draw_tp_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    return inst, inp, metro, swapt
+
+
+def _oracle(inst, inp, metro, swapt):
+    b, s = W.tp_as_groups(inp["bonds"], inp["spins"], inst.NT)
+    return oracle.OracleSim(inst.L, inst.G, inst.NT, inst.C, inst.seed, b, s, metro, swapt)
+
+
+def _tp_from_oracle_spins(sp, NT):
+    """Oracle spins [R][NT][C][N] (bit 0) -> temperature-packed words [R][C][N]."""
+    R, _, C, N = sp.shape
+    out = np.zeros((R, C, N), np.uint32)
+    for t in range(NT):
+        out |= (sp[:, t] & np.uint32(1)) << np.uint32(t)
+    return out
+
+
+def _compare_calls(L, R, NT, C, calls, swap_every, seed=77):
+    inst, inp, metro, swapt = _inputs(L, R, NT, C, seed)
+    gpu = ea.TPEnsemble(L, R, NT, C, seed, inp["bonds"], inp["spins"], metro, swapt)
+    sim = _oracle(inst, inp, metro, swapt)
+    sp0, en0 = gpu.read()
+    np.testing.assert_array_equal(en0.cpu().numpy(), sim.energies()[..., 0], err_msg="initial energies")
+    for k, n in enumerate(calls):
+        out = gpu.sweep(n, swap_every, energy_log=True, swap_log=True)
+        ref = sim.sweep(n, swap_every, energy_log=True, swap_log=True, threads=8)
+        el = out["energy_log"].cpu().numpy()
+        np.testing.assert_array_equal(el, ref["energy_log"][..., 0], err_msg=f"energy log, call {k}")
+        sl = out["swap_log"].cpu().numpy().view(np.uint32)
+        rl = ref["swap_log"] & np.uint32(1)                          # [passes][R][C][NT-1]
+        want = np.zeros(sl.shape, np.uint32)
+        for p in range(NT - 1):
+            want |= rl[..., p] << np.uint32(p)
+        np.testing.assert_array_equal(sl, want, err_msg=f"swap log, call {k}")
+        sp, en = gpu.read()
+        np.testing.assert_array_equal(sp.cpu().numpy().view(np.uint32),
+                                      _tp_from_oracle_spins(sim.spins(), NT), err_msg=f"spins, call {k}")
+        np.testing.assert_array_equal(en.cpu().numpy(), sim.energies()[..., 0], err_msg=f"energies, call {k}")
+    assert gpu.sweep_index == sum(calls)
+    assert gpu.pass_index == sim.pass_index
+    return gpu
+
+
+@pytest.mark.parametrize("L,R,NT,C,n,swap_every", [
+    (4, 3, 16, 2, 60, 1),      # the smallest configuration's shape, one realization per word
+    (6, 2, 5, 1, 40, 3),       # ragged quad count (27 quads), one copy
+    (8, 4, 24, 2, 30, 1),      # the scale configuration's ladder
+    (10, 2, 32, 2, 20, 2),     # full words, 125 quads
+    (12, 2, 7, 2, 16, 1),      # two quads a thread group, ragged
+    (14, 1, 2, 2, 12, 1),      # one pair
+    (16, 2, 32, 2, 12, 10),    # the largest configuration's ladder
+    (20, 1, 9, 1, 6, 2),
+    (24, 1, 32, 2, 4, 1),      # 221 KB of shared memory
+    (32, 1, 32, 2, 3, 1),      # bonds read from global memory
+])
+def test_tpack_matches_oracle(L, R, NT, C, n, swap_every):
+    _compare_calls(L, R, NT, C, [n], swap_every)
+
+
+def test_tpack_single_temperature_has_no_swaps():
+    gpu = _compare_calls(8, 2, 1, 2, [15], 1)
+    assert gpu.pass_index == 15          # passes are counted; with one slot they exchange nothing
+
+
+def test_tpack_calls_split_anywhere():
+    # pass indices and sweep counters continue across calls, swap every 3 sweeps
+    _compare_calls(8, 3, 12, 2, [5, 1, 7, 4], 3)
+
+
+def test_tpack_realization_matches_bit0_of_the_packed_form():
+    """Realization r equals realization 32r of the realization-packed GPU form."""
+    L, R, NT, C, n = 8, 3, 16, 2, 25
+    inst, inp, metro, swapt = _inputs(L, R, NT, C, 5)
+    tp = ea.TPEnsemble(L, R, NT, C, 5, inp["bonds"], inp["spins"], metro, swapt)
+    b, s = W.tp_as_groups(inp["bonds"], inp["spins"], NT)
+    rng = np.random.Generator(np.random.PCG64(1))
+    # the other 31 realizations of each group are unrelated random ones
+    b = b | (rng.integers(0, 2**32, size=b.shape, dtype=np.uint64).astype(np.uint32) & np.uint32(~1 & 0xFFFFFFFF))
+    s = s | (rng.integers(0, 2**32, size=s.shape, dtype=np.uint64).astype(np.uint32) & np.uint32(~1 & 0xFFFFFFFF))
+    rp = ea.Ensemble(L, R, NT, C, 5, b, s, metro, swapt)
+    o1 = tp.sweep(n, 1, energy_log=True)
+    o2 = rp.sweep(n, 1, energy_log=True)
+    np.testing.assert_array_equal(o1["energy_log"].cpu().numpy(), o2["energy_log"].cpu().numpy()[..., 0])
+    sp, _ = tp.read()
+    np.testing.assert_array_equal(sp.cpu().numpy().view(np.uint32),
+                                  _tp_from_oracle_spins(rp.read_spins().cpu().numpy().view(np.uint32), NT))

@@ -70,6 +70,43 @@ def draw_inputs(inst: Instance) -> dict:
     return {"bonds": bonds, "spins": spins, "betas": betas}
 
 
+def draw_tp_inputs(inst: Instance) -> dict:
+    """Inputs of the temperature-packed form for ``inst.G`` realizations.
+
+    bonds [R][3][N] uint8 (1 <=> J = -1), each a fair coin; spins [R][C][N]
+    uint32 with bit t (t < NT) the initial spin of slot t, each a fair coin
+    (bits at or above NT zero); betas as ``draw_inputs``.  R = inst.G here:
+    one realization per entry, not 32.
+    """
+    rng = np.random.Generator(np.random.PCG64(inst.input_seed))
+    N = inst.N
+    bonds = rng.integers(0, 2, size=(inst.G, 3, N), dtype=np.uint8)
+    spins = rng.integers(0, 2**32, size=(inst.G, inst.C, N), dtype=np.uint64).astype(np.uint32)
+    if inst.NT < 32:
+        spins &= np.uint32((1 << inst.NT) - 1)
+    betas = geometric_ladder(inst.NT, inst.tmin, inst.tmax)
+    return {"bonds": bonds, "spins": spins, "betas": betas}
+
+
+def tp_as_groups(bonds: np.ndarray, spins: np.ndarray, NT: int) -> tuple[np.ndarray, np.ndarray]:
+    """Temperature-packed inputs rewritten in the realization-packed layout with
+    realization r as bit 0 of word-group r (the other 31 bits zero): bonds
+    [R][3][N] uint32, spins [R][NT][C][N] uint32.  A pure change of layout."""
+    R, C, N = spins.shape
+    b = bonds.astype(np.uint32) & np.uint32(1)
+    s = np.zeros((R, NT, C, N), np.uint32)
+    for t in range(NT):
+        s[:, t] = (spins >> np.uint32(t)) & np.uint32(1)
+    return b, s
+
+
+# Few realizations, many temperatures: the temperature-packed form's workload
+# (R = G realizations, one per word).
+TPACK = Instance(L=16, G=76, NT=32, C=2, seed=6, tmin=0.95, tmax=2.0, input_seed=106)
+TPACK_SWEEPS = 2000
+TPACK_SWAP_EVERY = 10
+
+
 # The five workloads of the hot path.  Shapes follow the ensembles of Sec. 5.2
 # (lattices of 8^3..16^3, 24-56 temperatures, swaps every 1-10 sweeps) scaled to
 # a GB300: realizations packed 32 per word, two copies per temperature for the
