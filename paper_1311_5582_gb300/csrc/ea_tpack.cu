@@ -35,7 +35,7 @@ namespace ea {
 namespace {
 
 constexpr int kTpMaxTemps = 32;
-constexpr int kTpThreads = 512;
+constexpr int kTpThreads = 1024;   // at most 64 registers a thread
 
 struct TpLaunch {
     uint32_t *spins;            // [R][C][2][H] by slot bit
@@ -116,6 +116,25 @@ __device__ __forceinline__ void tp_acc_add3(uint32_t (&acc)[kPlanes], uint32_t x
     }
 }
 
+// Sets bit t of m_k[x] iff uniform x of v is below threshold k of slot t.  The
+// tests are wide multiply-adds on the FMA pipe (below_wide).  Bit t of m_0 is
+// ORed in on the integer ALU pipe; those of m_1 and m_2 are added on the FMA
+// pipe as m += below * (-2^t) (below is 0 or all ones and bit t is still
+// clear), which balances the two pipes (the Philox rounds load both).
+__device__ __forceinline__ void tp_mask_bits(uint32_t (&m0)[4], uint32_t (&m1)[4], uint32_t (&m2)[4],
+                                             const uint4 v, const uint64_t *th, int t)
+{
+    const uint64_t n0 = th[0], n1 = th[1], n2 = th[2];
+    const uint32_t negbit = 0u - (1u << t);
+    const uint32_t rr[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        m0[x] |= below_wide(rr[x], n0) & (0u - negbit);
+        m1[x] = below_wide(rr[x], n1) * negbit + m1[x];
+        m2[x] = below_wide(rr[x], n2) * negbit + m2[x];
+    }
+}
+
 // One half-sweep (colour col) of one unit.  Thread (quad group qg, site i)
 // takes quads qg, qg + nqg, ...; the trip count qper is the same for every
 // thread so that the whole warp takes part in each shuffle.  MODE 0: update
@@ -138,15 +157,7 @@ __device__ __forceinline__ void tp_half(uint32_t *S, const uint32_t *J, const ui
             if (inq) {
                 for (int t = i; t < NT; t += 4) {
                     const uint4 v = philox((uint32_t)q, ctag | (uint32_t)t, s, r, rk);
-                    const uint64_t n0 = nthr[3 * t], n1 = nthr[3 * t + 1], n2 = nthr[3 * t + 2];
-                    const uint32_t bit = 1u << t;
-                    const uint32_t rr[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int x = 0; x < 4; ++x) {
-                        m0[x] |= below_wide(rr[x], n0) & bit;
-                        m1[x] |= below_wide(rr[x], n1) & bit;
-                        m2[x] |= below_wide(rr[x], n2) & bit;
-                    }
+                    tp_mask_bits(m0, m1, m2, v, nthr + 3 * t, t);
                 }
             }
 #pragma unroll
