@@ -202,10 +202,11 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(wl, budget_s=15.0, threads=None):
+def cpu_baseline(wl, budget_s=15.0, threads=None, single_thread_s=3.0):
     """The oracle as it stands, on this host's cores, on a bounded sample of the
     workload: the first `threads` word-groups for as many sweeps (from sweep 0,
-    same schedule and measurement) as fit the time budget."""
+    same schedule and measurement) as fit the time budget; beside it the oracle
+    on one core and one word-group."""
     import oracle
     inst = wl["inst"]
     threads = threads or max(1, min(os.cpu_count() or 1, inst.G))
@@ -229,9 +230,17 @@ def cpu_baseline(wl, budget_s=15.0, threads=None):
     n = max(10, int(10 * budget_s / max(t_probe, 1e-3)))
     t = run(n)
     flips = n * inst.N * inst.NT * inst.C * 32 * g
-    return {"value": t / flips * 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{g} of {inst.G} word-groups ({32 * g} realizations), {n} sweeps "
-                      f"with the same swap and measurement schedule, {t:.1f} s"}
+    out = {"value": t / flips * 1e12, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{g} of {inst.G} word-groups ({32 * g} realizations), {n} sweeps "
+                     f"with the same swap and measurement schedule, {t:.1f} s"}
+    # one core, one word-group: the figure comparable to a single-thread CPU code
+    g, threads = 1, 1
+    t1 = run(10)
+    n1 = max(10, int(10 * single_thread_s / max(t1, 1e-3)))
+    t1 = run(n1)
+    out["single_thread"] = {"value": t1 / (n1 * inst.N * inst.NT * inst.C * 32) * 1e12, "unit": UNIT,
+                            "cores": 1, "sample": f"1 word-group (32 realizations), {n1} sweeps, {t1:.1f} s"}
+    return out
 
 
 def _flips(inst, sweeps):
@@ -575,7 +584,14 @@ def main():
     ap.add_argument("--served-requests", type=int, default=32)
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched mix with default plans (--sweeps sweeps) and print its object")
+    ap.add_argument("--tpack-only", action="store_true",
+                    help="run only the temperature-packed workload (--sweeps sweeps) and print its object")
     args = ap.parse_args()
+    if args.tpack_only:
+        import torch
+        import paper_1311_5582_gb300 as ea
+        print(json.dumps(bench_tpack(ea, torch, _alu_peak_tops(torch), sweeps=args.sweeps or 200)))
+        return 0
     if args.batched_only:
         import torch
         import paper_1311_5582_gb300 as ea
