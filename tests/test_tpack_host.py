@@ -1,0 +1,49 @@
+"""The swap pass of the temperature-packed form as one bit permutation (CPU).
+
+The kernel applies a replica-exchange pass (pairs p = 0..NT-2 in order, pair p
+exchanging slots p and p+1 of a realization when bit p of the accepted mask M
+is set; Sec. 2.4) to a word whose bit t is slot t by the closed form
+
+    new = ((w >> 1) & M) | ((M + (starts & w)) & ends),
+    ends = ~M & valid,  starts = ((~M << 1) | 1) & valid,
+
+because an accepted run of pairs a..b-1 rotates slots a..b by one, and adding
+the bit at a to M carries it through the run's ones to b.  This test checks that
+identity against the pass applied pair by pair, exhaustively for NT <= 10 and
+on random words and masks for NT up to 32.
+"""
+import numpy as np
+
+
+def closed_form(w, M, NT):
+    valid = (1 << NT) - 1
+    ends = ~M & valid
+    starts = ((~M << 1) | 1) & valid
+    return (((w >> 1) & M) | ((M + (starts & w)) & ends)) & 0xFFFFFFFF
+
+
+def pair_by_pair(w, M, NT):
+    bits = [(w >> t) & 1 for t in range(NT)]
+    for p in range(NT - 1):
+        if (M >> p) & 1:
+            bits[p], bits[p + 1] = bits[p + 1], bits[p]
+    return sum(b << t for t, b in enumerate(bits))
+
+
+def test_exhaustive_small_ladders():
+    for NT in range(1, 9):
+        for M in range(1 << max(NT - 1, 0)):
+            for w in range(1 << NT):
+                assert closed_form(w, M, NT) == pair_by_pair(w, M, NT), (NT, M, w)
+
+
+def test_random_words_up_to_32_slots():
+    rng = np.random.Generator(np.random.PCG64(7))
+    for NT in (9, 10, 16, 24, 31, 32):
+        for _ in range(3000):
+            M = int(rng.integers(0, 1 << (NT - 1)))
+            w = int(rng.integers(0, 1 << NT))
+            assert closed_form(w, M, NT) == pair_by_pair(w, M, NT), (NT, M, w)
+        # all pairs accepted: the coldest configuration moves to the hottest slot
+        M = (1 << (NT - 1)) - 1
+        assert closed_form(1, M, NT) == 1 << (NT - 1)
