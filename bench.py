@@ -457,6 +457,20 @@ def bench_tpack(ea, torch, peak_tops, sweeps=200):
     out["packed_form_same_trajectories"] = {"value": t_rp / flips * 1e12, "unit": UNIT,
                                             "note": "per flip of the same realizations (bit 0 of each group)"}
     out["speedup_vs_packed_form"] = t_rp / t_tp
+    # few realizations: 8 x 2 units, each split into slot groups, against one CTA per unit
+    few = W.Instance(L=inst.L, G=8, NT=inst.NT, C=inst.C, seed=7, tmin=inst.tmin, tmax=inst.tmax,
+                     input_seed=107)
+    fi = W.draw_tp_inputs(few)
+    tp = ea.TPEnsemble(few.L, few.G, few.NT, few.C, few.seed, fi["bonds"], fi["spins"], metro, swapt)
+    k = tp.split
+    t_split, l_split = timed(tp)
+    tp.set_split(1)
+    t_one, _ = timed(tp)
+    tp.close()
+    f_few = wl["sweeps"] * few.N * few.NT * few.C * few.G
+    out["few_realizations"] = {"realizations": few.G, "value": t_split / f_few * 1e12, "unit": UNIT,
+                               "slot_groups": k, "gpu_launches": l_split,
+                               "one_cta_per_unit": t_one / f_few * 1e12, "speedup": t_one / t_split}
     return out
 
 

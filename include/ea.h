@@ -421,9 +421,20 @@ int ea_tp_sweep(ea_tp *tp, uint32_t n_sweeps, uint32_t swap_every, int32_t *ener
 /* Copies the state to DEVICE buffers, each may be NULL: spins [R][C][N] (bit t
  * = slot t, bits >= NT zero), energies [R][NT][C] int32.  Asynchronous. */
 int ea_tp_read(ea_tp *tp, uint32_t *spins, int32_t *energies);
-/* Global sweep and pass indices and the number of kernels launched so far
- * (each pointer may be NULL). */
-int ea_tp_info(const ea_tp *tp, uint64_t *sweep_index, uint64_t *pass_index, uint64_t *launches);
+/* Global sweep and pass indices, the number of kernels launched so far and
+ * the number of slot groups per (realization, copy) unit (each pointer may be
+ * NULL). */
+int ea_tp_info(const ea_tp *tp, uint64_t *sweep_index, uint64_t *pass_index, uint64_t *launches,
+               uint32_t *split);
+/* Splits each (realization, copy) unit into k slot groups (k a power of two,
+ * 1 <= k <= min(32, NT); groups of ceil(NT / k) slots, empty ones dropped), one
+ * CTA each: slots do not interact between swap passes, so every group sweeps
+ * its own slots up to the next pass and a merge launch then combines the groups
+ * and runs the pass.  Results do not depend on k.  ea_tp_create picks the
+ * smallest k <= 8 that gives at least one CTA per SM (1 when R * C fills the
+ * GPU).  May allocate device memory (k - 1 more copies of the spins);
+ * synchronises the stream when it frees some.  EA_EINVAL for another k. */
+int ea_tp_set_split(ea_tp *tp, uint32_t k);
 /* Synchronises the context's stream and frees its device memory. */
 void ea_tp_destroy(ea_tp *tp);
 

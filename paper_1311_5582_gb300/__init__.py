@@ -98,7 +98,7 @@ EXPORTS = ["ea_build_tables", "ea_build_tables_field", "ea_supported_L", "ea_cre
            "ea_server_create", "ea_submit", "ea_poll", "ea_server_stats_get", "ea_server_destroy",
            "ea_run",
            "ea_pt_swap_static", "ea_tp_create", "ea_tp_sweep", "ea_tp_read", "ea_tp_info",
-           "ea_tp_destroy", "ea_strerror"]
+           "ea_tp_set_split", "ea_tp_destroy", "ea_strerror"]
 
 
 def load_library(path: str | None = None):
@@ -175,7 +175,9 @@ def load_library(path: str | None = None):
     lib.ea_tp_create.argtypes = [ctypes.POINTER(_TpConfig), vp, ctypes.POINTER(vp)]
     lib.ea_tp_sweep.argtypes = [vp, u32, u32, vp, vp]
     lib.ea_tp_read.argtypes = [vp, vp, vp]
-    lib.ea_tp_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.ea_tp_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                               ctypes.POINTER(u32)]
+    lib.ea_tp_set_split.argtypes = [vp, u32]
     lib.ea_tp_destroy.argtypes = [vp]
     lib.ea_tp_destroy.restype = None
     for name in ("ea_build_tables", "ea_build_tables_field", "ea_create_field", "ea_magnetisations",
@@ -190,7 +192,7 @@ def load_library(path: str | None = None):
                  "ea_batch_autotune", "ea_batch_sweep_each", "ea_batch_set_wait_limit",
                  "ea_batch_inject_stall", "ea_server_create", "ea_submit",
                  "ea_poll", "ea_server_stats_get", "ea_tp_create", "ea_tp_sweep", "ea_tp_read",
-                 "ea_tp_info"):
+                 "ea_tp_info", "ea_tp_set_split"):
         getattr(lib, name).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -666,10 +668,19 @@ class TPEnsemble:
             pass
 
     def _info(self):
-        s, p, n = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
-        _check(self.lib.ea_tp_info(self.ctx, ctypes.byref(s), ctypes.byref(p), ctypes.byref(n)),
-               "ea_tp_info")
-        return s.value, p.value, n.value
+        s, p, n, k = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint32(0)
+        _check(self.lib.ea_tp_info(self.ctx, ctypes.byref(s), ctypes.byref(p), ctypes.byref(n),
+                                   ctypes.byref(k)), "ea_tp_info")
+        return s.value, p.value, n.value, k.value
+
+    @property
+    def split(self) -> int:
+        """Slot groups (CTAs) per (realization, copy) unit."""
+        return self._info()[3]
+
+    def set_split(self, k: int):
+        """ea_tp_set_split: k slot groups per unit (a power of two <= min(32, NT))."""
+        _check(self.lib.ea_tp_set_split(self.ctx, int(k)), "ea_tp_set_split")
 
     @property
     def sweep_index(self) -> int:

@@ -52,6 +52,11 @@ struct TpLaunch {
     uint32_t pass_local0;       // row of swap_log for that pass
     int32_t *energy_log;        // [n_sweeps][R][NT][C] or null
     uint32_t *swap_log;         // [passes][R][C] or null
+    // slot split: CTA (unit, blockIdx.y) owns slots [y * spg, (y + 1) * spg) and
+    // writes them to slices[y]; null = one CTA per unit owning every slot
+    uint32_t *slices;           // [nsplit][R][C][2][H]
+    uint32_t spg;               // slots per group
+    uint32_t nsplit;            // groups (gridDim.y)
 };
 
 // The words a site update reads: own spin word, its six neighbours and the six
@@ -135,14 +140,15 @@ __device__ __forceinline__ void tp_mask_bits(uint32_t (&m0)[4], uint32_t (&m1)[4
     }
 }
 
-// One half-sweep (colour col) of one unit.  Thread (quad group qg, site i)
-// takes quads qg, qg + nqg, ...; the trip count qper is the same for every
-// thread so that the whole warp takes part in each shuffle.  MODE 0: update
+// One half-sweep (colour col) of one unit, slots [t_lo, t_hi) (omask = their
+// bits; the other bits of the words are left as they are).  Thread (quad group
+// qg, site i) takes quads qg, qg + nqg, ...; the trip count qper is the same
+// for every thread so that the whole warp takes part in each shuffle.  MODE 0: update
 // without counting; 1: update and count the post-update unsatisfied bonds of
 // the (colour-1) sites; 2: count the current unsatisfied bonds, no update.
 template <int L, int MODE>
 __device__ __forceinline__ void tp_half(uint32_t *S, const uint32_t *J, const uint64_t *nthr, int col,
-                                        int qg, int nqg, int qper, int i, int NT, uint32_t valid,
+                                        int qg, int nqg, int qper, int i, int t_lo, int t_hi, uint32_t omask,
                                         uint32_t s, uint32_t r, uint32_t ctag, const RoundKeys &rk,
                                         uint32_t (&acc)[kPlanes])
 {
@@ -155,7 +161,7 @@ __device__ __forceinline__ void tp_half(uint32_t *S, const uint32_t *J, const ui
         if constexpr (MODE != 2) {
             uint32_t m0[4] = {0u, 0u, 0u, 0u}, m1[4] = {0u, 0u, 0u, 0u}, m2[4] = {0u, 0u, 0u, 0u};
             if (inq) {
-                for (int t = i; t < NT; t += 4) {
+                for (int t = t_lo + i; t < t_hi; t += 4) {
                     const uint4 v = philox((uint32_t)q, ctag | (uint32_t)t, s, r, rk);
                     tp_mask_bits(m0, m1, m2, v, nthr + 3 * t, t);
                 }
@@ -182,7 +188,7 @@ __device__ __forceinline__ void tp_half(uint32_t *S, const uint32_t *J, const ui
             u0 = a0 ^ b0;
             full_add(a1, b1, a0 & b0, u1, u2);
             const uint32_t ge3 = u2 | (u1 & u0), ge2 = u2 | u1, ge1 = ge2 | u0;
-            f = (ge3 | (ge2 & M2) | (ge1 & M1) | M0) & valid;
+            f = (ge3 | (ge2 & M2) | (ge1 & M1) | M0) & omask;
             S[col * H + 4 * q + i] = own ^ f;
             if constexpr (MODE == 1) {
                 // flipped sites hold 6 - u unsatisfied bonds
@@ -205,10 +211,11 @@ __device__ __forceinline__ void tp_half(uint32_t *S, const uint32_t *J, const ui
     }
 }
 
-// Adds 2 x (the warp's per-slot counts) into E[t]: a shuffle butterfly of
-// bit-sliced adders leaves the warp total (kPlanes + 5 planes) in every lane,
-// then lane t reads bit t of each plane.
-__device__ __forceinline__ void tp_reduce_energy(const uint32_t (&acc)[kPlanes], int *E, int lane, int NT)
+// Adds 2 x (the warp's per-slot counts) into E[t], t in [t_lo, t_hi): a
+// shuffle butterfly of bit-sliced adders leaves the warp total (kPlanes + 5
+// planes) in every lane, then lane t reads bit t of each plane.
+__device__ __forceinline__ void tp_reduce_energy(const uint32_t (&acc)[kPlanes], int *E, int lane, int t_lo,
+                                                 int t_hi)
 {
     constexpr int PT = kPlanes + 5;
     uint32_t v[PT];
@@ -229,7 +236,7 @@ __device__ __forceinline__ void tp_reduce_energy(const uint32_t (&acc)[kPlanes],
     int cnt = 0;
 #pragma unroll
     for (int p = 0; p < PT; ++p) cnt += (int)((v[p] >> lane) & 1u) << p;
-    if (lane < NT && cnt != 0) atomicAdd(&E[lane], 2 * cnt);
+    if (lane >= t_lo && lane < t_hi && cnt != 0) atomicAdd(&E[lane], 2 * cnt);
 }
 
 // Layout of the dynamic shared memory: spins [2][H], then (J_SMEM) bonds [3][2][H].
@@ -251,6 +258,10 @@ k_tp_sweep(TpLaunch a, int recompute_only)
     const int i = tid & 3, qg = tid >> 2, nqg = nthr_cta >> 2;
     const int qper = (Q + nqg - 1) / nqg;
     const uint32_t valid = NT >= 32 ? kFull : ((1u << NT) - 1u);
+    // slots this CTA updates
+    const int t_lo = a.slices ? (int)(blockIdx.y * a.spg) : 0;
+    const int t_hi = a.slices ? min(NT, t_lo + (int)a.spg) : NT;
+    const uint32_t own = (t_hi >= 32 ? kFull : ((1u << t_hi) - 1u)) & ~((1u << t_lo) - 1u);
 
     uint32_t *gS = a.spins + (size_t)unit * N;
     const uint32_t *gJ = a.bonds + (size_t)r * 3 * N;
@@ -271,8 +282,8 @@ k_tp_sweep(TpLaunch a, int recompute_only)
     if (recompute_only) {
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-        tp_half<L, 2>(S, J, nthr, 1, qg, nqg, qper, i, NT, valid, 0u, r, 0u, a.rk, acc);
-        tp_reduce_energy(acc, E, lane, NT);
+        tp_half<L, 2>(S, J, nthr, 1, qg, nqg, qper, i, 0, NT, valid, 0u, r, 0u, a.rk, acc);
+        tp_reduce_energy(acc, E, lane, 0, NT);
         __syncthreads();
         if (tid < kTpMaxTemps) a.energy[(size_t)unit * kLanes + tid] = tid < NT ? E[tid] : 0;
         return;
@@ -286,15 +297,15 @@ k_tp_sweep(TpLaunch a, int recompute_only)
         const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
         const bool needE = swap_now || a.energy_log != nullptr || (n + 1 == a.n_sweeps);
         if (needE && tid < kTpMaxTemps) E[tid] = -3 * N;
-        tp_half<L, 0>(S, J, nthr, 0, qg, nqg, qper, i, NT, valid, (uint32_t)s, r, tag0, a.rk, acc);
+        tp_half<L, 0>(S, J, nthr, 0, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, r, tag0, a.rk, acc);
         __syncthreads();
         if (needE) {
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-            tp_half<L, 1>(S, J, nthr, 1, qg, nqg, qper, i, NT, valid, (uint32_t)s, r, tag1, a.rk, acc);
-            tp_reduce_energy(acc, E, lane, NT);
+            tp_half<L, 1>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, r, tag1, a.rk, acc);
+            tp_reduce_energy(acc, E, lane, t_lo, t_hi);
         } else {
-            tp_half<L, 0>(S, J, nthr, 1, qg, nqg, qper, i, NT, valid, (uint32_t)s, r, tag1, a.rk, acc);
+            tp_half<L, 0>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, r, tag1, a.rk, acc);
         }
         __syncthreads();
         if (swap_now) {
@@ -339,14 +350,77 @@ k_tp_sweep(TpLaunch a, int recompute_only)
             ++P;
             ++pass_local;
         }
-        if (a.energy_log != nullptr && tid < NT)
+        if (a.energy_log != nullptr && tid >= t_lo && tid < t_hi)
             a.energy_log[(((size_t)n * a.R + r) * NT + tid) * a.C + c] = E[tid];
         // E is rewritten at the top of the next sweep only by the thread that logged it
     }
     __syncthreads();
-    for (int w = tid; w < N / 4; w += nthr_cta)
-        __stcg(reinterpret_cast<uint4 *>(gS) + w, reinterpret_cast<const uint4 *>(S)[w]);
-    if (tid < kTpMaxTemps) a.energy[(size_t)unit * kLanes + tid] = tid < NT ? E[tid] : 0;
+    if (a.slices) {
+        // this group's bits go to its slice; the merge kernel ORs the slices
+        uint32_t *sl = a.slices + ((size_t)blockIdx.y * gridDim.x + unit) * N;
+        for (int w = tid; w < N / 4; w += nthr_cta) {
+            const uint4 x = reinterpret_cast<const uint4 *>(S)[w];
+            __stcg(reinterpret_cast<uint4 *>(sl) + w, make_uint4(x.x & own, x.y & own, x.z & own, x.w & own));
+        }
+    } else {
+        for (int w = tid; w < N / 4; w += nthr_cta)
+            __stcg(reinterpret_cast<uint4 *>(gS) + w, reinterpret_cast<const uint4 *>(S)[w]);
+    }
+    if (tid >= t_lo && tid < t_hi) a.energy[(size_t)unit * kLanes + tid] = E[tid];
+    else if (!a.slices && tid < kTpMaxTemps) a.energy[(size_t)unit * kLanes + tid] = 0;
+}
+
+// Slot-split form: merges the groups' slices into the unit's words and, with
+// do_swap, runs the swap pass on them (one CTA per unit): warp 0 takes the
+// decision chain as in k_tp_sweep, then every word gets the pass's bit
+// permutation.  elog_row (or null): the energy-log row of the interval's last
+// sweep, rewritten with the energies after the pass.
+__global__ void __launch_bounds__(256)
+k_tp_merge(TpLaunch a, int N, int do_swap, uint64_t P, uint32_t pass_local, int32_t *elog_row)
+{
+    __shared__ uint32_t smask;
+    const uint32_t unit = blockIdx.x;
+    const uint32_t c = unit % a.C, r = unit / a.C;
+    const int NT = (int)a.NT, tid = threadIdx.x, lane = tid & 31;
+    const uint32_t valid = NT >= 32 ? kFull : ((1u << NT) - 1u);
+    if (tid < 32) {
+        int32_t *Eg = a.energy + (size_t)unit * kLanes;
+        const int e = lane < NT ? Eg[lane] : 0;
+        uint32_t m = 0;
+        int mine = e;
+        if (do_swap) {
+            int bnd = 0;
+            if (lane + 1 < NT) {
+                const uint4 v = philox((uint32_t)lane << 3, (1u << 24) | (c << 8), (uint32_t)P, r, a.rk);
+                bnd = accept_bound(a.swapt + (size_t)lane * a.swap_len, a.swap_len, v.x);
+            }
+            int cur = __shfl_sync(kFull, e, 0);
+            for (int p = 0; p + 1 < NT; ++p) {
+                const int nx = __shfl_sync(kFull, e, p + 1);
+                const int bp = __shfl_sync(kFull, bnd, p);
+                const bool ok = cur - nx >= bp;
+                if (lane == p) mine = ok ? nx : cur;
+                cur = ok ? cur : nx;
+                m |= (uint32_t)ok << p;
+            }
+            if (lane == NT - 1) mine = cur;
+            if (lane < NT) Eg[lane] = mine;
+            if (lane == 0 && a.swap_log) a.swap_log[((size_t)pass_local * a.R + r) * a.C + c] = m;
+            if (elog_row && lane < NT) elog_row[((size_t)r * NT + lane) * a.C + c] = mine;
+        }
+        if (lane == 0) smask = m;
+    }
+    __syncthreads();
+    const uint32_t M = smask, ends = ~M & valid, starts = ((~M << 1) | 1u) & valid;
+    const size_t stride = (size_t)gridDim.x * N;
+    const uint32_t *src = a.slices + (size_t)unit * N;
+    uint32_t *dst = a.spins + (size_t)unit * N;
+    for (int w = tid; w < N; w += blockDim.x) {
+        uint32_t x = 0;
+        for (uint32_t g = 0; g < a.nsplit; ++g) x |= __ldcg(src + g * stride + w);
+        if (do_swap) x = ((x >> 1) & M) | ((M + (starts & x)) & ends);
+        dst[w] = x;
+    }
 }
 
 // spins: API [R][C][N] (site order) <-> device [R][C][2][H] (colour-split), bits >= NT cleared on import.
@@ -434,7 +508,8 @@ cudaError_t tp_launch_L(const TpLaunch &a, int recompute_only, cudaStream_t st)
     const cudaError_t e = cudaFuncSetAttribute(k_tp_sweep<L, JS>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_tp_sweep<L, JS><<<a.R * a.C, tp_threads(L), smem, st>>>(a, recompute_only);
+    const dim3 grid(a.R * a.C, a.slices ? a.nsplit : 1);
+    k_tp_sweep<L, JS><<<grid, tp_threads(L), smem, st>>>(a, recompute_only);
     return cudaGetLastError();
 }
 
@@ -460,6 +535,8 @@ struct ea_tp {
     int32_t *d_energy;
     uint64_t sweep, pass, launches;
     ea::RoundKeys rk;
+    uint32_t split, spg, nsplit;   // requested groups, slots per group, groups in use
+    uint32_t *d_slices;            // [nsplit][R][C][N] when nsplit > 1
 };
 
 namespace {
@@ -474,7 +551,30 @@ void tp_free(ea_tp *t)
     cudaFree(t->d_swapt);
     cudaFree(t->d_nthr);
     cudaFree(t->d_energy);
+    cudaFree(t->d_slices);
     delete t;
+}
+
+// Slot groups per unit: k groups of ceil(NT / k) slots (the groups in use are
+// the non-empty ones); slices for them are (re)allocated here.
+int tp_apply_split(ea_tp *t, uint32_t k)
+{
+    const uint32_t spg = (t->NT + k - 1) / k;
+    const uint32_t nsplit = (t->NT + spg - 1) / spg;
+    if (t->d_slices && nsplit != t->nsplit) {
+        const cudaError_t e = cudaStreamSynchronize(t->stream);
+        if (e != cudaSuccess) return tp_cuda_fail(e);
+        cudaFree(t->d_slices);
+        t->d_slices = nullptr;
+    }
+    if (nsplit > 1 && !t->d_slices) {
+        const cudaError_t e = cudaMalloc(&t->d_slices, (size_t)nsplit * t->R * t->C * t->N * 4);
+        if (e != cudaSuccess) return tp_cuda_fail(e);
+    }
+    t->split = k;
+    t->spg = spg;
+    t->nsplit = nsplit;
+    return EA_OK;
 }
 
 bool tp_supported_L(uint32_t L)
@@ -567,6 +667,18 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     // the staging buffer is read by the import kernels: wait before freeing it
     EA_TP_TRY(cudaStreamSynchronize(st));
     cudaFree(staging);
+    staging = nullptr;
+    // enough CTAs for the SMs: up to eight slot groups per unit while R * C is small
+    int dev = 0, sms = 0;
+    EA_TP_TRY(cudaGetDevice(&dev));
+    EA_TP_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    uint32_t k = 1;
+    while ((uint64_t)R * C * k < (uint64_t)sms && k * 2 <= 8 && k * 2 <= NT) k *= 2;
+    const int rc = tp_apply_split(t, k);
+    if (rc != EA_OK) {
+        tp_free(t);
+        return rc;
+    }
     *out = t;
     return EA_OK;
 }
@@ -588,22 +700,73 @@ extern "C" int ea_tp_sweep(ea_tp *t, uint32_t n_sweeps, uint32_t swap_every, int
     a.NT = t->NT;
     a.C = t->C;
     a.rk = t->rk;
-    a.s0 = t->sweep;
-    a.n_sweeps = n_sweeps;
-    a.swap_every = swap_every;
-    a.P0 = t->pass;
-    a.pass_local0 = 0;
-    a.energy_log = energy_log;
+    if (t->nsplit <= 1) {
+        // one CTA per unit: sweeps and swap passes of the whole call in one launch
+        a.s0 = t->sweep;
+        a.n_sweeps = n_sweeps;
+        a.swap_every = swap_every;
+        a.P0 = t->pass;
+        a.pass_local0 = 0;
+        a.energy_log = energy_log;
+        a.swap_log = swap_log;
+        const cudaError_t e = ea::tp_launch((int)t->L, a, 0, t->stream);
+        if (e != cudaSuccess) return tp_cuda_fail(e);
+        ++t->launches;
+        uint64_t passes = 0;
+        if (swap_every != 0)
+            passes = (t->sweep + n_sweeps) / swap_every - t->sweep / swap_every;
+        t->sweep += n_sweeps;
+        t->pass += passes;
+        return EA_OK;
+    }
+    // slot groups: each interval (sweeps up to the next swap pass) is one launch
+    // of nsplit CTAs per unit, then one merge launch that runs the pass
+    a.slices = t->d_slices;
+    a.spg = t->spg;
+    a.nsplit = t->nsplit;
+    a.swap_every = 0;
     a.swap_log = swap_log;
-    const cudaError_t e = ea::tp_launch((int)t->L, a, 0, t->stream);
-    if (e != cudaSuccess) return tp_cuda_fail(e);
-    ++t->launches;
-    uint64_t passes = 0;
-    if (swap_every != 0)
-        passes = (t->sweep + n_sweeps) / swap_every - t->sweep / swap_every;
-    t->sweep += n_sweeps;
-    t->pass += passes;
+    const size_t row_words = (size_t)t->R * t->NT * t->C;
+    const uint64_t end = t->sweep + n_sweeps;
+    uint64_t s = t->sweep;
+    uint32_t row = 0, pass_local = 0;
+    while (s < end) {
+        uint64_t last = end - 1;
+        bool sw = false;
+        if (swap_every != 0) {
+            const uint64_t nxt = (s / swap_every + 1) * swap_every - 1;
+            if (nxt < end) {
+                last = nxt;
+                sw = true;
+            }
+        }
+        const uint32_t n_int = (uint32_t)(last - s + 1);
+        a.s0 = s;
+        a.n_sweeps = n_int;
+        a.energy_log = energy_log ? energy_log + (size_t)row * row_words : nullptr;
+        cudaError_t e = ea::tp_launch((int)t->L, a, 0, t->stream);
+        if (e != cudaSuccess) return tp_cuda_fail(e);
+        const int do_swap = sw && t->NT > 1;
+        int32_t *elog_row = (energy_log && do_swap) ? energy_log + (size_t)(row + n_int - 1) * row_words : nullptr;
+        ea::k_tp_merge<<<t->R * t->C, 256, 0, t->stream>>>(a, (int)t->N, do_swap, t->pass, pass_local, elog_row);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return tp_cuda_fail(e);
+        t->launches += 2;
+        if (sw) {
+            ++t->pass;
+            ++pass_local;
+        }
+        s += n_int;
+        row += n_int;
+    }
+    t->sweep = end;
     return EA_OK;
+}
+
+extern "C" int ea_tp_set_split(ea_tp *t, uint32_t k)
+{
+    if (!t || k == 0 || k > 32 || (k & (k - 1)) != 0 || k > t->NT) return EA_EINVAL;
+    return tp_apply_split(t, k);
 }
 
 extern "C" int ea_tp_read(ea_tp *t, uint32_t *spins, int32_t *energies)
@@ -623,9 +786,11 @@ extern "C" int ea_tp_read(ea_tp *t, uint32_t *spins, int32_t *energies)
     return cudaGetLastError() == cudaSuccess ? EA_OK : EA_ECUDA;
 }
 
-extern "C" int ea_tp_info(const ea_tp *t, uint64_t *sweep_index, uint64_t *pass_index, uint64_t *launches)
+extern "C" int ea_tp_info(const ea_tp *t, uint64_t *sweep_index, uint64_t *pass_index, uint64_t *launches,
+                          uint32_t *split)
 {
     if (!t) return EA_EINVAL;
+    if (split) *split = t->nsplit;
     if (sweep_index) *sweep_index = t->sweep;
     if (pass_index) *pass_index = t->pass;
     if (launches) *launches = t->launches;

@@ -178,5 +178,6 @@ def test_tp_create_validates_arguments_before_touching_the_device():
     lib = ea.load_library()
     assert lib.ea_tp_sweep(None, 1, 1, None, None) == -1
     assert lib.ea_tp_read(None, None, None) == -1
-    assert lib.ea_tp_info(None, None, None, None) == -1
+    assert lib.ea_tp_info(None, None, None, None, None) == -1
+    assert lib.ea_tp_set_split(None, 1) == -1
     lib.ea_tp_destroy(None)

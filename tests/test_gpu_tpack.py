@@ -47,9 +47,11 @@ def _tp_from_oracle_spins(sp, NT):
     return out
 
 
-def _compare_calls(L, R, NT, C, calls, swap_every, seed=77):
+def _compare_calls(L, R, NT, C, calls, swap_every, seed=77, split=None):
     inst, inp, metro, swapt = _inputs(L, R, NT, C, seed)
     gpu = ea.TPEnsemble(L, R, NT, C, seed, inp["bonds"], inp["spins"], metro, swapt)
+    if split is not None:
+        gpu.set_split(split)
     sim = _oracle(inst, inp, metro, swapt)
     sp0, en0 = gpu.read()
     np.testing.assert_array_equal(en0.cpu().numpy(), sim.energies()[..., 0], err_msg="initial energies")
@@ -85,18 +87,35 @@ def _compare_calls(L, R, NT, C, calls, swap_every, seed=77):
     (24, 1, 32, 2, 4, 1),      # 221 KB of shared memory
     (32, 1, 32, 2, 3, 1),      # bonds read from global memory
 ])
-def test_tpack_matches_oracle(L, R, NT, C, n, swap_every):
-    _compare_calls(L, R, NT, C, [n], swap_every)
+@pytest.mark.parametrize("split", [None, 1])
+def test_tpack_matches_oracle(L, R, NT, C, n, swap_every, split):
+    """split None: the slot groups ea_tp_create picks (several per unit for these
+    few realizations); 1: one CTA per unit with the swap passes in the kernel."""
+    _compare_calls(L, R, NT, C, [n], swap_every, split=split)
+
+
+@pytest.mark.parametrize("L,R,NT,C,calls,swap_every,split", [
+    (8, 2, 24, 2, [9, 12], 1, 8),      # groups of 3 slots
+    (6, 2, 5, 1, [13, 20], 3, 4),      # groups of 2 slots: three groups in use
+    (16, 1, 32, 2, [7, 8], 5, 32),     # one slot a group
+    (10, 3, 17, 2, [11], 4, 16),       # groups of 2, the last of 1
+    (32, 1, 32, 1, [3], 2, 2),
+])
+def test_tpack_slot_groups_match_oracle(L, R, NT, C, calls, swap_every, split):
+    gpu = _compare_calls(L, R, NT, C, calls, swap_every, split=split)
+    assert gpu.split == -(-NT // -(-NT // split))
 
 
 def test_tpack_single_temperature_has_no_swaps():
     gpu = _compare_calls(8, 2, 1, 2, [15], 1)
+    assert gpu.split == 1
     assert gpu.pass_index == 15          # passes are counted; with one slot they exchange nothing
 
 
-def test_tpack_calls_split_anywhere():
+@pytest.mark.parametrize("split", [None, 1])
+def test_tpack_calls_split_anywhere(split):
     # pass indices and sweep counters continue across calls, swap every 3 sweeps
-    _compare_calls(8, 3, 12, 2, [5, 1, 7, 4], 3)
+    _compare_calls(8, 3, 12, 2, [5, 1, 7, 4], 3, split=split)
 
 
 def test_tpack_realization_matches_bit0_of_the_packed_form():
@@ -116,3 +135,20 @@ def test_tpack_realization_matches_bit0_of_the_packed_form():
     sp, _ = tp.read()
     np.testing.assert_array_equal(sp.cpu().numpy().view(np.uint32),
                                   _tp_from_oracle_spins(rp.read_spins().cpu().numpy().view(np.uint32), NT))
+
+
+def test_tpack_split_changes_between_calls_and_rejects_bad_values():
+    L, R, NT, C = 8, 2, 12, 2
+    inst, inp, metro, swapt = _inputs(L, R, NT, C, 3)
+    gpu = ea.TPEnsemble(L, R, NT, C, 3, inp["bonds"], inp["spins"], metro, swapt)
+    sim = _oracle(inst, inp, metro, swapt)
+    for k in (4, 1, 8, 2):
+        gpu.set_split(k)
+        gpu.sweep(6, 2)
+        sim.sweep(6, 2, threads=8)
+    sp, en = gpu.read()
+    np.testing.assert_array_equal(sp.cpu().numpy().view(np.uint32), _tp_from_oracle_spins(sim.spins(), NT))
+    np.testing.assert_array_equal(en.cpu().numpy(), sim.energies()[..., 0])
+    for bad in (0, 3, 16, 64):          # not a power of two, or more groups than slots
+        with pytest.raises(ea.EAError):
+            gpu.set_split(bad)
