@@ -431,8 +431,8 @@ int ea_tp_info(const ea_tp *tp, uint64_t *sweep_index, uint64_t *pass_index, uin
  * CTA each: slots do not interact between swap passes, so every group sweeps
  * its own slots up to the next pass and a merge launch then combines the groups
  * and runs the pass.  Results do not depend on k.  ea_tp_create picks the
- * smallest k <= 8 that gives at least one CTA per SM (1 when R * C fills the
- * GPU).  May allocate device memory (k more copies of the spins, one a group);
+ * largest k <= 8 with R * C * k CTAs within one per SM (1 when R * C fills
+ * the GPU).  May allocate device memory (k more copies of the spins, one a group);
  * synchronises the stream when it frees some.  EA_EINVAL for another k. */
 int ea_tp_set_split(ea_tp *tp, uint32_t k);
 /* Synchronises the context's stream and frees its device memory. */
