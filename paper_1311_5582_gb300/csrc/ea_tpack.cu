@@ -26,6 +26,11 @@
 // permutation: new bit t = old bit t + 1 where pair t was accepted, else the
 // bit at the start of the run of accepted pairs that ends at t (an integer
 // addition carries each run's start bit to its end).
+//
+// Few realizations leave most SMs idle with one CTA per unit, so a unit can be
+// split into slot groups (slots do not interact between swap passes): one CTA
+// per group sweeps only its slots' bits up to the next pass and stores them in
+// its slice, and k_tp_merge ORs the slices and runs the pass.
 #include <new>
 
 #include "../../include/ea.h"
