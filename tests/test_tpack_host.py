@@ -47,3 +47,24 @@ def test_random_words_up_to_32_slots():
         # all pairs accepted: the coldest configuration moves to the hottest slot
         M = (1 << (NT - 1)) - 1
         assert closed_form(1, M, NT) == 1 << (NT - 1)
+
+
+def test_tp_inputs_and_their_realization_packed_layout():
+    """The temperature-packed inputs and their rewrite as bit 0 of word-groups
+    (used to hand the same ensemble to the oracle) are a pure change of layout."""
+    import workloads as W
+    inst = W.Instance(L=6, G=3, NT=13, C=2, seed=1, tmin=0.9, tmax=2.0, input_seed=5)
+    inp = W.draw_tp_inputs(inst)
+    assert inp["bonds"].shape == (3, 3, 216) and set(np.unique(inp["bonds"])) <= {0, 1}
+    assert inp["spins"].shape == (3, 2, 216) and int(inp["spins"].max()) < (1 << 13)
+    b, s = W.tp_as_groups(inp["bonds"], inp["spins"], inst.NT)
+    assert b.shape == (3, 3, 216) and s.shape == (3, 13, 2, 216)
+    assert int(b.max()) <= 1 and int(s.max()) <= 1          # only bit 0 of each group is used
+    back = np.zeros_like(inp["spins"])
+    for t in range(inst.NT):
+        back |= s[:, t] << np.uint32(t)
+    np.testing.assert_array_equal(back, inp["spins"])
+    np.testing.assert_array_equal(b, inp["bonds"].astype(np.uint32))
+    # fair coins: about half the slot bits and half the bonds are set
+    frac = np.mean([(inp["spins"] >> np.uint32(t)) & 1 for t in range(inst.NT)])
+    assert 0.45 < frac < 0.55 and 0.45 < inp["bonds"].mean() < 0.55
