@@ -14,8 +14,9 @@ N = 1 samples of the L=16 / L=32 ensembles ("large"), the batched mixed-size
 form and the served trace ("batched", "served").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-For N > 1 launch under torch.distributed.run; each rank runs its own ensemble
-(weak scaling, no data exchange) and rank 0 prints one JSON line.
+For N > 1 launch under torch.distributed.run: the N ranks hold the word-groups
+of one ensemble of N x 2048 realizations, 64 groups each with their global
+group index (weak scaling, no data exchange), and rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -118,11 +119,31 @@ def dist_env():
     return rank, world, local
 
 
-def rank_instance(inst, rank):
-    """Weak scaling: rank r simulates its own ensemble of the same shape
-    (its own disorder draws and Philox key); nothing is exchanged."""
-    return W.Instance(L=inst.L, G=inst.G, NT=inst.NT, C=inst.C, seed=inst.seed + 7919 * rank,
-                      tmin=inst.tmin, tmax=inst.tmax, input_seed=inst.input_seed + 7919 * rank)
+def job_instance(inst, world):
+    """Weak scaling over one ensemble: N ranks simulate one ensemble of N times
+    the workload's word-groups (same Philox key, disorder drawn for all of them);
+    at N = 1 it is the workload itself."""
+    if world <= 1:
+        return inst
+    return W.Instance(L=inst.L, G=inst.G * world, NT=inst.NT, C=inst.C, seed=inst.seed,
+                      tmin=inst.tmin, tmax=inst.tmax, input_seed=inst.input_seed)
+
+
+def rank_groups(G_total, rank, world):
+    """Word-groups [g0, g1) of the job's ensemble that rank `rank` holds.  Groups
+    are independent and their random numbers carry the global group index
+    (group_base = g0), so the shards together follow exactly the trajectory of
+    the whole ensemble on one device; nothing is exchanged."""
+    return G_total * rank // world, G_total * (rank + 1) // world
+
+
+def rank_inputs(inst, rank, world):
+    """(job instance, this rank's (g0, g1), its bonds / spins and the ladder)."""
+    job = job_instance(inst, world)
+    inp = W.draw_inputs(job)
+    g0, g1 = rank_groups(job.G, rank, world)
+    return job, (g0, g1), {"bonds": inp["bonds"][g0:g1], "spins": inp["spins"][g0:g1],
+                           "betas": inp["betas"]}
 
 
 def aggregate(times_s, flips_per_rank):
@@ -626,12 +647,13 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
-    inst = rank_instance(wl["inst"], rank)
-    inp = W.draw_inputs(inst)
+    job, (g0, g1), inp = rank_inputs(wl["inst"], rank, world)
+    inst = W.Instance(L=job.L, G=g1 - g0, NT=job.NT, C=job.C, seed=job.seed, tmin=job.tmin,
+                      tmax=job.tmax, input_seed=job.input_seed)
     metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
     stream = torch.cuda.Stream()
     ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"],
-                      metro, swapt, stream=stream)
+                      metro, swapt, stream=stream, group_base=g0)
     qh = torch.zeros((inst.NT, inst.N + 1), dtype=torch.int64, device="cuda")
     es = torch.zeros(inst.NT, dtype=torch.int64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")  # > L2 (129 MB)
@@ -721,7 +743,8 @@ def main():
         ea.ea_run(inst.L, inst.G, inst.NT, inst.C, inst.seed, h_in["bonds"], h_in["spins"],
                   h_in["metro"], h_in["swapt"], wl["sweeps"], wl["swap_every"],
                   measure_from=wl["measure_from"], measure_every=wl["measure_every"],
-                  want_spins=True, want_qhist=True, want_esum=True, host_out=h_out, stream=stream)
+                  want_spins=True, want_qhist=True, want_esum=True, host_out=h_out, stream=stream,
+                  group_base=g0)
     t_e2e = reduce_max((time.perf_counter() - t0) / e2e_steps, world)
     h2d = sum(v.nbytes for v in h_in.values())
     d2h = sum(v.nbytes for v in h_out.values())
@@ -733,7 +756,10 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": wl["name"], "l2_flush": True, "L": inst.L,
-                       "realizations": 32 * inst.G, "temps": inst.NT, "copies": inst.C,
+                       "realizations": 32 * job.G, "temps": inst.NT, "copies": inst.C,
+                       "parallelism": (f"{world} ranks x {inst.G} word-groups of one ensemble "
+                                       "(group_base = rank x groups), no data exchange"
+                                       if world > 1 else "1 GPU"),
                        "sweeps_per_step": wl["sweeps"], "swap_every": wl["swap_every"],
                        "kernel_launches_per_step": launches / args.steps},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",

@@ -28,6 +28,8 @@
  *     colour = (x + y + z) & 1.
  *   Swap pass P, pair p, realization b: counter ((p << 3) | (b >> 2),
  *     (1 << 24) | (c << 8), P, g), output word b & 3.
+ *   g is the global group index, ea_config::group_base + the group's index
+ *     in the context's arrays.
  * A sweep updates colour 0 then colour 1.  Site i flips iff dE <= 0 or
  * r < metro[t][u], u = number of unsatisfied bonds of i.  After sweep s
  * (global index since creation) a swap pass runs iff swap_every > 0 and
@@ -74,6 +76,12 @@ typedef struct {
     const uint32_t *metro;    /* host [NT][3], copied */
     const uint32_t *swapt;    /* host [NT-1][swap_len], copied; may be NULL if swap_len == 0 */
     uint32_t swap_len;
+    uint32_t group_base;      /* global index of word-group 0: group g of this context draws
+                                 the random numbers of group group_base + g (the counters'
+                                 fourth word), so contexts holding groups [b, b + G) of one
+                                 ensemble reproduce exactly what those groups do in the whole
+                                 ensemble (Sec. 3.3: realizations are independent jobs);
+                                 group_base + G <= 2^32.  0 for a whole ensemble. */
 } ea_config;
 
 /* Options of one ea_sweep call.  All output pointers are DEVICE pointers and
@@ -157,12 +165,23 @@ int ea_create_field(const ea_config *cfg, const ea_field *field, void *stream, e
  * spins: DEVICE int32 [G][NT][C][32].  Any context.  Asynchronous. */
 int ea_magnetisations(ea_ctx *ctx, int32_t *out);
 
-/* Runs args->n_sweeps checkerboard sweeps with the swap passes and
- * measurements the arguments ask for; asynchronous on the context's stream. */
+/* Runs args->n_sweeps sweeps of the method: each a two-stage checkerboard
+ * sweep (Sec. 3.1: colour 0, then colour 1) of single-spin-flip Metropolis
+ * updates (Sec. 2.3; flip iff r < metro[t][u] or dE <= 0, Sec. 4.3.1-4.3.2),
+ * followed by the replica-exchange pass of Sec. 2.4 when (s + 1) % swap_every
+ * == 0, and the measurements the arguments ask for (Sec. 4.1).  Outputs and
+ * their layouts are those of ea_sweep_args (DEVICE pointers).  EA_EINVAL for
+ * a NULL context or arguments, or a qhist with one copy.
+ * Asynchronous on the context's stream; device faults surface at the next
+ * synchronising call. */
 int ea_sweep(ea_ctx *ctx, const ea_sweep_args *args);
 
-/* One replica-exchange pass now (pass index P, then P += 1), on energies
- * recomputed from the spins.  masks: DEVICE [G][C][NT-1] or NULL.  Asynchronous. */
+/* One replica-exchange pass now (Sec. 2.4; pass index P, then P += 1) on
+ * energies recomputed from the spins: for each realization, pairs p = 0..NT-2
+ * in order, accepted iff E_p - E_{p+1} >= 0 or r < swapt[p][k-1] (Sec. 4.3.2),
+ * an accepted pair exchanging the slots' configurations and energies.
+ * masks: DEVICE [G][C][NT-1] (bit b = realization b accepted pair p) or NULL.
+ * EA_EINVAL for a NULL context.  Asynchronous. */
 int ea_pt_swap(ea_ctx *ctx, uint32_t *masks);
 
 /* Measurement pass (Sec. 4.1): recomputes the energies from the spins.
@@ -182,14 +201,21 @@ int ea_measure(ea_ctx *ctx, int32_t *energies, uint32_t *ndiff, uint64_t *qhist)
  * with one copy. */
 int ea_measure_planes(ea_ctx *ctx, int mode, int32_t *out);
 
-/* Spins by slot into DEVICE dst [G][NT][C][N].  Asynchronous. */
+/* Spins by temperature slot (the configuration of Eq. 1 each slot holds
+ * after the exchanges of Sec. 2.4) into DEVICE dst [G][NT][C][N], bit 1 <=>
+ * S = +1, site order of the data conventions above.  The caller owns dst.
+ * EA_EINVAL for a NULL context or dst.  Asynchronous. */
 int ea_read_spins(ea_ctx *ctx, uint32_t *dst);
 
-/* Spins by slot into HOST dst [G][NT][C][N]; synchronises the stream. */
+/* As ea_read_spins into HOST dst [G][NT][C][N]; synchronises the stream
+ * (EA_ECUDA if a device fault is pending). */
 int ea_read_spins_host(ea_ctx *ctx, uint32_t *dst);
 
 /* Replaces the state (checkpoint restore): spins from DEVICE src
- * [G][NT][C][N] by slot, and the global sweep and swap-pass indices. */
+ * [G][NT][C][N] by slot (layout of ea_read_spins; the caller keeps src), and
+ * the global sweep and swap-pass indices that the counters of Sec. 4.3.2's
+ * generator continue from; energies are recomputed from the spins (Eq. 1).
+ * EA_EINVAL for a NULL context or src.  Asynchronous. */
 int ea_write_spins(ea_ctx *ctx, const uint32_t *src, uint64_t sweep_index, uint64_t pass_index);
 
 /* Global sweep index s of the next sweep and pass index P of the next swap pass. */
@@ -356,18 +382,24 @@ int ea_run(const ea_config *cfg, const ea_sweep_args *args, void *stream, int32_
  * no counterpart: this exists for callers that cannot call cudaMalloc while
  * they run (an application that pre-reserves all device memory for its own
  * pool, a host thread that must not stall other streams on an allocation).
- * It performs the pass of ea_pt_swap on caller-owned DEVICE buffers:
+ * It performs the field-free pass of ea_pt_swap (h = 0: the decision is
+ * E_p - E_{p+1} >= -4k against swapt; contexts made with a field decide on
+ * Et instead and must not use it) on caller-owned DEVICE buffers:
  *   spins    [G][NT][C][N] by slot (the layout of ea_read_spins), exchanged in place;
  *   energies [G][NT][C][32] int32 of those spins (as ea_measure returns them),
  *            permuted in place to follow the exchanged configurations;
- *   swapt    [NT-1][swap_len] as at creation; masks [G][C][NT-1] or NULL.
- * seed and pass_index give the random numbers (pass P of the context API).
+ *   swapt    DEVICE [NT-1][swap_len], the table of ea_build_tables;
+ *   masks    DEVICE [G][C][NT-1] or NULL.
+ * seed and pass_index give the random numbers (pass P of the context API);
+ * group g of the buffers draws those of group g (group_base 0).
  * Its scratch (the accepted-pair masks between its two kernels) is a static
- * device array of the library sized for G * C <= 4096; larger ensembles get
- * EA_EINVAL.  The first call on each device looks up that array's device
- * address (make it before any stream capture).  Every call shares the array:
- * calls whose kernels overlap on the GPU (other streams, other host threads)
- * race; calls on one stream are ordered.  Asynchronous on stream. */
+ * device array of the library sized for G * C <= 4096; larger ensembles, and
+ * L with L^3 >= 2^32, get EA_EINVAL.  The first call on each device looks up
+ * that array's device address and keeps it for the process (make that call
+ * before any stream capture; after a cudaDeviceReset the address is stale and
+ * this call must not be used).  Every call shares the array: calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race; calls
+ * on one stream are ordered.  Asynchronous on stream. */
 int ea_pt_swap_static(uint32_t *spins, int32_t *energies, const uint32_t *swapt, uint32_t swap_len,
                       uint32_t L, uint32_t n_groups, uint32_t n_temps, uint32_t n_copies,
                       uint64_t seed, uint64_t pass_index, uint32_t *masks, void *stream);
@@ -403,6 +435,9 @@ typedef struct {
     const uint32_t *metro;    /* host [NT][3] as ea_config; copied */
     const uint32_t *swapt;    /* host [NT-1][swap_len] as ea_config; copied */
     uint32_t swap_len;
+    uint32_t real_base;       /* global index of realization 0: realization r draws the random
+                                 numbers of realization real_base + r (as ea_config::group_base);
+                                 real_base + R <= 2^32.  0 for a whole ensemble. */
 } ea_tp_config;
 
 /* Validates cfg (EA_EINVAL on a bad shape or table, EA_EUNSUPPORTED on L),

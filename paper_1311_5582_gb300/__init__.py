@@ -35,7 +35,8 @@ class _Config(ctypes.Structure):
                 ("n_temps", ctypes.c_uint32), ("n_copies", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("bonds", ctypes.c_void_p),
                 ("spins0", ctypes.c_void_p), ("metro", ctypes.c_void_p),
-                ("swapt", ctypes.c_void_p), ("swap_len", ctypes.c_uint32)]
+                ("swapt", ctypes.c_void_p), ("swap_len", ctypes.c_uint32),
+                ("group_base", ctypes.c_uint32)]
 
 
 class _SweepArgs(ctypes.Structure):
@@ -60,7 +61,8 @@ class _TpConfig(ctypes.Structure):
                 ("n_temps", ctypes.c_uint32), ("n_copies", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64), ("bonds", ctypes.c_void_p),
                 ("spins0", ctypes.c_void_p), ("metro", ctypes.c_void_p),
-                ("swapt", ctypes.c_void_p), ("swap_len", ctypes.c_uint32)]
+                ("swapt", ctypes.c_void_p), ("swap_len", ctypes.c_uint32),
+                ("real_base", ctypes.c_uint32)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -259,7 +261,7 @@ def ea_supported_L(L: int) -> bool:
     return bool(load_library().ea_supported_L(L))
 
 
-def _config(L, G, NT, C, seed, bonds, spins, metro, swapt):
+def _config(L, G, NT, C, seed, bonds, spins, metro, swapt, group_base=0):
     if metro is None:   # field ensembles: the field carries the Metropolis table
         metro = np.zeros((0, 3), np.uint32)
     keep = [np.ascontiguousarray(a, np.uint32) for a in (bonds, spins, metro, swapt)]
@@ -267,7 +269,7 @@ def _config(L, G, NT, C, seed, bonds, spins, metro, swapt):
     N = L ** 3
     assert b.shape == (G, 3, N) and s.shape == (G, NT, C, N) and m.shape in ((NT, 3), (0, 3))
     cfg = _Config(L, G, NT, C, int(seed), b.ctypes.data, s.ctypes.data, m.ctypes.data if m.size else None,
-                  w.ctypes.data if w.size else None, w.shape[1] if w.ndim == 2 else 0)
+                  w.ctypes.data if w.size else None, w.shape[1] if w.ndim == 2 else 0, int(group_base))
     return cfg, keep
 
 
@@ -282,16 +284,22 @@ class Ensemble:
     """One simulated ensemble (an ea_ctx): G word-groups x NT slots x C copies of an L^3 lattice.
 
     field=(h_num, h_den, metro_field) runs it in the external field h = h_num / h_den
-    (ea_create_field); metro is then unused and swapt is the field swap table."""
+    (ea_create_field); metro is then unused and swapt is the field swap table.
+    group_base: global index of group 0 in the random-number counters, so that
+    groups [group_base, group_base + G) of a larger ensemble run exactly as they
+    would inside it."""
 
-    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, stream=None, field=None):
+    def __init__(self, L, G, NT, C, seed, bonds, spins, metro, swapt, stream=None, field=None,
+                 group_base=0):
         import torch
         self.lib = load_library()
         self.L, self.G, self.NT, self.C = int(L), int(G), int(NT), int(C)
         self.N = self.L ** 3
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.handle, self.stream = _stream_handle(stream)
-        cfg, _keep = _config(self.L, self.G, self.NT, self.C, seed, bonds, spins, metro, swapt)
+        cfg, _keep = _config(self.L, self.G, self.NT, self.C, seed, bonds, spins, metro, swapt,
+                             group_base)
+        self.group_base = int(group_base)
         self.swap_len = cfg.swap_len
         h = ctypes.c_void_p(None)
         if field is None:
@@ -544,8 +552,8 @@ class Server:
         self._out = {}          # ticket -> (outputs dict, inputs kept alive)
 
     def submit(self, L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every,
-               want_spins=True, want_energies=True) -> int:
-        cfg, keep = _config(L, G, NT, C, seed, bonds, spins, metro, swapt)
+               want_spins=True, want_energies=True, group_base=0) -> int:
+        cfg, keep = _config(L, G, NT, C, seed, bonds, spins, metro, swapt, group_base)
         N = int(L) ** 3
         out = {"spins": np.zeros((G, NT, C, N), np.uint32) if want_spins else None,
                "energies": np.zeros((G, NT, C, 32), np.int32) if want_energies else None}
@@ -594,11 +602,11 @@ class Server:
 
 def ea_run(L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every, measure_from=0,
            measure_every=0, want_spins=True, want_qhist=False, want_esum=False, host_out=None,
-           stream=None):
+           stream=None, group_base=0):
     """Host-buffer entry point: host arrays in, host arrays out (ea_run)."""
     lib = load_library()
     handle, _ = _stream_handle(stream)
-    cfg, _keep = _config(L, G, NT, C, seed, bonds, spins, metro, swapt)
+    cfg, _keep = _config(L, G, NT, C, seed, bonds, spins, metro, swapt, group_base)
     N = L ** 3
     ho = host_out or {}
     energies = ho.get("energies", np.zeros((G, NT, C, 32), np.int32))
@@ -612,12 +620,40 @@ def ea_run(L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every, 
     return {"energies": energies, "spins": sp, "qhist": qh, "esum": es}
 
 
+def _check_static_args(spins, energies, swapt, L, G, NT, C, masks):
+    """Shapes, dtypes and devices of ea_pt_swap_static's tensors, checked before
+    anything reaches the GPU: the kernels index every buffer by (L, G, NT, C)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None
+    N = int(L) ** 3
+    want = {"spins": (spins, G * NT * C * N), "energies": (energies, G * NT * C * 32)}
+    if masks is not None:
+        want["masks"] = (masks, G * C * max(NT - 1, 0))
+    if swapt is not None:
+        want["swapt"] = (swapt, None)
+    for name, (t, numel) in want.items():
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor on the current CUDA device")
+        if not t.is_cuda or t.device != dev:
+            raise ValueError(f"{name} must live on the current CUDA device, not {t.device}")
+        if not t.is_contiguous() or t.element_size() != 4:
+            raise ValueError(f"{name} must be contiguous with 4-byte elements")
+        if numel is not None and t.numel() != numel:
+            raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    if swapt is not None and (swapt.dim() != 2 or swapt.shape[0] != NT - 1):
+        raise ValueError(f"swapt must be [NT-1][swap_len] = [{NT - 1}][...], got {tuple(swapt.shape)}")
+
+
 def ea_pt_swap_static(spins, energies, swapt, L, n_groups, n_temps, n_copies, seed, pass_index,
                       masks=None, stream=None):
     """Allocation-free replica-exchange pass on caller-owned device tensors (in place).
 
     spins: int32/uint32 device tensor [G][NT][C][N]; energies: int32 [G][NT][C][32];
-    swapt: device tensor [NT-1][swap_len]; masks: optional int32 [G][C][NT-1]."""
+    swapt: device tensor [NT-1][swap_len]; masks: optional int32 [G][C][NT-1].
+    Raises ValueError, before any launch, for a tensor of the wrong size, dtype
+    width or device."""
+    _check_static_args(spins, energies, swapt, int(L), int(n_groups), int(n_temps), int(n_copies),
+                       masks)
     lib = load_library()
     handle, _ = _stream_handle(stream)
     swap_len = int(swapt.shape[1]) if swapt is not None and swapt.dim() == 2 else 0
@@ -634,9 +670,10 @@ class TPEnsemble:
     realization-packed form (its bit 0), so it follows the trajectory of
     realization 32r of an Ensemble with the same inputs.
 
-    bonds: [R][3][N] uint8 (1 <=> J = -1); spins: [R][C][N] uint32 (bit t = slot t)."""
+    bonds: [R][3][N] uint8 (1 <=> J = -1); spins: [R][C][N] uint32 (bit t = slot t).
+    real_base: global index of realization 0 in the random-number counters."""
 
-    def __init__(self, L, R, NT, C, seed, bonds, spins, metro, swapt, stream=None):
+    def __init__(self, L, R, NT, C, seed, bonds, spins, metro, swapt, stream=None, real_base=0):
         import torch
         self.lib = load_library()
         self.L, self.R, self.NT, self.C = int(L), int(R), int(NT), int(C)
@@ -651,7 +688,8 @@ class TPEnsemble:
         assert m.shape == (self.NT, 3)
         self.swap_len = w.shape[1] if w.ndim == 2 else 0
         cfg = _TpConfig(self.L, self.R, self.NT, self.C, int(seed), b.ctypes.data, sp.ctypes.data,
-                        m.ctypes.data, w.ctypes.data if w.size else None, self.swap_len)
+                        m.ctypes.data, w.ctypes.data if w.size else None, self.swap_len,
+                        int(real_base))
         h = ctypes.c_void_p(None)
         _check(self.lib.ea_tp_create(ctypes.byref(cfg), self.handle, ctypes.byref(h)), "ea_tp_create")
         self.ctx = h

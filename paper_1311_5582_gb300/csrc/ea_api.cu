@@ -73,6 +73,7 @@ ea::SweepLaunch base_launch(ea_ctx *c)
     a.h_num = c->h_num;
     a.h_den = c->h_den;
     a.step = c->step;
+    a.g_base = c->g_base;
     return a;
 }
 
@@ -295,6 +296,7 @@ int create_ctx(const ea_config *cfg_in, cudaStream_t stream, cudaMemPool_t pool,
     if (cfg->n_groups == 0 || cfg->n_temps == 0 || cfg->n_temps > (uint32_t)ea::kMaxTemps)
         return EA_EINVAL;
     if (cfg->n_copies < 1 || cfg->n_copies > 2) return EA_EINVAL;
+    if ((uint64_t)cfg->group_base + cfg->n_groups > (1ull << 32)) return EA_EINVAL;
     if (!cfg->bonds || !cfg->spins0 || (!cfg->metro && !field)) return EA_EINVAL;
     if (cfg->n_temps > 1 && cfg->swap_len > 0 && !cfg->swapt) return EA_EINVAL;
     int rc = validate_tables(cfg->metro, cfg->swapt, cfg->n_temps, cfg->swap_len);
@@ -309,6 +311,7 @@ int create_ctx(const ea_config *cfg_in, cudaStream_t stream, cudaMemPool_t pool,
     c->N = L * L * L;
     c->swap_len = cfg->swap_len;
     c->seed = cfg->seed;
+    c->g_base = cfg->group_base;
     c->stream = stream;
     c->pool = pool;
     c->rk = ea::make_round_keys(cfg->seed);

@@ -53,6 +53,7 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
     const uint32_t unit = unit0 + (uint32_t)ui;
     const int c = (int)(unit % a.C);
     const uint32_t g = unit / a.C;
+    const uint32_t gr = g + a.g_base;                   // group index of the random numbers
     const int qper = (Gm::Q + tpl - 1) / tpl;
 
     uint32_t *gS = a.spins + (size_t)unit0 * NT * N;
@@ -115,33 +116,33 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
         if constexpr (FIELD) {
             if (act) {
                 if (needE)
-                    half_sweep_field<L, false, true>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, T,
+                    half_sweep_field<L, false, true>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, gr, tag0, a.rk, T,
                                                      acc, accM);
                 else
-                    half_sweep_field<L, false, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk,
+                    half_sweep_field<L, false, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, gr, tag0, a.rk,
                                                       T, acc, accM);
             }
             __syncthreads();
             if (needE) {
                 if (act)
-                    half_sweep_field<L, true, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, T,
+                    half_sweep_field<L, true, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk, T,
                                                     acc, accM);
                 reduce_counters(acc, tpl, E, lane, warp, 2, MT);
                 reduce_counters(accM, tpl, Mv, lane, warp, 2, MT);
             } else if (act) {
-                half_sweep_field<L, false, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, T,
+                half_sweep_field<L, false, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk, T,
                                                   acc, accM);
             }
         } else {
             if (act)
-                half_sweep<L, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, t0, t1, t2, acc);
+                half_sweep<L, false>(mine, myJ, 0, tl, tpl, qper, (uint32_t)s, gr, tag0, a.rk, t0, t1, t2, acc);
             __syncthreads();
             if (needE) {
                 if (act)
-                    half_sweep<L, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                    half_sweep<L, true>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
                 reduce_counters(acc, tpl, E, lane, warp, 2, MT);
             } else if (act) {
-                half_sweep<L, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                half_sweep<L, false>(mine, myJ, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
             }
         }
         __syncthreads();
@@ -299,6 +300,7 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int c = (int)(unit % a.C);
     const uint32_t g = unit / a.C;
+    const uint32_t gr = g + a.g_base;                   // group index of the random numbers
     const int tbase = chunk * nlat;
     const int NT = (int)a.NT;
     const int l = tid / tpl, tl = tid - l * tpl;
@@ -345,13 +347,13 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
         if (active) {
             if constexpr (FIELD) {
                 if (needM)
-                    half_sweep_field<L, false, true>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, T,
+                    half_sweep_field<L, false, true>(mine, J, 0, tl, tpl, qper, (uint32_t)s, gr, tag0, a.rk, T,
                                                      acc, accM);
                 else
-                    half_sweep_field<L, false, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, T,
+                    half_sweep_field<L, false, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, gr, tag0, a.rk, T,
                                                       acc, accM);
             } else {
-                half_sweep<L, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, g, tag0, a.rk, t0, t1, t2, acc);
+                half_sweep<L, false>(mine, J, 0, tl, tpl, qper, (uint32_t)s, gr, tag0, a.rk, t0, t1, t2, acc);
             }
         }
         __syncthreads();
@@ -359,13 +361,13 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
             if (active) {
                 if constexpr (FIELD) {
                     if (needM)
-                        half_sweep_field<L, true, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk,
+                        half_sweep_field<L, true, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk,
                                                         T, acc, accM);
                     else
-                        half_sweep_field<L, true, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk,
+                        half_sweep_field<L, true, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk,
                                                          T, acc, accM);
                 } else {
-                    half_sweep<L, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                    half_sweep<L, true>(mine, J, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
                 }
             }
             reduce_counters(acc, tpl, E, lane, warp, 2, nlat);
@@ -383,10 +385,10 @@ __device__ __forceinline__ void chunk_body(uint32_t *base, const SweepLaunch &a,
             }
         } else if (active) {
             if constexpr (FIELD)
-                half_sweep_field<L, false, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, T, acc,
+                half_sweep_field<L, false, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk, T, acc,
                                                   accM);
             else
-                half_sweep<L, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                half_sweep<L, false>(mine, J, 1, tl, tpl, qper, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
         }
         __syncthreads();
     }
@@ -412,7 +414,7 @@ __device__ __forceinline__ void swap_unit_body(uint32_t *base, const SweepLaunch
     for (int i = tid; i < (NT - 1) * kLanes; i += nthr) {
         const int p = i >> 5, b = i & 31;
         bnd[i] = accept_bound(a.swapt + (size_t)p * a.swap_len, a.swap_len,
-                              swap_uniform(a.rk, p, b, P, g, c));
+                              swap_uniform(a.rk, p, b, P, g + a.g_base, c));
     }
     __syncthreads();
     if (warp == 0) {

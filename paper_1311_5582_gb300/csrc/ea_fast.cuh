@@ -376,6 +376,7 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int c = (int)(unit % a.C);
     const uint32_t g = unit / a.C;
+    const uint32_t gr = g + a.g_base;                   // group index of the random numbers
     const int half = (NT + 1) / 2;
     int l, par, tl;
     Mp::map(tid, l, par, tl);
@@ -430,7 +431,7 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
         for (int i = first; i < (NT - 1) * 8; i += step) {
             const int p = i >> 3, bq = i & 7;
             const uint4 v = philox(((uint32_t)p << 3) | (uint32_t)bq,
-                                   (1u << 24) | ((uint32_t)c << 8), (uint32_t)Q, g, a.rk);
+                                   (1u << 24) | ((uint32_t)c << 8), (uint32_t)Q, gr, a.rk);
             const uint32_t *row = swt + (size_t)p * len;
             uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;      // invariant: row[0..k) > r
             for (uint32_t st = top; st != 0; st >>= 1) {
@@ -471,23 +472,23 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
         // colour 0: x parity = par; colour 1: x parity = par ^ 1 (warp-uniform)
         if (!active) {
         } else if (par == 0)
-            half_fast<L, HP, QPER, 0, 0, false, PL>(mine, Js, qd, qv, (uint32_t)s, g, tag0, a.rk, t0, t1, t2, acc);
+            half_fast<L, HP, QPER, 0, 0, false, PL>(mine, Js, qd, qv, (uint32_t)s, gr, tag0, a.rk, t0, t1, t2, acc);
         else
-            half_fast<L, HP, QPER, 0, 1, false, PL>(mine, Js, qd, qv, (uint32_t)s, g, tag0, a.rk, t0, t1, t2, acc);
+            half_fast<L, HP, QPER, 0, 1, false, PL>(mine, Js, qd, qv, (uint32_t)s, gr, tag0, a.rk, t0, t1, t2, acc);
         __syncthreads();
         if (needE) {
             if (!active) {
             } else if (par == 0)
-                half_fast<L, HP, QPER, 1, 1, true, PL>(mine, Js, qd, qv, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                half_fast<L, HP, QPER, 1, 1, true, PL>(mine, Js, qd, qv, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
             else
-                half_fast<L, HP, QPER, 1, 0, true, PL>(mine, Js, qd, qv, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                half_fast<L, HP, QPER, 1, 0, true, PL>(mine, Js, qd, qv, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
             reduce_groups<PL, HP>(acc, E, lane, warp, 2, NT);
         } else {
             if (!active) {
             } else if (par == 0)
-                half_fast<L, HP, QPER, 1, 1, false, PL>(mine, Js, qd, qv, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                half_fast<L, HP, QPER, 1, 1, false, PL>(mine, Js, qd, qv, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
             else
-                half_fast<L, HP, QPER, 1, 0, false, PL>(mine, Js, qd, qv, (uint32_t)s, g, tag1, a.rk, t0, t1, t2, acc);
+                half_fast<L, HP, QPER, 1, 0, false, PL>(mine, Js, qd, qv, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
         }
         __syncthreads();
         if (swap_now) {

@@ -60,6 +60,7 @@ struct SweepLaunch {
     const uint64_t *metro_f;        // [NT][2][7] thresholds, 2^32 = always
     int32_t *mag;                   // [G][C][NT][32] magnetisations by slot
     int32_t h_num, h_den, step;     // step of Et = h_den E - h_num M differences
+    uint32_t g_base;                // global index of word-group 0 in the random-number counters
 };
 
 enum PlanForm { kFormUnit = 0, kFormUnitFast = 1, kFormChunked = 2 };
@@ -146,6 +147,7 @@ struct ea_ctx {
     int32_t h_num, h_den, step;
     uint64_t *d_metro_f;           // [NT][2][7]
     int32_t *d_mag;                // [G][C][NT][32] magnetisations by slot
+    uint32_t g_base;               // global index of group 0 (ea_config::group_base)
     uint64_t sweep, pass;
     uint64_t launches;
     std::vector<ea::Plan> plans;   // every kernel plan that can run this ensemble

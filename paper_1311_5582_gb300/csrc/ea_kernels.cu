@@ -40,7 +40,7 @@ k_swap_decide(const __grid_constant__ SweepLaunch a, uint64_t P, uint32_t *masks
     for (int i = tid; i < (NT - 1) * kLanes; i += blockDim.x) {
         const int p = i >> 5, b = i & 31;
         bnd[i] = accept_bound(a.swapt + (size_t)p * a.swap_len, a.swap_len,
-                              swap_uniform(a.rk, p, b, P, g, c));
+                              swap_uniform(a.rk, p, b, P, g + a.g_base, c));
     }
     __syncthreads();
     if (warp == 0 && a.h_num != 0) {

@@ -331,6 +331,7 @@ int check_request(const ea_config *cfg)
     if (!ea::supported_L((int)cfg->L)) return EA_EUNSUPPORTED;
     if (cfg->n_groups == 0 || cfg->n_temps == 0 || cfg->n_temps > (uint32_t)ea::kMaxTemps) return EA_EINVAL;
     if (cfg->n_copies < 1 || cfg->n_copies > 2) return EA_EINVAL;
+    if ((uint64_t)cfg->group_base + cfg->n_groups > (1ull << 32)) return EA_EINVAL;
     if (!cfg->bonds || !cfg->spins0 || !cfg->metro) return EA_EINVAL;
     if (cfg->n_temps > 1 && cfg->swap_len > 0 && !cfg->swapt) return EA_EINVAL;
     return EA_OK;

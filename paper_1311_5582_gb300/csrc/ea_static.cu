@@ -22,7 +22,9 @@ constexpr uint32_t kStaticMaxUnits = 4096;
 static __device__ __align__(256) uint32_t g_static_masks[kStaticMaxUnits * kMaxTemps];
 
 // Device address of g_static_masks per device, looked up once with that
-// device current (the host-side name is only a stand-in for the symbol).
+// device current (the host-side name is only a stand-in for the symbol).  The
+// cache assumes the device's primary context lives as long as the process: a
+// cudaDeviceReset unloads the module, and this call must not be used after one.
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 uint32_t *g_static_ptr[kMaxDevices] = {};
@@ -111,6 +113,7 @@ extern "C" int ea_pt_swap_static(uint32_t *spins, int32_t *energies, const uint3
     if (L < 2 || (L & 1u) || n_groups == 0 || n_temps == 0 || n_temps > (uint32_t)kMaxTemps ||
         n_copies < 1 || n_copies > 2)
         return EA_EINVAL;
+    if ((uint64_t)L * L * L > 0xFFFFFFFFull) return EA_EINVAL;              // N in 32 bits
     if ((uint64_t)n_groups * n_copies > kStaticMaxUnits) return EA_EINVAL;   // scratch limit
     if (n_temps > 1 && swap_len > 0 && !swapt) return EA_EINVAL;
     if (n_temps < 2) return EA_OK;    // no pairs: nothing to exchange

@@ -62,6 +62,7 @@ struct TpLaunch {
     uint32_t *slices;           // [nsplit][R][C][2][H]
     uint32_t spg;               // slots per group
     uint32_t nsplit;            // groups (gridDim.y)
+    uint32_t r_base;            // global index of realization 0 in the random-number counters
 };
 
 // The words a site update reads: own spin word, its six neighbours and the six
@@ -258,6 +259,7 @@ k_tp_sweep(TpLaunch a, int recompute_only)
     uint32_t *S = tp_smem;
     const uint32_t unit = blockIdx.x;
     const uint32_t c = unit % a.C, r = unit / a.C;
+    const uint32_t rr = r + a.r_base;                   // realization index of the random numbers
     const int NT = (int)a.NT;
     const int tid = threadIdx.x, nthr_cta = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int i = tid & 3, qg = tid >> 2, nqg = nthr_cta >> 2;
@@ -287,7 +289,7 @@ k_tp_sweep(TpLaunch a, int recompute_only)
     if (recompute_only) {
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-        tp_half<L, 2>(S, J, nthr, 1, qg, nqg, qper, i, 0, NT, valid, 0u, r, 0u, a.rk, acc);
+        tp_half<L, 2>(S, J, nthr, 1, qg, nqg, qper, i, 0, NT, valid, 0u, rr, 0u, a.rk, acc);
         tp_reduce_energy(acc, E, lane, 0, NT);
         __syncthreads();
         if (tid < kTpMaxTemps) a.energy[(size_t)unit * kLanes + tid] = tid < NT ? E[tid] : 0;
@@ -302,15 +304,15 @@ k_tp_sweep(TpLaunch a, int recompute_only)
         const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
         const bool needE = swap_now || a.energy_log != nullptr || (n + 1 == a.n_sweeps);
         if (needE && tid < kTpMaxTemps) E[tid] = -3 * N;
-        tp_half<L, 0>(S, J, nthr, 0, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, r, tag0, a.rk, acc);
+        tp_half<L, 0>(S, J, nthr, 0, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, rr, tag0, a.rk, acc);
         __syncthreads();
         if (needE) {
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-            tp_half<L, 1>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, r, tag1, a.rk, acc);
+            tp_half<L, 1>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, rr, tag1, a.rk, acc);
             tp_reduce_energy(acc, E, lane, t_lo, t_hi);
         } else {
-            tp_half<L, 0>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, r, tag1, a.rk, acc);
+            tp_half<L, 0>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, rr, tag1, a.rk, acc);
         }
         __syncthreads();
         if (swap_now) {
@@ -319,7 +321,7 @@ k_tp_sweep(TpLaunch a, int recompute_only)
                 const int e = lane < NT ? E[lane] : 0;
                 int bnd = 0;
                 if (lane + 1 < NT) {
-                    const uint4 v = philox((uint32_t)lane << 3, (1u << 24) | (c << 8), (uint32_t)P, r, a.rk);
+                    const uint4 v = philox((uint32_t)lane << 3, (1u << 24) | (c << 8), (uint32_t)P, rr, a.rk);
                     bnd = accept_bound(a.swapt + (size_t)lane * a.swap_len, a.swap_len, v.x);
                 }
                 // sequential pairs 0..NT-2 on the energies carried upward
@@ -386,6 +388,7 @@ k_tp_merge(TpLaunch a, int N, int do_swap, uint64_t P, uint32_t pass_local, int3
     __shared__ uint32_t smask;
     const uint32_t unit = blockIdx.x;
     const uint32_t c = unit % a.C, r = unit / a.C;
+    const uint32_t rr = r + a.r_base;                   // realization index of the random numbers
     const int NT = (int)a.NT, tid = threadIdx.x, lane = tid & 31;
     const uint32_t valid = NT >= 32 ? kFull : ((1u << NT) - 1u);
     if (tid < 32) {
@@ -396,7 +399,7 @@ k_tp_merge(TpLaunch a, int N, int do_swap, uint64_t P, uint32_t pass_local, int3
         if (do_swap) {
             int bnd = 0;
             if (lane + 1 < NT) {
-                const uint4 v = philox((uint32_t)lane << 3, (1u << 24) | (c << 8), (uint32_t)P, r, a.rk);
+                const uint4 v = philox((uint32_t)lane << 3, (1u << 24) | (c << 8), (uint32_t)P, rr, a.rk);
                 bnd = accept_bound(a.swapt + (size_t)lane * a.swap_len, a.swap_len, v.x);
             }
             int cur = __shfl_sync(kFull, e, 0);
@@ -540,6 +543,7 @@ struct ea_tp {
     int32_t *d_energy;
     uint64_t sweep, pass, launches;
     ea::RoundKeys rk;
+    uint32_t r_base;               // ea_tp_config::real_base
     uint32_t split, spg, nsplit;   // requested groups, slots per group, groups in use
     uint32_t *d_slices;            // [nsplit][R][C][N] when nsplit > 1
 };
@@ -610,6 +614,7 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     if (L < 4 || (L & 1u) || R == 0 || NT == 0 || NT > (uint32_t)ea::kTpMaxTemps || C < 1 || C > 2)
         return EA_EINVAL;
     if (!tp_supported_L(L)) return EA_EUNSUPPORTED;
+    if ((uint64_t)cfg->real_base + R > (1ull << 32)) return EA_EINVAL;
     for (uint32_t t = 0; t < NT; ++t)
         if (cfg->metro[t * 3] > cfg->metro[t * 3 + 1] || cfg->metro[t * 3 + 1] > cfg->metro[t * 3 + 2])
             return EA_EINVAL;
@@ -632,6 +637,7 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     t->swap_len = len;
     t->stream = (cudaStream_t)stream;
     t->rk = ea::make_round_keys(cfg->seed);
+    t->r_base = cfg->real_base;
     const size_t n_spin = (size_t)R * C * N, n_bond = (size_t)R * 3 * N;
     EA_TP_TRY(cudaMalloc(&t->d_spins, n_spin * 4));
     EA_TP_TRY(cudaMalloc(&t->d_bonds, n_bond * 4));
@@ -667,6 +673,7 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     a.NT = NT;
     a.C = C;
     a.rk = t->rk;
+    a.r_base = t->r_base;
     EA_TP_TRY(ea::tp_launch((int)L, a, 1, st));
     t->launches = 3;
     // the staging buffer is read by the import kernels: wait before freeing it
@@ -707,6 +714,7 @@ extern "C" int ea_tp_sweep(ea_tp *t, uint32_t n_sweeps, uint32_t swap_every, int
     a.NT = t->NT;
     a.C = t->C;
     a.rk = t->rk;
+    a.r_base = t->r_base;
     if (t->nsplit <= 1) {
         // one CTA per unit: sweeps and swap passes of the whole call in one launch
         a.s0 = t->sweep;

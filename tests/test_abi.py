@@ -90,6 +90,7 @@ def test_create_validates_arguments_before_touching_the_device():
     c = ea._Config.from_buffer_copy(cfg); c.n_copies = 3; bad.append((c, -1))
     c = ea._Config.from_buffer_copy(cfg); c.n_temps = 65; bad.append((c, -1))
     c = ea._Config.from_buffer_copy(cfg); c.bonds = None; bad.append((c, -1))
+    c = ea._Config.from_buffer_copy(cfg); c.group_base = 2**32 - 1; c.n_groups = 2; bad.append((c, -1))
     for c, want in bad:
         assert _create_rc(c) == want
     # non-monotone Metropolis row
@@ -145,7 +146,7 @@ def test_field_builder_and_create_reject_bad_fields():
     assert rc(0, 1, mf) == -1
 
 
-def _tp_create(L=4, R=2, NT=4, C=2, metro=None, swapt=None, bonds=True, spins=True):
+def _tp_create(L=4, R=2, NT=4, C=2, metro=None, swapt=None, bonds=True, spins=True, real_base=0):
     lib = ea.load_library()
     N = L ** 3
     b = np.zeros((R, 3, N), np.uint8)
@@ -155,7 +156,8 @@ def _tp_create(L=4, R=2, NT=4, C=2, metro=None, swapt=None, bonds=True, spins=Tr
     m = m if metro is None else metro
     w = w if swapt is None else swapt
     cfg = ea._TpConfig(L, R, NT, C, 1, b.ctypes.data if bonds else None, s.ctypes.data if spins else None,
-                       m.ctypes.data, w.ctypes.data if w.size else None, w.shape[1] if w.ndim == 2 else 0)
+                       m.ctypes.data, w.ctypes.data if w.size else None, w.shape[1] if w.ndim == 2 else 0,
+                       real_base)
     h = ctypes.c_void_p(None)
     return lib.ea_tp_create(ctypes.byref(cfg), None, ctypes.byref(h)), h
 
@@ -170,6 +172,7 @@ def test_tp_create_validates_arguments_before_touching_the_device():
     assert _tp_create(L=18)[0] == -5                     # even but not compiled
     assert _tp_create(bonds=False)[0] == -1
     assert _tp_create(spins=False)[0] == -1
+    assert _tp_create(real_base=2**32 - 1)[0] == -1      # realizations past the 32-bit counter word
     bad = np.array([[5, 3, 9]] * 4, np.uint32)           # thresholds must not decrease in u
     assert _tp_create(metro=bad)[0] == -1
     w = ea.ea_build_tables(W.geometric_ladder(4, 1.0, 2.0), 64)[1].copy()
@@ -181,3 +184,31 @@ def test_tp_create_validates_arguments_before_touching_the_device():
     assert lib.ea_tp_info(None, None, None, None, None) == -1
     assert lib.ea_tp_set_split(None, 1) == -1
     lib.ea_tp_destroy(None)
+
+
+def test_static_pass_wrapper_rejects_bad_tensors_before_any_launch():
+    """ea_pt_swap_static indexes its buffers by (L, G, NT, C): the binding refuses
+    host tensors, wrong sizes, wrong element widths and a malformed table."""
+    torch = pytest.importorskip("torch")
+    L, G, NT, C = 4, 2, 3, 2
+    N = L ** 3
+    host = dict(spins=torch.zeros(G * NT * C * N, dtype=torch.int32),
+                energies=torch.zeros(G * NT * C * 32, dtype=torch.int32),
+                swapt=torch.zeros((NT - 1, 5), dtype=torch.int32))
+    with pytest.raises(ValueError):
+        ea.ea_pt_swap_static(host["spins"], host["energies"], host["swapt"], L, G, NT, C, 1, 0)
+    if not torch.cuda.is_available():
+        return
+    dev = {k: v.cuda() for k, v in host.items()}
+    bad = [
+        dict(dev, spins=dev["spins"][:-1]),                              # one word short
+        dict(dev, energies=dev["energies"].to(torch.int64)),             # 8-byte elements
+        dict(dev, swapt=torch.zeros((NT, 5), dtype=torch.int32, device="cuda")),   # NT rows
+        dict(dev, energies=host["energies"]),                            # host tensor
+    ]
+    for b in bad:
+        with pytest.raises(ValueError):
+            ea.ea_pt_swap_static(b["spins"], b["energies"], b["swapt"], L, G, NT, C, 1, 0)
+    with pytest.raises(ValueError):
+        ea.ea_pt_swap_static(dev["spins"], dev["energies"], dev["swapt"], L, G, NT, C, 1, 0,
+                             masks=torch.zeros(3, dtype=torch.int32, device="cuda"))

@@ -53,3 +53,7 @@ def test_static_pass_rejects_ensembles_beyond_its_scratch():
     rc = lib.ea_pt_swap_static(dummy.data_ptr(), dummy.data_ptr(), None, 0, 4, 4097, 2, 1, 1, 0,
                                None, None)
     assert rc == -1
+    # a lattice whose site count does not fit 32 bits is refused the same way
+    rc = lib.ea_pt_swap_static(dummy.data_ptr(), dummy.data_ptr(), None, 0, 1626, 1, 2, 1, 1, 0,
+                               None, None)
+    assert rc == -1
