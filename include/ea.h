@@ -221,7 +221,10 @@ int ea_write_spins(ea_ctx *ctx, const uint32_t *src, uint64_t sweep_index, uint6
 /* Global sweep index s of the next sweep and pass index P of the next swap pass. */
 int ea_get_counters(const ea_ctx *ctx, uint64_t *sweep_index, uint64_t *pass_index);
 
-/* Waits for the context's stream; returns EA_ECUDA on a device fault. */
+/* Waits for the context's stream; returns EA_ECUDA on a device fault and
+ * EA_ETIMEOUT (clearing it) if a kernel's bounded wait between its warps ran
+ * out since the last check (it never should; the state is then not advanced
+ * consistently and must be rewritten with ea_write_spins). */
 int ea_sync(ea_ctx *ctx);
 
 /* Number of kernel launches this context has enqueued so far. */

@@ -86,7 +86,7 @@ class _Field(ctypes.Structure):
     _fields_ = [("h_num", ctypes.c_int32), ("h_den", ctypes.c_int32), ("metro", ctypes.c_void_p)]
 
 
-PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked"}
+PLAN_FORMS = {0: "unit", 1: "unit-fast", 2: "chunked", 3: "unit-wave"}
 
 EXPORTS = ["ea_build_tables", "ea_build_tables_field", "ea_supported_L", "ea_create",
            "ea_create_field", "ea_magnetisations", "ea_destroy", "ea_sweep",

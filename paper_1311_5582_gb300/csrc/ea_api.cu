@@ -427,6 +427,17 @@ int run_sweeps(ea_ctx *c, const ea_sweep_args *args, const ea::Plan &plan)
         a.P0 = c->pass;
         a.pass_local0 = 0;
         const bool overlaps = c->C == 2 && args->qhist != nullptr && args->measure_every != 0;
+        if (plan.form == ea::kFormUnitWave) {
+            const bool meas = args->measure_every != 0 && (args->qhist != nullptr || args->esum != nullptr);
+            if (!meas) {
+                EA_TRY(ea::launch_sweep_unit_wave(a, plan.swap_in_smem, st, &c->launches));
+                return EA_OK;
+            }
+            // measured calls run under the first specialised plan (same results)
+            for (const ea::Plan &q : c->plans)
+                if (q.form == ea::kFormUnitFast) return run_sweeps(c, args, q);
+            return EA_EUNSUPPORTED;
+        }
         if (plan.form == ea::kFormUnitFast)
             EA_TRY(ea::launch_sweep_unit_fast(a, (int)c->L, plan.threads_per_lattice,
                                               plan.swap_in_smem, overlaps, c->smem_optin, st,
@@ -664,6 +675,13 @@ int ea_sync(ea_ctx *c)
     if (!c) return EA_EINVAL;
     EA_TRY(cudaStreamSynchronize(c->stream));
     EA_TRY(cudaGetLastError());
+    // a bounded device-side wait that ran out raises the context's error flag
+    int err = 0;
+    EA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) {
+        EA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+        return EA_ETIMEOUT;
+    }
     return EA_OK;
 }
 
@@ -709,7 +727,7 @@ int ea_run(const ea_config *cfg, const ea_sweep_args *args, void *stream, int32_
             e = cudaMemcpyAsync(qhist_host, d_q, nq * 8, cudaMemcpyDeviceToHost, c->stream);
         if (rc == EA_OK && e == cudaSuccess && esum_host)
             e = cudaMemcpyAsync(esum_host, d_es, (size_t)c->NT * 8, cudaMemcpyDeviceToHost, c->stream);
-        if (rc == EA_OK && e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (rc == EA_OK && e == cudaSuccess) rc = ea_sync(c);
         if (rc == EA_OK && e == cudaSuccess && spins_host) rc = ea_read_spins_host(c, spins_host);
     }
     cudaStreamSynchronize(c->stream);

@@ -106,7 +106,7 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
                 const int row = i >> 5, b = i & 31;
                 const int ub = row / (NT - 1), p = row - ub * (NT - 1);
                 const uint32_t un = unit0 + (uint32_t)ub;
-                const uint32_t r = swap_uniform(a.rk, p, b, P, un / a.C, (int)(un % a.C));
+                const uint32_t r = swap_uniform(a.rk, p, b, P, un / a.C + a.g_base, (int)(un % a.C));
                 const int b4 = accept_bound(swt + (size_t)p * a.swap_len, a.swap_len, r);
                 bnd[i] = FIELD ? (b4 / 4) * a.step : b4;      // -K x the step of Et
             }

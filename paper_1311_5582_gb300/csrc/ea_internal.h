@@ -63,7 +63,7 @@ struct SweepLaunch {
     uint32_t g_base;                // global index of word-group 0 in the random-number counters
 };
 
-enum PlanForm { kFormUnit = 0, kFormUnitFast = 1, kFormChunked = 2 };
+enum PlanForm { kFormUnit = 0, kFormUnitFast = 1, kFormChunked = 2, kFormUnitWave = 3 };
 
 struct Plan {
     int form;               // PlanForm
@@ -85,6 +85,13 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
                              bool field = false);
 
 int fast_unit_threads(int L, int HP, int NT);
+// Unit kernel with the wavefront replica exchange (L = 8, NT <= kWaveMaxTemps,
+// one warp per two slots; launches without qhist / esum measurement).
+constexpr int kWaveMaxTemps = 32;
+int wave_unit_threads(int L, int NT);
+size_t wave_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem);
+cudaError_t launch_sweep_unit_wave(const SweepLaunch &a, bool swap_in_smem, cudaStream_t st,
+                                   uint64_t *launches);
 // Dynamic shared memory of the specialised unit kernel (with or without the
 // swap table, the measurement snapshots and the shared-memory histogram).
 size_t fast_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem, bool snap, bool hist_smem);

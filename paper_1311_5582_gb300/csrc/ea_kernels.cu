@@ -528,7 +528,24 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
     std::vector<Plan> out;
     if (NT < 1 || NT > kMaxTemps || !supported_L(L)) return out;
     const int N = L * L * L;
-    // fast unit form (L % 8 == 0): best first; field-free only
+    // wavefront unit form (L = 8): best first; field-free only
+    if (!field && wave_unit_threads(L, NT) != 0) {
+        const bool sw_smem = wave_unit_smem(L, NT, swap_len, true) <= smem_optin;
+        const size_t smem = wave_unit_smem(L, NT, swap_len, sw_smem);
+        if (smem <= smem_optin) {
+            Plan p;
+            p.form = kFormUnitWave;
+            p.unit = true;
+            p.threads_per_lattice = 16;
+            p.lattices_per_cta = NT;
+            p.threads = wave_unit_threads(L, NT);
+            p.smem = smem;
+            p.j_in_smem = true;
+            p.swap_in_smem = sw_smem;
+            out.push_back(p);
+        }
+    }
+    // fast unit form (L % 8 == 0); field-free only
     if (!field) {
         const bool sw_smem = fast_unit_smem(L, NT, swap_len, true, false, false) <= smem_optin;
         const size_t smem = fast_unit_smem(L, NT, swap_len, sw_smem, false, false);
