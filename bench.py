@@ -279,12 +279,13 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
     persistent batched launch, against the same instances launched one after
     another; both sides autotuned, both timed from warm state with L2 flushed."""
     insts = W.batch_instances()
-    ens = []
+    ens, twins = [], []          # plain launches / the batch, from the same inputs
     for inst in insts:
         inp = W.draw_inputs(inst)
         metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
-        ens.append(ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"],
-                               inp["spins"], metro, swapt))
+        for dst in (ens, twins):
+            dst.append(ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"],
+                                   inp["spins"], metro, swapt))
     flips = sum(_flips(i, sweeps) for i in insts)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
@@ -310,7 +311,7 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
     l1 = sum(e.launches for e in ens)
     t_plain = timed(plain)
     plain_launches = sum(e.launches for e in ens) - l1
-    batch = ea.Batch(ens)
+    batch = ea.Batch(twins)
     if autotune:
         batch.autotune(probe_sweeps=200, swap_every=swap_every)
 
@@ -323,6 +324,12 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
     t_batch = timed(batched)
     del l0
     plans = [batch.plans(i)[batch.plan(i)] for i in range(len(insts))]
+    # both sides ran the same sweeps from the same state: identical results
+    same = all(np.array_equal(a.read_spins_host(), b.read_spins_host())
+               and np.array_equal(a.measure()[0].cpu().numpy(), b.measure()[0].cpu().numpy())
+               and a.counters == b.counters for a, b in zip(ens, twins))
+    if not same:
+        raise AssertionError("batched results differ from the per-instance launches")
     return {
         "workload": "EA +-J batched mix: " + ", ".join(
             f"L={i.L} {32 * i.G} realizations x {i.NT} temps" for i in insts)
@@ -330,7 +337,7 @@ def bench_batched(ea, torch, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVER
         "value": t_batch / flips * 1e12, "unit": UNIT, "plain_value": t_plain / flips * 1e12,
         "roofline_frac": flips / 32 * ALG_OPS_PER_SITE_WORD / t_batch / 1e12 / _alu_peak_tops(torch),
         "speedup_vs_plain": t_plain / t_batch, "gpu_launches": batch.launches - b0,
-        "plain_gpu_launches": plain_launches, "flips": flips,
+        "plain_gpu_launches": plain_launches, "flips": flips, "identical_to_plain": bool(same),
         "plans": [f"{p['form']} t{p['threads']} g{p['group_threads']} u{p['units_per_cta']}"
                   for p in plans],
     }

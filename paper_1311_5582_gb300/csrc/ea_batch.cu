@@ -95,6 +95,11 @@ std::vector<BPlan> batch_candidates(const ea_ctx *c, size_t optin)
             if (q.form == p.form && q.p1 == p.p1 && q.p2 == p.p2) return;
         out.push_back(p);
     };
+    // wavefront unit body (L = 8)
+    if (wave_unit_threads(L, NT) != 0) {
+        const bool sw = wave_unit_smem(L, NT, c->swap_len, true) <= optin;
+        add({kBWave, 16, 0, wave_unit_threads(L, NT), sw, true, wave_unit_smem(L, NT, c->swap_len, sw)});
+    }
     // specialised unit kernel (variants compiled into the batch kernel)
     const int fast[][2] = {{8, 8}, {8, 4}, {16, 32}, {16, 64}};
     for (const auto &v : fast) {
@@ -143,6 +148,9 @@ std::vector<BPlan> batch_candidates(const ea_ctx *c, size_t optin)
 // busy threads, then unit bodies before chunks.
 int default_candidate(const std::vector<BPlan> &cands, int maxt)
 {
+    // the wavefront body wherever it fits the width (its exchange overlaps the sweeps)
+    for (int i = 0; i < (int)cands.size(); ++i)
+        if (cands[(size_t)i].form == kBWave && cands[(size_t)i].threads <= maxt) return i;
     int most = 0;
     for (const BPlan &p : cands)
         if (p.threads <= maxt && p.threads > most) most = p.threads;
@@ -345,7 +353,7 @@ int ea_batch_plan_info(const ea_batch *b, uint32_t member, int index, ea_plan_de
         return EA_EINVAL;
     const ea::BPlan &p = b->cands[member][(size_t)index];
     const int NT = (int)b->ctxs[member]->NT;
-    out->form = p.form == ea::kBFast ? 1 : p.form == ea::kBUnit ? 0 : 2;
+    out->form = p.form == ea::kBWave ? 3 : p.form == ea::kBFast ? 1 : p.form == ea::kBUnit ? 0 : 2;
     out->threads = p.threads;
     out->group_threads = p.p1;
     out->lattices_per_cta = p.form == ea::kBChunk ? p.p2 : p.form == ea::kBUnit ? p.p2 * NT : NT;
@@ -449,6 +457,7 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
         I.a.C = c->C;
         I.a.rk = c->rk;
         I.a.err = c->d_err;
+        I.a.g_base = c->g_base;
         I.a.s0 = c->sweep;
         I.a.n_sweeps = n_sweeps;
         I.a.swap_every = swap_every;

@@ -7,17 +7,18 @@
 
 #include "ea_bodies.cuh"
 #include "ea_fast.cuh"
+#include "ea_wave.cuh"
 
 namespace ea {
 
 constexpr int kBatchMaxThreads = 512;
 constexpr uint32_t kSpinLimit = 1u << 26;   // default wait: ~ tens of seconds of 256 ns naps
 
-enum BatchForm { kBUnit = 0, kBFast = 1, kBChunk = 2 };
+enum BatchForm { kBUnit = 0, kBFast = 1, kBChunk = 2, kBWave = 3 };
 
 struct BatchInst {
     SweepLaunch a;          // s0, n_sweeps, P0, swap_every of this call
-    int32_t L, form, p1, p2;    // p1: threads per lattice (unit, chunk) or HP (fast);
+    int32_t L, form, p1, p2;    // p1: threads per lattice (unit, chunk), HP (fast), 16 (wave);
                                 // p2: units per task (unit) or lattices per chunk (chunked)
     int32_t swap_smem, j_smem;
     uint32_t units;         // G * C; a unit task starts at unit `task.unit`
@@ -206,8 +207,13 @@ k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tas
             run_unit(I.L, base, s_a, t.unit, I.p1, I.swap_smem,
                      (int)min((uint32_t)I.p2, I.units - t.unit));
         else if (I.form == kBFast) run_fast(I.L, I.p1, base, s_a, t.unit, I.swap_smem);
+        else if (I.form == kBWave) unit_wave_body<false>(base, s_a, t.unit, I.swap_smem);
         else run_chunk(I.L, I.j_smem, base, s_a, t.unit, (int)t.chunk, I.p1, I.p2);
         __syncthreads();
+        if (I.form == kBWave) {
+            wave_release(base, (int)I.a.NT);
+            __syncthreads();
+        }
         if (I.form != kBChunk) {
             if (threadIdx.x == 0 && t.piece + 1 < I.pieces) {
                 __threadfence();

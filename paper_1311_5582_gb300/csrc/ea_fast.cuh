@@ -97,15 +97,23 @@ __device__ __forceinline__ uint32_t below_mask(uint32_t r, uint64_t neg_t)
 }
 
 // Flip mask (same decision as flip_mask): lanes with u >= 3, or u >= 2 and
-// r < t2, or u >= 1 and r < t1, or r < t0 (the thresholds are monotone).
+// r < t2, or u >= 1 and r < t1, or r < t0.  The masks m_i = [r < t_i] are
+// all-ones or all-zeros words and, the thresholds being monotone, m0 implies
+// m1 implies m2, so
+//   [u>=3] | [u>=2] m2 | [u>=1] m1 | m0 = u2 | u1 (u0 | m2) | u0 m1 | m0,
+// three LOP3s before the last OR (which the caller may fold into its XOR).
+__device__ __forceinline__ uint32_t flip_mask_part(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t m1,
+                                                   uint32_t m2)
+{
+    const uint32_t a = u0 | m2;
+    const uint32_t t = u2 | (u1 & a);
+    return t | (u0 & m1);
+}
 __device__ __forceinline__ uint32_t flip_mask_fma(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t r,
                                                   uint64_t n0, uint64_t n1, uint64_t n2)
 {
     const uint32_t m0 = below_mask(r, n0), m1 = below_mask(r, n1), m2 = below_mask(r, n2);
-    const uint32_t ge3 = u2 | (u1 & u0);
-    const uint32_t ge2 = u2 | u1;
-    const uint32_t ge1 = ge2 | u0;
-    return ge3 | (ge2 & m2) | (ge1 & m1) | m0;
+    return flip_mask_part(u0, u1, u2, m1, m2) | m0;
 }
 
 template <int PL>
@@ -187,9 +195,11 @@ __device__ __forceinline__ void quad_fast(uint32_t *S, const uint32_t *J, const 
         full_add(e3, e4, e5, b0, b1);
         u0 = a0 ^ b0;
         full_add(a1, b1, a0 & b0, u1, u2);
-        const uint32_t f = flip_mask_fma(u0, u1, u2, rr[j], t0, t1, t2);
-        ns[j] = sj ^ f;
+        const uint32_t m0 = below_mask(rr[j], t0), m1 = below_mask(rr[j], t1), m2 = below_mask(rr[j], t2);
+        const uint32_t fp = flip_mask_part(u0, u1, u2, m1, m2);
+        ns[j] = sj ^ (fp | m0);                          // one LOP3
         if constexpr (WITH_E) {
+            const uint32_t f = fp | m0;
             x0[j] = u0;
             x1[j] = u1 ^ (f & ~u0);
             x2[j] = u2 ^ (f & ~(u0 & u1));

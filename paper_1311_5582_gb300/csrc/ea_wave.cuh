@@ -20,7 +20,7 @@
 // The warps run staggered by about two pair steps each; the exchange, the
 // decisions and the bound search of the next pass overlap the sweeps of the
 // other warps instead of stopping the CTA.  Hand-offs are shared-memory
-// flags written with release and read with acquire semantics; every wait is
+// mbarriers (the waiting warp is suspended, not spinning); every wait is
 // bounded (on expiry the unit raises the context's error flag and stops).
 // Each decision uses exactly the energies, bounds and order of the
 // sequential pass, so the trajectory is that of every other kernel.
@@ -31,11 +31,11 @@
 namespace ea {
 namespace {
 
-constexpr int kWaveSpinLimit = 1 << 26;    // polls of one wait (seconds) before giving up
+constexpr int kWaveWaitLimit = 1 << 22;    // suspending polls of one wait (seconds) before giving up
 
 // Shared-memory layout of the wavefront kernel, in 32-bit words.
 struct WaveLayout {
-    size_t s, js, eo, cur, flag_e, flag_h, abort, tsw, words;
+    size_t s, js, eo, cur, bar_e, bar_h, abort, tsw, words;
     __host__ __device__ WaveLayout(int N, int NT, uint32_t swap_len, bool swap_smem)
     {
         const int nw = (NT + 1) / 2;
@@ -44,37 +44,70 @@ struct WaveLayout {
         js = o; o += (size_t)3 * N;               // [3][2][H] bonds
         eo = o; o += (size_t)NT * kLanes;         // energy of slot 2k after the sweep, for warp k-1
         cur = o; o += (size_t)nw * kLanes;        // carried energy from warp k to warp k+1
-        flag_e = o; o += (size_t)nw;              // warp k: sweeps whose E_{2k} is published
-        flag_h = o; o += (size_t)nw;              // warp k: passes applied up to slot 2k+2
+        o = (o + 1) & ~(size_t)1;                 // 8-byte alignment of the barriers
+        bar_e = o; o += 2 * (size_t)nw;           // mbarrier k: E_{2k+2} of warp k+1 is published
+        bar_h = o; o += 2 * (size_t)nw;           // mbarrier k: warp k applied its pass steps
         abort = o; o += 1;
         tsw = o; o += swap_smem && NT > 1 ? (size_t)(NT - 1) * swap_len : 0;
         words = o;
     }
 };
 
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Hand-offs between warps: a shared-memory mbarrier that completes one phase
+// when the 32 lanes of the producer warp have arrived (arrive has release
+// semantics for each lane's earlier writes, the consumer's wait acquire).
+// A waiting warp is suspended by the hardware instead of spinning, so it
+// takes no issue slots from the warps that are sweeping.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "r"(v)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
                  : "memory");
 }
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
-    uint32_t v;
-    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"((uint32_t)__cvta_generic_to_shared(p))
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
                  : "memory");
-    return v;
+    return ok != 0;
 }
 
-// Waits (whole warp) until *flag >= target (flags count sweeps of this call,
-// starting at 1).  Returns false if the unit was aborted or the wait ran out;
-// the latter raises the abort flag and the context's error flag.
-__device__ __forceinline__ bool wave_wait(const uint32_t *flag, uint32_t target, uint32_t *abort, int *err)
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
 {
-    for (int it = 0; it < kWaveSpinLimit; ++it) {
-        if (ld_acquire(flag) >= target) return true;
-        if (ld_acquire(abort) != 0u) return false;
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Invalidates the hand-off barriers of a finished unit (after a CTA barrier)
+// before the shared memory is used for anything else.
+__device__ __forceinline__ void wave_release(uint32_t *base, int NT)
+{
+    const WaveLayout lay(8 * 8 * 8, NT, 0, false);
+    uint64_t *bar_e = reinterpret_cast<uint64_t *>(base + lay.bar_e);
+    uint64_t *bar_h = reinterpret_cast<uint64_t *>(base + lay.bar_h);
+    for (int i = threadIdx.x; i < (NT + 1) / 2; i += blockDim.x) {
+        mbar_inval(&bar_e[i]);
+        mbar_inval(&bar_h[i]);
     }
-    st_release(abort, 1u);
+}
+
+// Waits (whole warp) for the phase of `bar` with the given parity.  Returns
+// false if the unit was aborted or the wait ran out; the latter raises the
+// abort flag and the context's error flag.
+__device__ __forceinline__ bool wave_wait(uint64_t *bar, uint32_t parity, volatile uint32_t *abort, int *err)
+{
+    for (int it = 0; it < kWaveWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort != 0u) return false;
+    }
+    *abort = 1u;
     atomicExch(err, 1);
     return false;
 }
@@ -200,7 +233,9 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     uint32_t *Js = base + lay.js;
     int *Eo = reinterpret_cast<int *>(base + lay.eo);
     int *Cur = reinterpret_cast<int *>(base + lay.cur);
-    uint32_t *flag_e = base + lay.flag_e, *flag_h = base + lay.flag_h, *abort = base + lay.abort;
+    uint64_t *bar_e = reinterpret_cast<uint64_t *>(base + lay.bar_e);
+    uint64_t *bar_h = reinterpret_cast<uint64_t *>(base + lay.bar_h);
+    volatile uint32_t *abort = base + lay.abort;
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, k = tid >> 5;
     const int c = (int)(unit % a.C);
@@ -224,7 +259,10 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         for (int w = tid; w < (NT - 1) * (int)a.swap_len; w += nthr) Tsw[w] = a.swapt[w];
         swt = Tsw;
     }
-    for (int i = tid; i < (NT + 1) / 2; i += nthr) flag_e[i] = flag_h[i] = 0u;
+    for (int i = tid; i < (NT + 1) / 2; i += nthr) {
+        mbar_init(&bar_e[i], kLanes);
+        mbar_init(&bar_h[i], kLanes);
+    }
     if (tid == 0) *abort = 0u;
     const uint64_t t0 = 0ull - (uint64_t)a.metro[ls * 3 + 0];
     const uint64_t t1 = 0ull - (uint64_t)a.metro[ls * 3 + 1];
@@ -242,6 +280,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         while (top <= (len >> 1)) top <<= 1;
     }
     __syncthreads();   // staged lattices, bonds, table and flags are complete; no CTA barrier after this
+    if (2 * k >= NT) return;                            // warps beyond the slots (wider CTAs of a batch)
 
     uint64_t P = a.P0;
     uint32_t pass_local = a.pass_local0;
@@ -249,6 +288,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     if (NT > 1 && a.swap_every != 0 && hasB) wave_bounds(swt, len, top, k, NT, c, P, gr, a.rk, lane, bA, bB);
     int EA = 0, EB = 0;                                 // energies of slots 2k, 2k+1 (lane = realization)
     bool ok_run = true;
+    uint32_t ph_e = 0, ph_h = 0;                        // parity of the next phase this warp waits for
 
     for (uint32_t n = 0; n < a.n_sweeps && ok_run; ++n) {
         const uint64_t s = a.s0 + n;
@@ -272,11 +312,11 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         if (swap_now) {
             // publish E_{2k} (pre-exchange) for pair 2k-1 of warp k-1
             Eo[2 * k * kLanes + lane] = EA;
-            __syncwarp();
-            if (lane == 0) st_release(&flag_e[k], n + 1);
+            if (k > 0) mbar_arrive(&bar_e[k - 1]);
             int cur = EA;
             if (k > 0) {
-                if (!wave_wait(&flag_h[k - 1], n + 1, abort, a.err)) { ok_run = false; break; }
+                if (!wave_wait(&bar_h[k - 1], ph_h, abort, a.err)) { ok_run = false; break; }
+                ph_h ^= 1u;
                 cur = Cur[(k - 1) * kLanes + lane];
             }
             uint32_t mA = 0, mB = 0;
@@ -298,7 +338,8 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
                 }
                 int nEB;
                 if (hasC) {
-                    if (!wave_wait(&flag_e[k + 1], n + 1, abort, a.err)) { ok_run = false; break; }
+                    if (!wave_wait(&bar_e[k], ph_e, abort, a.err)) { ok_run = false; break; }
+                    ph_e ^= 1u;
                     const int e2 = Eo[(2 * k + 2) * kLanes + lane];
                     const bool okB = cur - e2 >= bB;
                     mB = __ballot_sync(kFull, okB);
@@ -314,8 +355,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
                                                        mux(y.w, x.w, mB));
                     }
                     Cur[k * kLanes + lane] = cur;
-                    __syncwarp();
-                    if (lane == 0) st_release(&flag_h[k], n + 1);
+                    mbar_arrive(&bar_h[k]);
                 } else {
 #pragma unroll
                     for (int j = 0; j < N / 128; ++j) pb[lane + 32 * j] = xb[j];

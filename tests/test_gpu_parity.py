@@ -235,3 +235,43 @@ def test_autotune_keeps_state_and_picks_a_plan():
     assert gpu.plan == int(np.argmin(ms))
     assert gpu.counters == (3, 3)
     compare(gpu, sims, 10, 1)
+
+
+def _plan_index(gpu, form):
+    for i, p in enumerate(gpu.plans()):
+        if p["form"] == form:
+            return i
+    return None
+
+
+@pytest.mark.parametrize("NT,C,swap_every", [(1, 2, 1), (2, 2, 1), (3, 1, 1), (5, 2, 2), (6, 2, 1),
+                                             (7, 2, 3), (24, 2, 1), (24, 1, 0), (31, 2, 1), (32, 2, 5)])
+def test_wavefront_plan_edge_cases(NT, C, swap_every):
+    """The L = 8 wavefront unit kernel (one warp per two slots, the pass run
+    pair by pair across warps): odd and even slot counts, one and two copies,
+    with and without passes, calls split at arbitrary sweeps; every log equal
+    to the oracle's."""
+    inst = W.Instance(L=8, G=2, NT=NT, C=C, seed=900 + NT, tmin=0.9, tmax=2.0, input_seed=NT * 7 + C)
+    gpu, sims, _ = pair(inst)
+    i = _plan_index(gpu, "unit-wave")
+    assert i is not None and gpu.plan == i         # the default plan at L = 8, NT <= 32
+    for n in (7, 1, 12):
+        compare(gpu, sims, n, swap_every)
+
+
+def test_wavefront_plan_measured_calls_fall_back_exactly():
+    """Calls that measure (q histogram, energy sums) run under the specialised
+    plan; before and after them the wavefront plan continues the same chain."""
+    inst = W.Instance(L=8, G=3, NT=12, C=2, seed=4, tmin=0.9, tmax=2.0, input_seed=77)
+    gpu, sims, _ = pair(inst)
+    compare(gpu, sims, 5, 1)
+    qh = torch.zeros((inst.NT, inst.N + 1), dtype=torch.int64, device="cuda")
+    es = torch.zeros(inst.NT, dtype=torch.int64, device="cuda")
+    gpu.sweep(10, 1, qhist=qh, esum=es, measure_from=gpu.sweep_index + 3, measure_every=2)
+    qh_o = np.zeros((inst.NT, inst.N + 1), np.uint64)
+    es_o = np.zeros(inst.NT, np.int64)
+    for _, sim in sims:
+        sim.sweep(10, 1, qhist=qh_o, esum=es_o, measure_from=sim.sweep_index + 3, measure_every=2)
+    np.testing.assert_array_equal(qh.cpu().numpy().view(np.uint64), qh_o)
+    np.testing.assert_array_equal(es.cpu().numpy(), es_o)
+    compare(gpu, sims, 6, 1)
