@@ -136,32 +136,20 @@ __device__ __forceinline__ void acc_add_sum5(uint32_t (&acc)[PL], const uint32_t
     }
 }
 
-// Metropolis update of one quad of colour COL whose rows have x parity PX.
-template <int L, int COL, int PX, bool WITH_E, int PL>
-__device__ __forceinline__ void quad_fast(uint32_t *S, const uint32_t *J, const QuadRow &d,
-                                          const uint4 r, uint64_t t0, uint64_t t1, uint64_t t2,
-                                          uint32_t (&acc)[PL])
+// Metropolis update of the four sites of one quad whose rows have x parity
+// PX, from its loaded words: own spins, the other colour's words at the same
+// class index (xo) and in the rows y +- 1, z +- 1, the bonds of the own colour
+// (+x, +y, +z at the site) and of the other colour (-x at xo, -y at the y - 1
+// row, -z at the z - 1 row).  Valid for rows of four class indices (L = 8),
+// where the x neighbour across the quad edge is in xo itself, and through
+// xe_s / xe_j otherwise.  Returns the new own spins; with WITH_E adds the
+// post-update unsatisfied-bond counts to acc.
+template <int PX, bool WITH_E, int PL>
+__device__ __forceinline__ uint4 quad_core(uint4 own, uint4 xo, uint4 vyp, uint4 vym, uint4 vzp, uint4 vzm,
+                                           uint4 jcx, uint4 jcy, uint4 jcz, uint4 jox, uint4 joy, uint4 joz,
+                                           uint32_t xe_s, uint32_t xe_j, const uint4 r, uint64_t t0,
+                                           uint64_t t1, uint64_t t2, uint32_t (&acc)[PL])
 {
-    using Gm = Geo<L>;
-    constexpr int N = Gm::N, H = Gm::H, R = Gm::R;
-    uint32_t *Sc = S + COL * H;
-    const uint32_t *So = S + (1 - COL) * H;
-    const uint32_t *Jc = J + COL * H;
-    const uint32_t *Jo = J + (1 - COL) * H;
-    const uint4 own = ld4(Sc + d.k0), xo = ld4(So + d.k0);
-    const uint4 vyp = ld4(So + d.yp), vym = ld4(So + d.ym);
-    const uint4 vzp = ld4(So + d.zp), vzm = ld4(So + d.zm);
-    const uint4 jcx = ld4(Jc + d.k0), jcy = ld4(Jc + N + d.k0), jcz = ld4(Jc + 2 * N + d.k0);
-    const uint4 jox = ld4(Jo + d.k0), joy = ld4(Jo + N + d.ym), joz = ld4(Jo + 2 * N + d.zm);
-    uint32_t xe_s, xe_j;
-    if constexpr (R == 4) {
-        xe_s = PX ? xo.x : xo.w;
-        xe_j = jox.w;
-    } else {
-        const int ie = PX ? d.xe1 : d.xe0;
-        xe_s = So[ie];
-        xe_j = Jo[ie];
-    }
     uint32_t nxp[4], nxm[4], jxm[4];
     if constexpr (PX == 0) {
         nxp[0] = xo.x; nxp[1] = xo.y; nxp[2] = xo.z; nxp[3] = xo.w;
@@ -205,12 +193,42 @@ __device__ __forceinline__ void quad_fast(uint32_t *S, const uint32_t *J, const 
             x2[j] = u2 ^ (f & ~(u0 & u1));
         }
     }
-    *reinterpret_cast<uint4 *>(Sc + d.k0) = make_uint4(ns[0], ns[1], ns[2], ns[3]);
     if constexpr (WITH_E) {
         uint32_t A[5];
         quad_sum(x0, x1, x2, A);
         acc_add_sum5<PL>(acc, A);
     }
+    return make_uint4(ns[0], ns[1], ns[2], ns[3]);
+}
+
+// Metropolis update of one quad of colour COL whose rows have x parity PX.
+template <int L, int COL, int PX, bool WITH_E, int PL>
+__device__ __forceinline__ void quad_fast(uint32_t *S, const uint32_t *J, const QuadRow &d,
+                                          const uint4 r, uint64_t t0, uint64_t t1, uint64_t t2,
+                                          uint32_t (&acc)[PL])
+{
+    using Gm = Geo<L>;
+    constexpr int N = Gm::N, H = Gm::H, R = Gm::R;
+    uint32_t *Sc = S + COL * H;
+    const uint32_t *So = S + (1 - COL) * H;
+    const uint32_t *Jc = J + COL * H;
+    const uint32_t *Jo = J + (1 - COL) * H;
+    const uint4 own = ld4(Sc + d.k0), xo = ld4(So + d.k0);
+    const uint4 vyp = ld4(So + d.yp), vym = ld4(So + d.ym);
+    const uint4 vzp = ld4(So + d.zp), vzm = ld4(So + d.zm);
+    const uint4 jcx = ld4(Jc + d.k0), jcy = ld4(Jc + N + d.k0), jcz = ld4(Jc + 2 * N + d.k0);
+    const uint4 jox = ld4(Jo + d.k0), joy = ld4(Jo + N + d.ym), joz = ld4(Jo + 2 * N + d.zm);
+    uint32_t xe_s, xe_j;
+    if constexpr (R == 4) {
+        xe_s = PX ? xo.x : xo.w;
+        xe_j = jox.w;
+    } else {
+        const int ie = PX ? d.xe1 : d.xe0;
+        xe_s = So[ie];
+        xe_j = Jo[ie];
+    }
+    *reinterpret_cast<uint4 *>(Sc + d.k0) = quad_core<PX, WITH_E, PL>(
+        own, xo, vyp, vym, vzp, vzm, jcx, jcy, jcz, jox, joy, joz, xe_s, xe_j, r, t0, t1, t2, acc);
 }
 
 template <int L, int HP, int QPER, int COL, int PX, bool WITH_E, int PL>

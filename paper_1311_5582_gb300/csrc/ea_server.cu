@@ -2,19 +2,24 @@
 // state resident on the device, and advances every resident request together
 // in rounds of one persistent batched launch (continuous batching).
 //
-// One worker thread owns the GPU work.  Each round it
-//   1. launches one batched call (ea_batch_sweep_each) in which the resident
-//      requests with the least work left -- as many as give about two
-//      (group, copy) units per SM -- advance by min(q, sweeps left) sweeps, q
-//      sized so that the round lasts about round_ms at the measured rate
-//      (shortest remaining work first, which minimises mean latency when
+// One worker thread owns the GPU work.  Rounds run back to back on one
+// compute stream: while round k runs, the worker
+//   1. decides and launches round k+1 (ea_batch_sweep_each on the other of two
+//      batch objects, so neither overwrites the tables of a call in flight):
+//      the resident requests with the least work left -- as many as give
+//      about two (group, copy) units per SM -- advance by min(q, sweeps left)
+//      sweeps, q sized so that a round lasts about round_ms at the measured
+//      rate (shortest remaining work first, which minimises mean latency when
 //      requests queue, while keeping the GPU full);
-//   2. while that runs, admits queued requests in arrival order as long as
-//      their device bytes fit the budget (contexts are created on a second
-//      stream from a stream-ordered memory pool, so nothing waits for the
-//      round); they join the next round;
-//   3. waits for the round, then writes the outputs of finished requests to
-//      their host buffers and releases their memory.
+//   2. right behind each round, enqueues the export of the requests that the
+//      round finishes (their sweep counts are known when it is launched), and
+//      an event;
+//   3. admits queued requests in arrival order as long as their device bytes
+//      fit the budget (contexts are created on a second stream from a
+//      stream-ordered memory pool); they join the next round;
+//   4. waits for the previous round's event only, then copies the finished
+//      requests' outputs to their host buffers on a third stream and releases
+//      their memory -- the GPU meanwhile runs the round already queued.
 // Every request's trajectory is the one ea_sweep would give it alone: the
 // batch keeps each member's own counters, tables and swap schedule.
 #include <algorithm>
@@ -53,9 +58,20 @@ struct Request {
     size_t bytes = 0;                             // device bytes while resident
     Clock::time_point t_submit;
     ea_ctx *ctx = nullptr;
-    uint32_t left = 0;                            // sweeps still to run
+    uint32_t left = 0;                            // sweeps not yet launched
     uint64_t words = 0;                           // site-words of one sweep (N * NT * C * G)
     uint32_t waited = 0;                          // consecutive rounds left out
+    uint32_t *d_spins = nullptr;                  // export scratch (pool) of a finishing request
+    int32_t *d_energies = nullptr;
+    int status = EA_OK;                           // of the export
+};
+
+// A launched round: its completion event and the requests it finishes.
+struct Round {
+    cudaEvent_t start = nullptr, done = nullptr;
+    std::vector<std::unique_ptr<Request>> finishing;
+    double work = 0.0;                            // site-word updates of the round
+    bool active = false;
 };
 
 // A request left out of this many consecutive rounds goes first in the next.
@@ -68,10 +84,12 @@ struct ea_server {
     size_t budget = 0, used = 0, peak = 0;
     uint32_t max_live = 256;
     double round_ms = 20.0;
-    cudaStream_t compute = nullptr, admit = nullptr;
+    cudaStream_t compute = nullptr, admit = nullptr, copy = nullptr;
     cudaEvent_t admitted = nullptr;
     cudaMemPool_t pool = nullptr;
-    ea_batch *batch = nullptr;
+    ea_batch *batch[2] = {nullptr, nullptr};      // rounds alternate between the two
+    Round rounds_ring[2];
+    uint64_t round_index = 0;
     std::thread worker;
     Clock::time_point t0;
 
@@ -165,108 +183,117 @@ void admit(ea_server *s)
     s->n_live = s->live.size();
 }
 
-// Writes the outputs of the finished requests among live[0, n) and releases them.
-void complete(ea_server *s, std::vector<size_t> &done)
+// Enqueues on the compute stream, behind the round that finishes request r,
+// the export of its final energies and spins into pool scratch.
+void enqueue_export(ea_server *s, Request &r)
 {
-    if (done.empty()) return;
-    std::vector<int> status(done.size(), EA_OK);
-    std::vector<std::pair<uint32_t *, int32_t *>> scratch(done.size(), {nullptr, nullptr});
-    for (size_t j = 0; j < done.size(); ++j) {
-        Request &r = *s->live[done[j]];
-        ea_ctx *c = r.ctx;
-        const size_t nsp = (size_t)c->G * c->NT * c->C * c->N, nen = (size_t)c->G * c->NT * c->C * ea::kLanes;
-        cudaError_t e = cudaSuccess;
-        int rc = EA_OK;
-        if (r.energies_out) {
-            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&scratch[j].second), nen * 4, s->pool, s->compute);
-            if (e == cudaSuccess) rc = ea_measure(c, scratch[j].second, nullptr, nullptr);
-            if (e == cudaSuccess && rc == EA_OK)
-                e = cudaMemcpyAsync(r.energies_out, scratch[j].second, nen * 4, cudaMemcpyDeviceToHost, s->compute);
-        }
-        if (e == cudaSuccess && rc == EA_OK && r.spins_out) {
-            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&scratch[j].first), nsp * 4, s->pool, s->compute);
-            if (e == cudaSuccess) rc = ea_read_spins(c, scratch[j].first);
-            if (e == cudaSuccess && rc == EA_OK)
-                e = cudaMemcpyAsync(r.spins_out, scratch[j].first, nsp * 4, cudaMemcpyDeviceToHost, s->compute);
-        }
-        status[j] = e != cudaSuccess ? (e == cudaErrorMemoryAllocation ? EA_ENOMEM : EA_ECUDA) : rc;
+    ea_ctx *c = r.ctx;
+    const size_t nsp = (size_t)c->G * c->NT * c->C * c->N, nen = (size_t)c->G * c->NT * c->C * ea::kLanes;
+    cudaError_t e = cudaSuccess;
+    int rc = EA_OK;
+    if (r.energies_out) {
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.d_energies), nen * 4, s->pool, s->compute);
+        if (e == cudaSuccess) rc = ea_measure(c, r.d_energies, nullptr, nullptr);
     }
-    const cudaError_t es = cudaStreamSynchronize(s->compute);
-    for (size_t j = 0; j < done.size(); ++j) {
-        Request &r = *s->live[done[j]];
-        if (scratch[j].first) cudaFreeAsync(scratch[j].first, s->compute);
-        if (scratch[j].second) cudaFreeAsync(scratch[j].second, s->compute);
-        ea::destroy_ctx(r.ctx, s->compute);
-        r.ctx = nullptr;
-        s->used -= r.bytes;
-        finish(s, r, es != cudaSuccess ? EA_ECUDA : status[j]);
+    if (e == cudaSuccess && rc == EA_OK && r.spins_out) {
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.d_spins), nsp * 4, s->pool, s->compute);
+        if (e == cudaSuccess) rc = ea_read_spins(c, r.d_spins);
     }
-    // drop the finished entries (indices ascending)
-    for (size_t j = done.size(); j-- > 0;) s->live.erase(s->live.begin() + (std::ptrdiff_t)done[j]);
-    done.clear();
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->n_live = s->live.size();
+    r.status = e != cudaSuccess ? (e == cudaErrorMemoryAllocation ? EA_ENOMEM : EA_ECUDA) : rc;
 }
 
-// One round over the resident requests live[0, n).
-void run_round(ea_server *s)
+// Waits for a launched round (and the exports behind it), copies the outputs
+// of the requests it finished to their host buffers on the copy stream, and
+// releases their scratch and device state.
+void deliver(ea_server *s, Round &rd)
 {
-    const size_t n = s->live.size();
-    std::vector<size_t> done;
-    // requests with nothing to run (zero sweeps) finish at once
-    for (size_t i = 0; i < n; ++i)
-        if (s->live[i]->left == 0) done.push_back(i);
-    if (!done.empty()) {
-        complete(s, done);
-        return;
+    const cudaError_t es = cudaEventSynchronize(rd.done);
+    float ms = 0.0f;
+    if (es == cudaSuccess && cudaEventElapsedTime(&ms, rd.start, rd.done) == cudaSuccess && ms > 0.5f)
+        s->rate = 0.5 * s->rate + 0.5 * (rd.work / (double)ms);
+    std::vector<int> status(rd.finishing.size(), EA_OK);
+    for (size_t j = 0; j < rd.finishing.size(); ++j) {
+        Request &r = *rd.finishing[j];
+        ea_ctx *c = r.ctx;
+        int st = es != cudaSuccess ? EA_ECUDA : r.status;
+        cudaError_t e = cudaSuccess;
+        if (st == EA_OK && r.energies_out)
+            e = cudaMemcpyAsync(r.energies_out, r.d_energies, (size_t)c->G * c->NT * c->C * ea::kLanes * 4,
+                                cudaMemcpyDeviceToHost, s->copy);
+        if (st == EA_OK && e == cudaSuccess && r.spins_out)
+            e = cudaMemcpyAsync(r.spins_out, r.d_spins, (size_t)c->G * c->NT * c->C * c->N * 4,
+                                cudaMemcpyDeviceToHost, s->copy);
+        if (e != cudaSuccess) st = EA_ECUDA;
+        status[j] = st;
     }
-    // Shortest remaining work first, as far as the GPU stays full: the requests
-    // with the least work left join this round, in that order, until their
-    // (group, copy) units give about two tasks per SM; the rest wait a round.
+    const cudaError_t ec = cudaStreamSynchronize(s->copy);
+    for (size_t j = 0; j < rd.finishing.size(); ++j) {
+        Request &r = *rd.finishing[j];
+        if (r.d_spins) cudaFreeAsync(r.d_spins, s->copy);
+        if (r.d_energies) cudaFreeAsync(r.d_energies, s->copy);
+        r.d_spins = nullptr;
+        r.d_energies = nullptr;
+        ea::destroy_ctx(r.ctx, s->compute);      // after every round already queued
+        r.ctx = nullptr;
+        s->used -= r.bytes;
+        finish(s, r, ec != cudaSuccess ? EA_ECUDA : status[j]);
+    }
+    rd.finishing.clear();
+    rd.active = false;
+}
+
+// Launches round k on batch object k % 2 (whose previous call, round k - 2,
+// has been delivered): the resident requests in order of least work left
+// until their (group, copy) units give about two tasks per SM; then the
+// exports of the requests this round finishes and the round's event.
+void run_round(ea_server *s, uint64_t k)
+{
+    Round &rd = s->rounds_ring[k & 1];
+    ea_batch *b = s->batch[k & 1];
+    const size_t n = s->live.size();
+    // requests with nothing to run (zero sweeps) finish with this round
+    std::vector<char> in_round(n, 0);
     std::vector<size_t> order(n);
     for (size_t i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
-        const Request &a = *s->live[x], &b = *s->live[y];
-        const bool aged_a = a.waited >= kAgeRounds, aged_b = b.waited >= kAgeRounds;
+        const Request &a = *s->live[x], &bq = *s->live[y];
+        const bool aged_a = a.waited >= kAgeRounds, aged_b = bq.waited >= kAgeRounds;
         if (aged_a != aged_b) return aged_a;      // starved requests first
-        return (double)a.left * (double)a.words < (double)b.left * (double)b.words;
+        return (double)a.left * (double)a.words < (double)bq.left * (double)bq.words;
     });
-    std::vector<char> in_round(n, 0);
     double words = 0.0;
     uint64_t units = 0;
     for (size_t j = 0; j < n; ++j) {
         const Request &r = *s->live[order[j]];
-        if (units >= 2ull * (uint64_t)s->sms && j > 0) break;
+        if (r.left == 0) continue;
+        if (units >= 2ull * (uint64_t)s->sms && words > 0.0) break;
         in_round[order[j]] = 1;
         words += (double)r.words;
         units += (uint64_t)r.ctx->G * r.ctx->C;
     }
-    double qd = s->round_ms * s->rate / (words > 0 ? words : 1.0);
+    const double qd = s->round_ms * s->rate / (words > 0 ? words : 1.0);
     const uint32_t q = (uint32_t)std::max(1.0, std::min(qd, 1048576.0));
-    ea_batch_clear(s->batch);
+    ea_batch_clear(b);
     std::vector<uint32_t> nsw(n), kev(n);
     int rc = EA_OK;
     for (size_t i = 0; i < n && rc == EA_OK; ++i) {
         Request &r = *s->live[i];
-        rc = ea_batch_add(s->batch, r.ctx);
+        rc = ea_batch_add(b, r.ctx);
         nsw[i] = in_round[i] ? std::min(q, r.left) : 0u;
         r.waited = in_round[i] ? 0u : r.waited + 1u;
         kev[i] = r.swap_every;
     }
     double work = 0.0;
     for (size_t i = 0; i < n; ++i) work += (double)nsw[i] * (double)s->live[i]->words;
-    const Clock::time_point t_start = Clock::now();
-    if (rc == EA_OK) rc = ea_batch_sweep_each(s->batch, nsw.data(), kev.data());
-    admit(s);                                    // overlaps the round
-    if (rc == EA_OK) rc = ea_batch_sync(s->batch);
-    const double dt = ms_between(t_start, Clock::now());
-    if (rc == EA_OK && dt > 0.5) s->rate = 0.5 * s->rate + 0.5 * (work / dt);
+    cudaEventRecord(rd.start, s->compute);
+    if (rc == EA_OK && work > 0.0) rc = ea_batch_sweep_each(b, nsw.data(), kev.data());
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->rounds += 1;
     }
     if (rc != EA_OK) {
-        // the round failed: every request in it fails with the round's status
+        // the round failed: every resident request fails with its status
+        cudaStreamSynchronize(s->compute);
         for (size_t i = 0; i < n; ++i) {
             Request &r = *s->live[i];
             ea::destroy_ctx(r.ctx, s->compute);
@@ -274,18 +301,30 @@ void run_round(ea_server *s)
             s->used -= r.bytes;
             finish(s, r, rc);
         }
-        s->live.erase(s->live.begin(), s->live.begin() + (std::ptrdiff_t)n);
+        s->live.clear();
         cudaStreamSynchronize(s->compute);
         std::lock_guard<std::mutex> lk(s->mu);
-        s->n_live = s->live.size();
+        s->n_live = 0;
         return;
     }
+    // requests whose sweeps are now all launched finish with this round
+    std::vector<std::unique_ptr<Request>> keep;
     for (size_t i = 0; i < n; ++i) {
-        Request &r = *s->live[i];
-        r.left -= nsw[i];
-        if (r.left == 0) done.push_back(i);
+        std::unique_ptr<Request> &r = s->live[i];
+        r->left -= nsw[i];
+        if (r->left == 0) {
+            enqueue_export(s, *r);
+            rd.finishing.push_back(std::move(r));
+        } else {
+            keep.push_back(std::move(r));
+        }
     }
-    complete(s, done);
+    s->live.swap(keep);
+    cudaEventRecord(rd.done, s->compute);
+    rd.work = work;
+    rd.active = true;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->n_live = s->live.size();
 }
 
 void worker_main(ea_server *s)
@@ -294,20 +333,27 @@ void worker_main(ea_server *s)
     Clock::time_point busy_from;
     bool busy = false;
     for (;;) {
+        const bool in_flight = s->rounds_ring[0].active || s->rounds_ring[1].active;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (s->live.empty())
+            if (s->live.empty() && !in_flight)
                 s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
             if (s->stop) break;
         }
         admit(s);
-        if (s->live.empty()) continue;
-        if (!busy) {
+        if (!busy && (!s->live.empty() || in_flight)) {
             busy = true;
             busy_from = Clock::now();
         }
-        run_round(s);
-        if (s->live.empty() && busy) {
+        const uint64_t k = s->round_index;
+        Round &prev = s->rounds_ring[(k + 1) & 1];       // round k - 1, if any
+        if (!s->live.empty()) {
+            run_round(s, k);                              // queued behind round k - 1
+            s->round_index = k + 1;
+        }
+        if (prev.active) deliver(s, prev);
+        const bool idle = s->live.empty() && !s->rounds_ring[0].active && !s->rounds_ring[1].active;
+        if (idle && busy) {
             busy = false;
             std::lock_guard<std::mutex> lk(s->mu);
             s->busy_s += ms_between(busy_from, Clock::now()) * 1e-3;
@@ -316,12 +362,40 @@ void worker_main(ea_server *s)
     // shutting down: drop what is left
     cudaStreamSynchronize(s->compute);
     cudaStreamSynchronize(s->admit);
+    cudaStreamSynchronize(s->copy);
+    for (Round &rd : s->rounds_ring) {
+        for (auto &r : rd.finishing) {
+            if (r->d_spins) cudaFreeAsync(r->d_spins, s->compute);
+            if (r->d_energies) cudaFreeAsync(r->d_energies, s->compute);
+            ea::destroy_ctx(r->ctx, s->compute);
+            r->ctx = nullptr;
+        }
+        rd.finishing.clear();
+        rd.active = false;
+    }
     for (auto &r : s->live) {
         ea::destroy_ctx(r->ctx, s->compute);
         r->ctx = nullptr;
     }
     s->live.clear();
     cudaStreamSynchronize(s->compute);
+}
+
+// Frees a server's streams, events, pool and batch objects (worker stopped).
+void release_server(ea_server *s)
+{
+    for (ea_batch *b : s->batch)
+        if (b) ea_batch_destroy(b);
+    for (Round &rd : s->rounds_ring) {
+        if (rd.start) cudaEventDestroy(rd.start);
+        if (rd.done) cudaEventDestroy(rd.done);
+    }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    if (s->admitted) cudaEventDestroy(s->admitted);
+    if (s->copy) cudaStreamDestroy(s->copy);
+    if (s->admit) cudaStreamDestroy(s->admit);
+    if (s->compute) cudaStreamDestroy(s->compute);
+    delete s;
 }
 
 // Up-front checks of a request (the tables are validated at admission).
@@ -358,7 +432,12 @@ int ea_server_create(const ea_server_opts *opts, ea_server **out)
     if (opts && opts->round_ms) s->round_ms = opts->round_ms;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->admitted, cudaEventDisableTiming);
+    for (Round &rd : s->rounds_ring) {
+        if (e == cudaSuccess) e = cudaEventCreate(&rd.start);
+        if (e == cudaSuccess) e = cudaEventCreate(&rd.done);
+    }
     if (e == cudaSuccess) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;
@@ -372,26 +451,18 @@ int ea_server_create(const ea_server_opts *opts, ea_server **out)
         e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     int rc = e == cudaSuccess ? EA_OK : EA_ECUDA;
-    if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch);
-    if (rc != EA_OK) {
-        if (s->batch) ea_batch_destroy(s->batch);
-        if (s->pool) cudaMemPoolDestroy(s->pool);
-        if (s->admitted) cudaEventDestroy(s->admitted);
-        if (s->admit) cudaStreamDestroy(s->admit);
-        if (s->compute) cudaStreamDestroy(s->compute);
-        delete s;
-        return rc;
+    if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch[0]);
+    if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch[1]);
+    if (rc == EA_OK) {
+        try {
+            s->worker = std::thread(worker_main, s);
+        } catch (...) {
+            rc = EA_ENOMEM;
+        }
     }
-    try {
-        s->worker = std::thread(worker_main, s);
-    } catch (...) {
-        ea_batch_destroy(s->batch);
-        cudaMemPoolDestroy(s->pool);
-        cudaEventDestroy(s->admitted);
-        cudaStreamDestroy(s->admit);
-        cudaStreamDestroy(s->compute);
-        delete s;
-        return EA_ENOMEM;
+    if (rc != EA_OK) {
+        release_server(s);
+        return rc;
     }
     *out = s;
     return EA_OK;
@@ -501,12 +572,7 @@ void ea_server_destroy(ea_server *s)
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
-    ea_batch_destroy(s->batch);
-    cudaMemPoolDestroy(s->pool);
-    cudaEventDestroy(s->admitted);
-    cudaStreamDestroy(s->admit);
-    cudaStreamDestroy(s->compute);
-    delete s;
+    release_server(s);
 }
 
 }  // extern "C"

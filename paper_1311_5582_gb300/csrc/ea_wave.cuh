@@ -115,30 +115,117 @@ __device__ __forceinline__ bool wave_wait(uint64_t *bar, uint32_t parity, volati
 // (a & ~m) | (b & m): one LOP3.
 __device__ __forceinline__ uint32_t mux(uint32_t a, uint32_t b, uint32_t m) { return (a & ~m) | (b & m); }
 
-// One quad of the lane: quad J of (row parity J >> 1, row index base + 16 (J & 1)).
-template <int COL, int J, bool WITH_E, int PL>
-__device__ __forceinline__ void wave_quad(uint32_t *mine, const uint32_t *Js, const QuadRow &d, uint4 r,
-                                          uint64_t t0, uint64_t t1, uint64_t t2, uint32_t (&acc)[PL])
+// Per-quad constants of the lane: shared-window byte addresses of the words
+// the quad reads (the colour and direction of each word are immediate offsets
+// from these), and the parts of the first two Philox rounds that depend on
+// the quad's counter word q = k0 / 4 and the group only.
+struct WaveQuad {
+    uint32_t s, yp, ym, zp, zm;     // lattice + k0, + yp, + ym, + zp, + zm
+    uint32_t j, jym, jzm;           // bonds + k0, + ym, + zm
+    uint32_t plo0, plo1, phi1;      // M0 q, M1 n, umulhi(M1, n) with n = umulhi(M0, q) ^ g ^ key1
+};
+
+__device__ __forceinline__ WaveQuad wave_quad_setup(const uint32_t *mine, const uint32_t *Js, const QuadRow &d,
+                                                    uint32_t gr, const RoundKeys &rk)
 {
-    constexpr int PX = ((J >> 1) + COL) & 1;
-    quad_fast<8, COL, PX, WITH_E, PL>(mine, Js, d, r, t0, t1, t2, acc);
+    WaveQuad w;
+    const uint32_t sb = smem_addr(mine), jb = smem_addr(Js);
+    w.s = sb + 4u * (uint32_t)d.k0;
+    w.yp = sb + 4u * (uint32_t)d.yp;
+    w.ym = sb + 4u * (uint32_t)d.ym;
+    w.zp = sb + 4u * (uint32_t)d.zp;
+    w.zm = sb + 4u * (uint32_t)d.zm;
+    w.j = jb + 4u * (uint32_t)d.k0;
+    w.jym = jb + 4u * (uint32_t)d.ym;
+    w.jzm = jb + 4u * (uint32_t)d.zm;
+    const uint32_t q = (uint32_t)d.k0 >> 2;
+    w.plo0 = kM0 * q;
+    const uint32_t n = __umulhi(kM0, q) ^ gr ^ rk.k[1];
+    w.plo1 = kM1 * n;
+    w.phi1 = __umulhi(kM1, n);
+    return w;
 }
 
-// Half-sweep of colour COL over the lane's four quads; the uniforms of the
-// next quad are drawn while the current one is updated.
-template <int COL, bool WITH_E, int PL>
-__device__ __forceinline__ void wave_half(uint32_t *mine, const uint32_t *Js, const QuadRow (&qd)[4],
-                                          uint32_t s, uint32_t gr, uint32_t ctag, const RoundKeys &rk,
-                                          uint64_t t0, uint64_t t1, uint64_t t2, uint32_t (&acc)[PL])
+// Rounds 2..9 of Philox4x32-10 from the state after round 1.
+__device__ __forceinline__ uint4 philox_from2(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              const RoundKeys &rk)
 {
-    uint4 r0 = philox((uint32_t)(qd[0].k0 >> 2), ctag, s, gr, rk);
-    uint4 r1 = philox((uint32_t)(qd[1].k0 >> 2), ctag, s, gr, rk);
-    wave_quad<COL, 0, WITH_E, PL>(mine, Js, qd[0], r0, t0, t1, t2, acc);
-    r0 = philox((uint32_t)(qd[2].k0 >> 2), ctag, s, gr, rk);
-    wave_quad<COL, 1, WITH_E, PL>(mine, Js, qd[1], r1, t0, t1, t2, acc);
-    r1 = philox((uint32_t)(qd[3].k0 >> 2), ctag, s, gr, rk);
-    wave_quad<COL, 2, WITH_E, PL>(mine, Js, qd[2], r0, t0, t1, t2, acc);
-    wave_quad<COL, 3, WITH_E, PL>(mine, Js, qd[3], r1, t0, t1, t2, acc);
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint32_t lo0 = kM0 * c0, hi0 = __umulhi(kM0, c0);
+        const uint32_t lo1 = kM1 * c2, hi1 = __umulhi(kM1, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ rk.k[2 * r];
+        const uint32_t n2 = hi0 ^ c3 ^ rk.k[2 * r + 1];
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Shared-memory vector load and store at a byte address plus an immediate.
+// The loads are not volatile (the scheduler may move them); `dep`, an opaque
+// zero made after the last barrier, keeps them from being moved above it.
+template <int OFF>
+__device__ __forceinline__ uint4 lds4(uint32_t addr, uint32_t dep)
+{
+    uint4 v;
+    asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4+%5];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "r"(addr), "n"(OFF), "r"(dep));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ void sts4(uint32_t addr, uint4 v)
+{
+    asm volatile("st.shared.v4.u32 [%0+%1], {%2, %3, %4, %5};" ::"r"(addr), "n"(OFF), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w));
+}
+__device__ __forceinline__ uint32_t opaque_zero()
+{
+    uint32_t z;
+    asm volatile("mov.u32 %0, 0;" : "=r"(z));
+    return z;
+}
+
+// Metropolis update of one quad of colour COL with x parity PX (L = 8).
+template <int COL, int PX, bool WITH_E, int PL>
+__device__ __forceinline__ void wave_quad(const WaveQuad &q, uint4 r, uint64_t t0, uint64_t t1, uint64_t t2,
+                                          uint32_t (&acc)[PL], uint32_t dep)
+{
+    constexpr int H4 = 256 * 4, N4 = 512 * 4;           // bytes of a colour half and of a bond direction
+    constexpr int C4 = COL * H4, O4 = (1 - COL) * H4;
+    const uint4 own = lds4<C4>(q.s, dep), xo = lds4<O4>(q.s, dep);
+    const uint4 vyp = lds4<O4>(q.yp, dep), vym = lds4<O4>(q.ym, dep);
+    const uint4 vzp = lds4<O4>(q.zp, dep), vzm = lds4<O4>(q.zm, dep);
+    const uint4 jcx = lds4<C4>(q.j, dep), jcy = lds4<N4 + C4>(q.j, dep), jcz = lds4<2 * N4 + C4>(q.j, dep);
+    const uint4 jox = lds4<O4>(q.j, dep), joy = lds4<N4 + O4>(q.jym, dep), joz = lds4<2 * N4 + O4>(q.jzm, dep);
+    const uint32_t xe_s = PX ? xo.x : xo.w;             // x neighbour across the row's edge (R = 4)
+    sts4<C4>(q.s, quad_core<PX, WITH_E, PL>(own, xo, vyp, vym, vzp, vzm, jcx, jcy, jcz, jox, joy, joz, xe_s,
+                                             jox.w, r, t0, t1, t2, acc));
+}
+
+// Half-sweep of colour COL over the lane's four quads (quad j: row parity
+// j >> 1, x parity ((j >> 1) + COL) & 1).  The sweep- and colour-only parts
+// of the first two Philox rounds are formed once; the uniforms of the next
+// quad are drawn while the current one is updated.
+template <int COL, bool WITH_E, int PL>
+__device__ __forceinline__ void wave_half(const WaveQuad (&wq)[4], uint32_t s, uint32_t ctag,
+                                          const RoundKeys &rk, uint64_t t0, uint64_t t1, uint64_t t2,
+                                          uint32_t (&acc)[PL])
+{
+    const uint32_t dep = opaque_zero();
+    const uint32_t lo1 = kM1 * s, n0 = __umulhi(kM1, s) ^ ctag ^ rk.k[0];
+    const uint32_t lo0b = kM0 * n0, hi0b = __umulhi(kM0, n0);
+    auto draw = [&](const WaveQuad &q) {
+        return philox_from2(q.phi1 ^ lo1 ^ rk.k[2], q.plo1, hi0b ^ q.plo0 ^ rk.k[3], lo0b, rk);
+    };
+    uint4 r0 = draw(wq[0]);
+    uint4 r1 = draw(wq[1]);
+    wave_quad<COL, COL, WITH_E, PL>(wq[0], r0, t0, t1, t2, acc, dep);
+    r0 = draw(wq[2]);
+    wave_quad<COL, COL, WITH_E, PL>(wq[1], r1, t0, t1, t2, acc, dep);
+    r1 = draw(wq[3]);
+    wave_quad<COL, 1 - COL, WITH_E, PL>(wq[2], r0, t0, t1, t2, acc, dep);
+    wave_quad<COL, 1 - COL, WITH_E, PL>(wq[3], r1, t0, t1, t2, acc, dep);
 }
 
 // Unsatisfied-bond totals of the warp's two slots: each half-warp sums its
@@ -175,14 +262,36 @@ __device__ __forceinline__ void wave_reduce(const uint32_t (&acc)[PL], int lane,
     UB = (int)(y >> 16);
 }
 
+// Number of leading entries of a non-increasing threshold row above r (the
+// acceptance bound of Sec. 2.4 with the table of Sec. 4.3.2 is -4 times it).
+// Entry k-1 is floor(exp(-4k dbeta) 2^32), so the count is close to
+// log2(2^32 / (r + 1)) / (32 - log2 row[0]); `slope` holds the reciprocal of
+// that denominator.  The estimate is then corrected by stepping along the row
+// until the defining inequalities hold, so the result is exact whatever the
+// rounding of the estimate (usually no step or one).
+__device__ __forceinline__ uint32_t count_above(const uint32_t *row, uint32_t len, uint32_t r, float slope)
+{
+    const float g = (32.0f - __log2f((float)r + 1.0f)) * slope;
+    uint32_t k = g < (float)len ? (uint32_t)g : len;    // also catches an infinite slope
+    while (k < len && row[k] > r) ++k;
+    while (k > 0 && row[k - 1] <= r) --k;
+    return k;
+}
+
+__device__ __forceinline__ float count_slope(const uint32_t *row, uint32_t len)
+{
+    if (len == 0 || row[0] == 0u) return 0.0f;
+    return 1.0f / (32.0f - __log2f((float)row[0]));    // +inf when row[0] rounds to 2^32
+}
+
 // Acceptance bounds of the warp's pairs 2k and 2k+1 in pass P for the
 // realization of this lane (Sec. 2.4 with the integer table of Sec. 4.3.2):
 // pair p is accepted iff E_p - E_{p+1} >= bound.  Lanes 0-7 draw the Philox
 // blocks of pair 2k (realizations 4q..4q+3 from lane q), lanes 8-15 those of
-// pair 2k+1; each lane then searches both rows for its own uniforms.
-__device__ __forceinline__ void wave_bounds(const uint32_t *swt, uint32_t len, uint32_t top, int k, int NT,
-                                            int c, uint64_t P, uint32_t gr, const RoundKeys &rk,
-                                            int lane, int &bA, int &bB)
+// pair 2k+1; each lane then counts both rows for its own uniforms.
+__device__ __forceinline__ void wave_bounds(const uint32_t *rowa, const uint32_t *rowb, uint32_t len, float sa,
+                                            float sb, int k, int c, uint64_t P, uint32_t gr,
+                                            const RoundKeys &rk, int lane, int &bA, int &bB)
 {
     const int pq = (lane >> 3) & 1, bq = lane & 7;
     const int p = 2 * k + pq;
@@ -200,18 +309,8 @@ __device__ __forceinline__ void wave_bounds(const uint32_t *swt, uint32_t len, u
         const uint32_t z = __shfl_sync(kFull, v.z, src + 8), q = __shfl_sync(kFull, v.w, src + 8);
         rb = w == 0 ? x : w == 1 ? y : w == 2 ? z : q;
     }
-    const int pa = min(2 * k, NT - 2), pb = min(2 * k + 1, NT - 2);   // rows in range; unused otherwise
-    const uint32_t *rowa = swt + (size_t)max(pa, 0) * len, *rowb = swt + (size_t)max(pb, 0) * len;
-    uint32_t ka = 0, kb = 0;                  // invariant: row[0..k) > r
-    for (uint32_t st = top; st != 0; st >>= 1) {
-        const uint32_t na = ka + st, nb = kb + st;
-        const uint32_t ea = na <= len ? rowa[na - 1] : 0u;
-        const uint32_t eb = nb <= len ? rowb[nb - 1] : 0u;
-        ka = ea > ra ? na : ka;
-        kb = eb > rb ? nb : kb;
-    }
-    bA = -4 * (int)ka;
-    bB = -4 * (int)kb;
+    bA = -4 * (int)count_above(rowa, len, ra, sa);
+    bB = -4 * (int)count_above(rowb, len, rb, sb);
 }
 
 // LOG = false compiles the body without the energy and swap logs (their
@@ -267,25 +366,24 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     const uint64_t t0 = 0ull - (uint64_t)a.metro[ls * 3 + 0];
     const uint64_t t1 = 0ull - (uint64_t)a.metro[ls * 3 + 1];
     const uint64_t t2 = 0ull - (uint64_t)a.metro[ls * 3 + 2];
-    QuadRow qd[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) qd[j] = quad_row<L>(j >> 1, li + 16 * (j & 1));
     uint32_t *mine = S + (size_t)ls * N;
+    WaveQuad wq[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) wq[j] = wave_quad_setup(mine, Js, quad_row<L>(j >> 1, li + 16 * (j & 1)), gr, a.rk);
     const uint32_t tag0 = ((uint32_t)c << 8) | (uint32_t)ls;
     const uint32_t tag1 = (1u << 16) | tag0;
     const uint32_t len = a.swap_len;
-    uint32_t top = 0;                                   // largest power of two <= len
-    if (len != 0) {
-        top = 1;
-        while (top <= (len >> 1)) top <<= 1;
-    }
     __syncthreads();   // staged lattices, bonds, table and flags are complete; no CTA barrier after this
     if (2 * k >= NT) return;                            // warps beyond the slots (wider CTAs of a batch)
+    // rows of the warp's pairs 2k and 2k+1 (clamped into range; unused when the pair does not exist)
+    const uint32_t *rowa = swt + (size_t)max(min(2 * k, NT - 2), 0) * len;
+    const uint32_t *rowb = swt + (size_t)max(min(2 * k + 1, NT - 2), 0) * len;
+    const float sa = count_slope(rowa, len), sb = count_slope(rowb, len);
 
     uint64_t P = a.P0;
     uint32_t pass_local = a.pass_local0;
     int bA = 0, bB = 0;
-    if (NT > 1 && a.swap_every != 0 && hasB) wave_bounds(swt, len, top, k, NT, c, P, gr, a.rk, lane, bA, bB);
+    if (NT > 1 && a.swap_every != 0 && hasB) wave_bounds(rowa, rowb, len, sa, sb, k, c, P, gr, a.rk, lane, bA, bB);
     int EA = 0, EB = 0;                                 // energies of slots 2k, 2k+1 (lane = realization)
     bool ok_run = true;
     uint32_t ph_e = 0, ph_h = 0;                        // parity of the next phase this warp waits for
@@ -297,16 +395,16 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         uint32_t acc[PL];
 #pragma unroll
         for (int p = 0; p < PL; ++p) acc[p] = 0;
-        if (act) wave_half<0, false, PL>(mine, Js, qd, (uint32_t)s, gr, tag0, a.rk, t0, t1, t2, acc);
+        if (act) wave_half<0, false, PL>(wq, (uint32_t)s, tag0, a.rk, t0, t1, t2, acc);
         __syncwarp();
         if (needE) {
-            if (act) wave_half<1, true, PL>(mine, Js, qd, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
+            if (act) wave_half<1, true, PL>(wq, (uint32_t)s, tag1, a.rk, t0, t1, t2, acc);
             int UA, UB;
             wave_reduce<PL>(acc, lane, UA, UB);          // also orders the colour-1 stores (shuffles)
             EA = 2 * UA - 3 * N;
             EB = 2 * UB - 3 * N;
         } else if (act) {
-            wave_half<1, false, PL>(mine, Js, qd, (uint32_t)s, gr, tag1, a.rk, t0, t1, t2, acc);
+            wave_half<1, false, PL>(wq, (uint32_t)s, tag1, a.rk, t0, t1, t2, acc);
         }
         __syncwarp();
         if (swap_now) {
@@ -374,7 +472,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
             }
             ++P;
             ++pass_local;
-            if (hasB) wave_bounds(swt, len, top, k, NT, c, P, gr, a.rk, lane, bA, bB);
+            if (hasB) wave_bounds(rowa, rowb, len, sa, sb, k, c, P, gr, a.rk, lane, bA, bB);
         } else if (swap_after(s, a.swap_every)) {
             ++P;                                        // NT == 1: passes count, nothing to exchange
             ++pass_local;

@@ -275,3 +275,15 @@ def test_wavefront_plan_measured_calls_fall_back_exactly():
     np.testing.assert_array_equal(qh.cpu().numpy().view(np.uint64), qh_o)
     np.testing.assert_array_equal(es.cpu().numpy(), es_o)
     compare(gpu, sims, 6, 1)
+
+
+@pytest.mark.parametrize("tmin,tmax,NT", [(1.5, 1.5, 6), (0.2, 50.0, 5), (0.9, 0.95, 24), (0.3, 3.0, 2)])
+def test_wavefront_plan_degenerate_ladders(tmin, tmax, NT):
+    """Acceptance counts at the ends of the table range: equal temperatures (every
+    entry 2^32 - 1, the count is the whole row), widely spaced ones (rows of zeros
+    or a few entries), a dense ladder, and a single pair."""
+    inst = W.Instance(L=8, G=2, NT=NT, C=2, seed=int(tmax * 10) + NT, tmin=tmin, tmax=tmax,
+                      input_seed=NT + 3)
+    gpu, sims, _ = pair(inst)
+    assert gpu.plans()[gpu.plan]["form"] == "unit-wave"
+    compare(gpu, sims, 20, 1)
