@@ -422,7 +422,7 @@ def bench_field(ea, torch, peak_tops, sweeps=200, h=(1, 2)):
     ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
     best = None
     for i, p in enumerate(ens.plans()):
-        if p["form"] == "unit-fast":
+        if p["form"] in ("unit-fast", "unit-wave"):     # the field runs the generic forms
             continue
         ens.select_plan(i)
         v, _ = timed(ens)
@@ -789,7 +789,7 @@ def main():
             line["tpack"] = bench_tpack(ea, torch, peak_tops)
             line["batched"] = bench_batched(ea, torch)
             line["served"] = bench_served(ea, args.served_requests)
-            line["served_load70"] = bench_served(ea, 16, load=0.7,
+            line["served_load70"] = bench_served(ea, 128, load=0.7,
                                                  rate_flips_s=1e12 / line["served"]["value"])
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(wl)

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <mutex>
 #include <vector>
 
 #include "../../include/ea.h"
@@ -207,7 +208,6 @@ struct ea_batch {
     bool have_graph;
     ea::BatchShape g_shape, last_shape;
     int g_grid;
-    size_t g_smem_set[2];                       // dynamic smem granted to the 384 / 512 kernels
     bool joins_dirty;
     cudaEvent_t done;
     bool pending;
@@ -272,6 +272,21 @@ std::vector<int> resolve(const ea_batch *b)
     for (size_t i = 0; i < r.size(); ++i)
         if (r[i] >= 0 && b->cands[i][(size_t)r[i]].threads > ea::kBatchSmallThreads) return r;
     return pick(ea::kBatchSmallThreads);
+}
+
+// Dynamic shared memory granted to the 384- and 512-thread batch kernels.
+// The attribute belongs to the kernel, not to a batch object, so every batch
+// of the process raises it through this one record and never lowers it.
+std::mutex g_smem_mu;
+size_t g_smem_granted[2] = {0, 0};
+
+cudaError_t grant_batch_smem(const void *kern, int which, size_t smem)
+{
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    if (g_smem_granted[which] >= smem) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) g_smem_granted[which] = smem;
+    return e;
 }
 
 int wait_pending(ea_batch *b)
@@ -549,11 +564,8 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
                 return cuda_err(e);
             b->joins_dirty = false;
         }
-        if (b->g_smem_set[threads == kBatchSmallThreads ? 0 : 1] < smem) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return cuda_err(e);
-            b->g_smem_set[threads == kBatchSmallThreads ? 0 : 1] = smem;
-        }
+        e = grant_batch_smem(kern, threads == kBatchSmallThreads ? 0 : 1, smem);
+        if (e != cudaSuccess) return cuda_err(e);
         int per_sm = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);

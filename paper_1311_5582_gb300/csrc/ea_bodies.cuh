@@ -86,10 +86,13 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
 
     uint64_t P = a.P0;
     uint32_t pass_local = a.pass_local0;
+    SwapCountdown swap_cd(a.s0, a.swap_every);
+    MeasureCountdown meas_cd(a.s0, a.measure_from, MEAS ? a.measure_every : 0u);
     for (uint32_t n = 0; n < a.n_sweeps; ++n) {
         const uint64_t s = a.s0 + n;
-        const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
-        const bool meas = MEAS && measured(s, a.measure_from, a.measure_every);
+        const bool swap_s = swap_cd.step();             // a pass follows sweep s
+        const bool swap_now = swap_s && NT > 1;
+        const bool meas = MEAS && meas_cd.step();
         const bool needE = swap_now || energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
         uint32_t acc[kPlanes], accM[kPlanes];
 #pragma unroll
@@ -214,7 +217,7 @@ __device__ __forceinline__ void unit_body(uint32_t *base, const SweepLaunch &a, 
                 }
             __syncthreads();
         }
-        if (swap_after(s, a.swap_every)) {
+        if (swap_s) {
             ++P;
             ++pass_local;
         }

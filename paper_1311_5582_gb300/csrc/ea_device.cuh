@@ -439,6 +439,40 @@ __device__ __forceinline__ bool measured(uint64_t s, uint64_t from, uint32_t eve
     return every != 0 && s >= from && ((s - from) % every) == 0;
 }
 
+// The same schedules without a 64-bit division per sweep: the number of
+// sweeps until the next selected one is formed once (one division) and
+// counted down.  step() tells whether the current sweep is selected and
+// moves on to the next.
+struct SwapCountdown {          // sweeps s with (s + 1) % every == 0
+    uint32_t every, left;
+    __device__ SwapCountdown(uint64_t s0, uint32_t every_) : every(every_), left(0)
+    {
+        if (every) left = every - 1u - (uint32_t)(s0 % every);
+    }
+    __device__ __forceinline__ bool step()
+    {
+        if (every == 0) return false;
+        const bool now = left == 0;
+        left = now ? every - 1u : left - 1u;
+        return now;
+    }
+};
+struct MeasureCountdown {       // sweeps s >= from with (s - from) % every == 0
+    uint32_t every;
+    uint64_t left;
+    __device__ MeasureCountdown(uint64_t s0, uint64_t from, uint32_t every_) : every(every_), left(0)
+    {
+        if (every) left = s0 >= from ? (uint64_t)((every - (uint32_t)((s0 - from) % every)) % every) : from - s0;
+    }
+    __device__ __forceinline__ bool step()
+    {
+        if (every == 0) return false;
+        const bool now = left == 0;
+        left = now ? (uint64_t)(every - 1u) : left - 1u;
+        return now;
+    }
+};
+
 // Number of leading entries of a non-increasing threshold row above r: the
 // swap of pair p is accepted iff E_p - E_{p+1} >= -4 * K (Sec. 2.4 with the
 // integer table of Sec. 4.3.2).

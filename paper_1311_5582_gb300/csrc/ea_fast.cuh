@@ -178,19 +178,28 @@ __device__ __forceinline__ uint4 quad_core(uint4 own, uint4 xo, uint4 vyp, uint4
         const uint32_t e3 = sj ^ my[j] ^ jym[j];
         const uint32_t e4 = sj ^ nz[j] ^ jz[j];
         const uint32_t e5 = sj ^ mz[j] ^ jzm[j];
-        uint32_t a0, a1, b0, b1, u0, u1, u2;
-        full_add(e0, e1, e2, a0, a1);
+        uint32_t a0, a1, b0, b1;
+        full_add(e0, e1, e2, a0, a1);                   // u = (a0 + 2 a1) + (b0 + 2 b1)
         full_add(e3, e4, e5, b0, b1);
-        u0 = a0 ^ b0;
-        full_add(a1, b1, a0 & b0, u1, u2);
         const uint32_t m0 = below_mask(rr[j], t0), m1 = below_mask(rr[j], t1), m2 = below_mask(rr[j], t2);
-        const uint32_t fp = flip_mask_part(u0, u1, u2, m1, m2);
-        ns[j] = sj ^ (fp | m0);                          // one LOP3
         if constexpr (WITH_E) {
-            const uint32_t f = fp | m0;
+            // the energy counters need u itself: u0, u1, u2, then the mask
+            const uint32_t u0 = a0 ^ b0;
+            uint32_t u1, u2;
+            full_add(a1, b1, a0 & b0, u1, u2);
+            const uint32_t f = flip_mask_part(u0, u1, u2, m1, m2) | m0;
+            ns[j] = sj ^ f;
             x0[j] = u0;
             x1[j] = u1 ^ (f & ~u0);
             x2[j] = u2 ^ (f & ~(u0 & u1));
+        } else {
+            // the mask straight from the two partial sums (m0 => m1 => m2):
+            //   [u>=3] | m2 [u>=2] | m1 [u>=1] | m0
+            //     = maj(a1, b1, a0 | b0 | m2) | (m2 & maj(a0, b0, m1)) | m0,
+            // four LOP3s and the flip folded into the last
+            const uint32_t v = a0 | b0 | m2;
+            const uint32_t t = maj3(a1, b1, v) | (m2 & maj3(a0, b0, m1));
+            ns[j] = sj ^ (t | m0);
         }
     }
     if constexpr (WITH_E) {
@@ -487,10 +496,13 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
     if (NT > 1 && a.swap_every != 0) bounds(P, (P & 1) ? bnd1 : bnd0, tid, nthr);
     __syncthreads();
 
+    SwapCountdown swap_cd(a.s0, a.swap_every);
+    MeasureCountdown meas_cd(a.s0, a.measure_from, MEAS ? a.measure_every : 0u);
     for (uint32_t n = 0; n < a.n_sweeps; ++n) {
         const uint64_t s = a.s0 + n;
-        const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
-        const bool meas = MEAS && measured(s, a.measure_from, a.measure_every);
+        const bool swap_s = swap_cd.step();             // a pass follows sweep s
+        const bool swap_now = swap_s && NT > 1;
+        const bool meas = MEAS && meas_cd.step();
         const bool needE = swap_now || energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
         uint32_t acc[PL];
 #pragma unroll
@@ -642,7 +654,7 @@ __device__ __forceinline__ void unit_fast_body(uint32_t *const base, const Sweep
                     swap_log[(((size_t)pass_local * a.G + g) * a.C + c) * (NT - 1) + p] = msk[p];
             __syncthreads();
         }
-        if (swap_after(s, a.swap_every)) {
+        if (swap_s) {
             ++P;
             ++pass_local;
         }

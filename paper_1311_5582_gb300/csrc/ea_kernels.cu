@@ -527,7 +527,6 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
     (void)C;
     std::vector<Plan> out;
     if (NT < 1 || NT > kMaxTemps || !supported_L(L)) return out;
-    const int N = L * L * L;
     // wavefront unit form (L = 8): best first; field-free only
     if (!field && wave_unit_threads(L, NT) != 0) {
         const bool sw_smem = wave_unit_smem(L, NT, swap_len, true) <= smem_optin;

@@ -299,9 +299,11 @@ k_tp_sweep(TpLaunch a, int recompute_only)
     uint64_t P = a.P0;
     uint32_t pass_local = a.pass_local0;
     const uint32_t tag0 = (c << 8), tag1 = (1u << 16) | (c << 8);
+    SwapCountdown swap_cd(a.s0, a.swap_every);
     for (uint32_t n = 0; n < a.n_sweeps; ++n) {
         const uint64_t s = a.s0 + n;
-        const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
+        const bool swap_s = swap_cd.step();             // a pass follows sweep s
+        const bool swap_now = swap_s && NT > 1;
         const bool needE = swap_now || a.energy_log != nullptr || (n + 1 == a.n_sweeps);
         if (needE && tid < kTpMaxTemps) E[tid] = -3 * N;
         tp_half<L, 0>(S, J, nthr, 0, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, rr, tag0, a.rk, acc);
@@ -353,7 +355,7 @@ k_tp_sweep(TpLaunch a, int recompute_only)
             }
             __syncthreads();
         }
-        if (swap_after(s, a.swap_every)) {
+        if (swap_s) {
             ++P;
             ++pass_local;
         }

@@ -388,9 +388,11 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     bool ok_run = true;
     uint32_t ph_e = 0, ph_h = 0;                        // parity of the next phase this warp waits for
 
+    SwapCountdown swap_cd(a.s0, a.swap_every);
     for (uint32_t n = 0; n < a.n_sweeps && ok_run; ++n) {
         const uint64_t s = a.s0 + n;
-        const bool swap_now = swap_after(s, a.swap_every) && NT > 1;
+        const bool swap_s = swap_cd.step();             // a pass follows sweep s
+        const bool swap_now = swap_s && NT > 1;
         const bool needE = swap_now || energy_log != nullptr || (n + 1 == a.n_sweeps);
         uint32_t acc[PL];
 #pragma unroll
@@ -473,7 +475,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
             ++P;
             ++pass_local;
             if (hasB) wave_bounds(rowa, rowb, len, sa, sb, k, c, P, gr, a.rk, lane, bA, bB);
-        } else if (swap_after(s, a.swap_every)) {
+        } else if (swap_s) {
             ++P;                                        // NT == 1: passes count, nothing to exchange
             ++pass_local;
         }
