@@ -417,12 +417,14 @@ def bench_field(ea, torch, peak_tops, sweeps=200, h=(1, 2)):
            "roofline_frac": achieved / peak_tops, "achieved_tops": achieved,
            "alg_ops_basis": f"{ALG_OPS_PER_SITE_WORD} per site-word (field-free count)",
            "plan": plan_text(ens), "gpu_launches": launches}
+    ens_form = ens.plans()[ens.plan]["form"]
     ens.close()
+    field_form = ens_form
     metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
     ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
     best = None
     for i, p in enumerate(ens.plans()):
-        if p["form"] in ("unit-fast", "unit-wave"):     # the field runs the generic forms
+        if p["form"] != field_form:                     # the same kernel form at h = 0
             continue
         ens.select_plan(i)
         v, _ = timed(ens)

@@ -271,6 +271,23 @@ int validate_field(const ea_field *f, uint32_t NT, uint32_t *metro0)
     return EA_OK;
 }
 
+// The wavefront kernel's kind for a field table (ea_field::metro, validated):
+// the first u at which every slot's thresholds reach 2^32 ("always"), per spin
+// value, must be 3 for one value and 4 for the other; 0 otherwise.
+int field_wave_kind(const ea_field *f, uint32_t NT)
+{
+    int ua[2] = {-1, -1};
+    for (uint32_t t = 0; t < NT; ++t)
+        for (int sp = 0; sp < 2; ++sp) {
+            const uint64_t *row = f->metro + ((size_t)t * 2 + sp) * 7;
+            int first = 7;
+            for (int u = 6; u >= 0 && row[u] == (1ull << 32); --u) first = u;
+            if (ua[sp] >= 0 && ua[sp] != first) return 0;
+            ua[sp] = first;
+        }
+    return wave_field_kind(ua[0], ua[1]);
+}
+
 int create_ctx(const ea_config *cfg_in, cudaStream_t stream, cudaMemPool_t pool, ea_ctx **out,
                const ea_field *field)
 {
@@ -325,7 +342,8 @@ int create_ctx(const ea_config *cfg_in, cudaStream_t stream, cudaMemPool_t pool,
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
     if (e != cudaSuccess) { delete c; return cuda_fail(e); }
     c->smem_optin = (size_t)optin;
-    c->plans = ea::make_plans((int)L, (int)c->NT, (int)c->C, c->swap_len, c->smem_optin, field != nullptr);
+    c->plans = ea::make_plans((int)L, (int)c->NT, (int)c->C, c->swap_len, c->smem_optin, field != nullptr,
+                              field ? field_wave_kind(field, c->NT) : 0);
     if (c->plans.empty()) {
         delete c;
         return EA_EUNSUPPORTED;
@@ -430,12 +448,12 @@ int run_sweeps(ea_ctx *c, const ea_sweep_args *args, const ea::Plan &plan)
         if (plan.form == ea::kFormUnitWave) {
             const bool meas = args->measure_every != 0 && (args->qhist != nullptr || args->esum != nullptr);
             if (!meas) {
-                EA_TRY(ea::launch_sweep_unit_wave(a, plan.swap_in_smem, st, &c->launches));
+                EA_TRY(ea::launch_sweep_unit_wave(a, plan.swap_in_smem, plan.field_kind, st, &c->launches));
                 return EA_OK;
             }
-            // measured calls run under the first specialised plan (same results)
+            // measured calls run under the first other unit plan (same results)
             for (const ea::Plan &q : c->plans)
-                if (q.form == ea::kFormUnitFast) return run_sweeps(c, args, q);
+                if (q.unit && q.form != ea::kFormUnitWave) return run_sweeps(c, args, q);
             return EA_EUNSUPPORTED;
         }
         if (plan.form == ea::kFormUnitFast)

@@ -211,7 +211,7 @@ k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tas
         else run_chunk(I.L, I.j_smem, base, s_a, t.unit, (int)t.chunk, I.p1, I.p2);
         __syncthreads();
         if (I.form == kBWave) {
-            wave_release(base, (int)I.a.NT);
+            wave_release(base, (int)I.a.NT, false);
             __syncthreads();
         }
         if (I.form != kBChunk) {

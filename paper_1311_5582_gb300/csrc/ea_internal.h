@@ -75,22 +75,29 @@ struct Plan {
     size_t smem;
     bool j_in_smem;
     bool swap_in_smem;      // unit forms: swap threshold table staged in shared memory
+    int field_kind = 0;     // wavefront form in a field: 34 or 43 (wave_field_kind), else 0
 };
 
 bool supported_L(int L);
 // Every kernel plan that can run (L, NT) within the device's opt-in shared
 // memory, best guess first.  Empty if none.
 // field: plans for the external-field kernels (generic unit and chunked forms).
+// field_kind: the wavefront kernel's field kind for this field (0: the field
+// runs the generic forms only).
 std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin,
-                             bool field = false);
+                             bool field = false, int field_kind = 0);
 
 int fast_unit_threads(int L, int HP, int NT);
 // Unit kernel with the wavefront replica exchange (L = 8, NT <= kWaveMaxTemps,
 // one warp per two slots; launches without qhist / esum measurement).
+// In an external field the kernel takes the fields whose always-accept
+// boundaries are u >= 3 for one spin value and u >= 4 for the other
+// (wave_field_kind: 34 or 43; 0 for any other pair).
 constexpr int kWaveMaxTemps = 32;
 int wave_unit_threads(int L, int NT);
-size_t wave_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem);
-cudaError_t launch_sweep_unit_wave(const SweepLaunch &a, bool swap_in_smem, cudaStream_t st,
+size_t wave_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem, bool field = false);
+int wave_field_kind(int ua0, int ua1);
+cudaError_t launch_sweep_unit_wave(const SweepLaunch &a, bool swap_in_smem, int field_kind, cudaStream_t st,
                                    uint64_t *launches);
 // Dynamic shared memory of the specialised unit kernel (with or without the
 // swap table, the measurement snapshots and the shared-memory histogram).

@@ -522,15 +522,16 @@ static bool chunk_plan(int L, int NT, size_t smem_optin, int tpl_pref, int nlat_
     return true;
 }
 
-std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin, bool field)
+std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t smem_optin, bool field,
+                             int field_kind)
 {
     (void)C;
     std::vector<Plan> out;
     if (NT < 1 || NT > kMaxTemps || !supported_L(L)) return out;
-    // wavefront unit form (L = 8): best first; field-free only
-    if (!field && wave_unit_threads(L, NT) != 0) {
-        const bool sw_smem = wave_unit_smem(L, NT, swap_len, true) <= smem_optin;
-        const size_t smem = wave_unit_smem(L, NT, swap_len, sw_smem);
+    // wavefront unit form (L = 8): best first; field-free, or the fields it takes
+    if ((!field || field_kind != 0) && wave_unit_threads(L, NT) != 0) {
+        const bool sw_smem = wave_unit_smem(L, NT, swap_len, true, field) <= smem_optin;
+        const size_t smem = wave_unit_smem(L, NT, swap_len, sw_smem, field);
         if (smem <= smem_optin) {
             Plan p;
             p.form = kFormUnitWave;
@@ -541,6 +542,7 @@ std::vector<Plan> make_plans(int L, int NT, int C, uint32_t swap_len, size_t sme
             p.smem = smem;
             p.j_in_smem = true;
             p.swap_in_smem = sw_smem;
+            p.field_kind = field ? field_kind : 0;
             out.push_back(p);
         }
     }

@@ -36,14 +36,14 @@ constexpr int kWaveWaitLimit = 1 << 22;    // suspending polls of one wait (seco
 // Shared-memory layout of the wavefront kernel, in 32-bit words.
 struct WaveLayout {
     size_t s, js, eo, cur, bar_e, bar_h, abort, tsw, words;
-    __host__ __device__ WaveLayout(int N, int NT, uint32_t swap_len, bool swap_smem)
+    __host__ __device__ WaveLayout(int N, int NT, uint32_t swap_len, bool swap_smem, bool field = false)
     {
-        const int nw = (NT + 1) / 2;
+        const int nw = (NT + 1) / 2, rec = field ? 3 : 1;   // Et (and E, M in a field)
         size_t o = 0;
         s = o; o += (size_t)NT * N;               // [NT][2][H] spins by slot
         js = o; o += (size_t)3 * N;               // [3][2][H] bonds
-        eo = o; o += (size_t)NT * kLanes;         // energy of slot 2k after the sweep, for warp k-1
-        cur = o; o += (size_t)nw * kLanes;        // carried energy from warp k to warp k+1
+        eo = o; o += (size_t)rec * NT * kLanes;   // slot 2k after the sweep, for warp k-1
+        cur = o; o += (size_t)rec * nw * kLanes;  // the carried configuration, warp k to warp k+1
         o = (o + 1) & ~(size_t)1;                 // 8-byte alignment of the barriers
         bar_e = o; o += 2 * (size_t)nw;           // mbarrier k: E_{2k+2} of warp k+1 is published
         bar_h = o; o += 2 * (size_t)nw;           // mbarrier k: warp k applied its pass steps
@@ -87,9 +87,9 @@ __device__ __forceinline__ void mbar_inval(uint64_t *bar)
 
 // Invalidates the hand-off barriers of a finished unit (after a CTA barrier)
 // before the shared memory is used for anything else.
-__device__ __forceinline__ void wave_release(uint32_t *base, int NT)
+__device__ __forceinline__ void wave_release(uint32_t *base, int NT, bool field)
 {
-    const WaveLayout lay(8 * 8 * 8, NT, 0, false);
+    const WaveLayout lay(8 * 8 * 8, NT, 0, false, field);
     uint64_t *bar_e = reinterpret_cast<uint64_t *>(base + lay.bar_e);
     uint64_t *bar_h = reinterpret_cast<uint64_t *>(base + lay.bar_h);
     for (int i = threadIdx.x; i < (NT + 1) / 2; i += blockDim.x) {
@@ -228,6 +228,136 @@ __device__ __forceinline__ void wave_half(const WaveQuad (&wq)[4], uint32_t s, u
     wave_quad<COL, 1 - COL, WITH_E, PL>(wq[3], r1, t0, t1, t2, acc, dep);
 }
 
+// External field h = h_num / h_den (Eq. 1 with the field term; the field runs
+// of Sec. 5), for fields whose always-accept boundary is u >= UA0 for spin
+// value S = -1 and u >= UA1 for S = +1 with {UA0, UA1} = {3, 4} (0 < |h| < 2).
+// A spin flips iff r < T[S][u]; below the boundary the thresholds are
+// non-decreasing in u, so the masks m[k] = [r < T[k]] are nested and the
+// flip mask of one spin value follows from the partial sums (a, b) of the
+// six unsatisfied-bond bits in a few LOP3s:
+//   UA = 3: [u>=3] | m2 [u>=2] | m1 [u>=1] | m0
+//         = maj(a1, b1, a0 | b0 | m2) | (m2 & maj(a0, b0, m1)) | m0
+//   UA = 4: [u>=4] | m3 [u>=3] | m2 [u>=2] | m1 [u>=1] | m0
+//         = maj(a1, b1, maj(a0, b0, m3)) | (m2 & (a1 | b1 | maj(a0, b0, m1))) | m0
+template <int UA>
+__device__ __forceinline__ uint32_t field_mask(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1,
+                                               const uint32_t (&m)[UA])
+{
+    if constexpr (UA == 3) {
+        const uint32_t v = a0 | b0 | m[2];
+        return maj3(a1, b1, v) | (m[2] & maj3(a0, b0, m[1])) | m[0];
+    } else {
+        static_assert(UA == 4, "always-accept boundary 3 or 4");
+        const uint32_t z = maj3(a0, b0, m[3]);
+        return maj3(a1, b1, z) | (m[2] & (a1 | b1 | maj3(a0, b0, m[1]))) | m[0];
+    }
+}
+
+// acc += number of set bits per lane among four words (both counters bit-sliced).
+template <int PL>
+__device__ __forceinline__ void acc_add_count4(uint32_t (&acc)[PL], uint32_t w0, uint32_t w1, uint32_t w2,
+                                               uint32_t w3)
+{
+    uint32_t s1, c1;
+    full_add(w0, w1, w2, s1, c1);
+    uint32_t A[5] = {s1 ^ w3, c1 ^ (s1 & w3), c1 & (s1 & w3), 0u, 0u};
+    acc_add_sum5<PL>(acc, A);
+}
+
+// Metropolis update of one quad in the field (L = 8): the flip mask per spin
+// value from field_mask, selected per lane by the spin bit; WITH_E adds the
+// post-update unsatisfied-bond counts to acc, WITH_M the up spins to accM.
+template <int COL, int PX, bool WITH_E, bool WITH_M, int UA0, int UA1, int PL, int PLM>
+__device__ __forceinline__ void wave_quad_field(const WaveQuad &q, uint4 r, const uint64_t (&n0)[UA0],
+                                                const uint64_t (&n1)[UA1], uint32_t (&acc)[PL],
+                                                uint32_t (&accM)[PLM], uint32_t dep)
+{
+    constexpr int H4 = 256 * 4, N4 = 512 * 4;
+    constexpr int C4 = COL * H4, O4 = (1 - COL) * H4;
+    const uint4 own = lds4<C4>(q.s, dep), xo = lds4<O4>(q.s, dep);
+    const uint4 vyp = lds4<O4>(q.yp, dep), vym = lds4<O4>(q.ym, dep);
+    const uint4 vzp = lds4<O4>(q.zp, dep), vzm = lds4<O4>(q.zm, dep);
+    const uint4 jcx = lds4<C4>(q.j, dep), jcy = lds4<N4 + C4>(q.j, dep), jcz = lds4<2 * N4 + C4>(q.j, dep);
+    const uint4 jox = lds4<O4>(q.j, dep), joy = lds4<N4 + O4>(q.jym, dep), joz = lds4<2 * N4 + O4>(q.jzm, dep);
+    const uint32_t xe_s = PX ? xo.x : xo.w;
+    uint32_t nxp[4], nxm[4], jxm[4];
+    if constexpr (PX == 0) {
+        nxp[0] = xo.x; nxp[1] = xo.y; nxp[2] = xo.z; nxp[3] = xo.w;
+        nxm[0] = xe_s; nxm[1] = xo.x; nxm[2] = xo.y; nxm[3] = xo.z;
+        jxm[0] = jox.w; jxm[1] = jox.x; jxm[2] = jox.y; jxm[3] = jox.z;
+    } else {
+        nxp[0] = xo.y; nxp[1] = xo.z; nxp[2] = xo.w; nxp[3] = xe_s;
+        nxm[0] = xo.x; nxm[1] = xo.y; nxm[2] = xo.z; nxm[3] = xo.w;
+        jxm[0] = jox.x; jxm[1] = jox.y; jxm[2] = jox.z; jxm[3] = jox.w;
+    }
+    const uint32_t sv[4] = {own.x, own.y, own.z, own.w};
+    const uint32_t jx[4] = {jcx.x, jcx.y, jcx.z, jcx.w};
+    const uint32_t ny[4] = {vyp.x, vyp.y, vyp.z, vyp.w}, my[4] = {vym.x, vym.y, vym.z, vym.w};
+    const uint32_t nz[4] = {vzp.x, vzp.y, vzp.z, vzp.w}, mz[4] = {vzm.x, vzm.y, vzm.z, vzm.w};
+    const uint32_t jy[4] = {jcy.x, jcy.y, jcy.z, jcy.w}, jym[4] = {joy.x, joy.y, joy.z, joy.w};
+    const uint32_t jz[4] = {jcz.x, jcz.y, jcz.z, jcz.w}, jzm[4] = {joz.x, joz.y, joz.z, joz.w};
+    const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+    uint32_t ns[4], x0[4], x1[4], x2[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t sj = sv[j];
+        const uint32_t e0 = sj ^ nxp[j] ^ jx[j];
+        const uint32_t e1 = sj ^ nxm[j] ^ jxm[j];
+        const uint32_t e2 = sj ^ ny[j] ^ jy[j];
+        const uint32_t e3 = sj ^ my[j] ^ jym[j];
+        const uint32_t e4 = sj ^ nz[j] ^ jz[j];
+        const uint32_t e5 = sj ^ mz[j] ^ jzm[j];
+        uint32_t a0, a1, b0, b1;
+        full_add(e0, e1, e2, a0, a1);
+        full_add(e3, e4, e5, b0, b1);
+        uint32_t m0[UA0], m1[UA1];
+#pragma unroll
+        for (int u = 0; u < UA0; ++u) m0[u] = below_mask(rr[j], n0[u]);
+#pragma unroll
+        for (int u = 0; u < UA1; ++u) m1[u] = below_mask(rr[j], n1[u]);
+        const uint32_t F0 = field_mask<UA0>(a0, a1, b0, b1, m0), F1 = field_mask<UA1>(a0, a1, b0, b1, m1);
+        ns[j] = (sj & ~F1) | (~sj & F0);                // s ^ f with f = S > 0 ? F1 : F0
+        if constexpr (WITH_E) {
+            const uint32_t f = sj ^ ns[j];
+            const uint32_t u0 = a0 ^ b0;
+            uint32_t u1, u2;
+            full_add(a1, b1, a0 & b0, u1, u2);
+            x0[j] = u0;
+            x1[j] = u1 ^ (f & ~u0);
+            x2[j] = u2 ^ (f & ~(u0 & u1));
+        }
+    }
+    sts4<C4>(q.s, make_uint4(ns[0], ns[1], ns[2], ns[3]));
+    if constexpr (WITH_E) {
+        uint32_t A[5];
+        quad_sum(x0, x1, x2, A);
+        acc_add_sum5<PL>(acc, A);
+    }
+    if constexpr (WITH_M) acc_add_count4<PLM>(accM, ns[0], ns[1], ns[2], ns[3]);
+}
+
+template <int COL, bool WITH_E, bool WITH_M, int UA0, int UA1, int PL, int PLM>
+__device__ __forceinline__ void wave_half_field(const WaveQuad (&wq)[4], uint32_t s, uint32_t ctag,
+                                                const RoundKeys &rk, const uint64_t (&n0)[UA0],
+                                                const uint64_t (&n1)[UA1], uint32_t (&acc)[PL],
+                                                uint32_t (&accM)[PLM])
+{
+    const uint32_t dep = opaque_zero();
+    const uint32_t lo1 = kM1 * s, n0r = __umulhi(kM1, s) ^ ctag ^ rk.k[0];
+    const uint32_t lo0b = kM0 * n0r, hi0b = __umulhi(kM0, n0r);
+    auto draw = [&](const WaveQuad &q) {
+        return philox_from2(q.phi1 ^ lo1 ^ rk.k[2], q.plo1, hi0b ^ q.plo0 ^ rk.k[3], lo0b, rk);
+    };
+    uint4 r0 = draw(wq[0]);
+    uint4 r1 = draw(wq[1]);
+    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[0], r0, n0, n1, acc, accM, dep);
+    r0 = draw(wq[2]);
+    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[1], r1, n0, n1, acc, accM, dep);
+    r1 = draw(wq[3]);
+    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[2], r0, n0, n1, acc, accM, dep);
+    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[3], r1, n0, n1, acc, accM, dep);
+}
+
 // Unsatisfied-bond totals of the warp's two slots: each half-warp sums its
 // lanes' bit-sliced counters with a butterfly of shuffles and bit-sliced
 // adders, lane t of each half then holds plane t, and one 32x32 bit transpose
@@ -286,12 +416,13 @@ __device__ __forceinline__ float count_slope(const uint32_t *row, uint32_t len)
 
 // Acceptance bounds of the warp's pairs 2k and 2k+1 in pass P for the
 // realization of this lane (Sec. 2.4 with the integer table of Sec. 4.3.2):
-// pair p is accepted iff E_p - E_{p+1} >= bound.  Lanes 0-7 draw the Philox
+// pair p is accepted iff E_p - E_{p+1} >= bound (in a field: Et_p - Et_{p+1},
+// the table in units of `step`; without one step = 4).  Lanes 0-7 draw the Philox
 // blocks of pair 2k (realizations 4q..4q+3 from lane q), lanes 8-15 those of
 // pair 2k+1; each lane then counts both rows for its own uniforms.
 __device__ __forceinline__ void wave_bounds(const uint32_t *rowa, const uint32_t *rowb, uint32_t len, float sa,
                                             float sb, int k, int c, uint64_t P, uint32_t gr,
-                                            const RoundKeys &rk, int lane, int &bA, int &bB)
+                                            const RoundKeys &rk, int lane, int step, int &bA, int &bB)
 {
     const int pq = (lane >> 3) & 1, bq = lane & 7;
     const int p = 2 * k + pq;
@@ -309,32 +440,39 @@ __device__ __forceinline__ void wave_bounds(const uint32_t *rowa, const uint32_t
         const uint32_t z = __shfl_sync(kFull, v.z, src + 8), q = __shfl_sync(kFull, v.w, src + 8);
         rb = w == 0 ? x : w == 1 ? y : w == 2 ? z : q;
     }
-    bA = -4 * (int)count_above(rowa, len, ra, sa);
-    bB = -4 * (int)count_above(rowb, len, rb, sb);
+    bA = -step * (int)count_above(rowa, len, ra, sa);
+    bB = -step * (int)count_above(rowb, len, rb, sb);
 }
 
 // LOG = false compiles the body without the energy and swap logs (their
-// pointers must then be null).  Launches that measure (qhist / esum) use
-// another kernel.
-template <bool LOG>
+// pointers must then be null).  FLD = 0 runs the field-free method; FLD = 34
+// (43) the external field with always-accept boundaries u >= 3 (4) for S = -1
+// and u >= 4 (3) for S = +1: decisions of the pass on Et = h_den E - h_num M,
+// magnetisations M counted beside the energies.  Launches that measure (qhist
+// / esum) use another kernel.
+template <bool LOG, int FLD = 0>
 __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const SweepLaunch &a, uint32_t unit,
                                                int swap_in_smem)
 {
     constexpr int L = 8;
     using Gm = Geo<L>;
     constexpr int N = Gm::N;
+    constexpr bool F = FLD != 0;
+    constexpr int UA0 = FLD == 43 ? 4 : 3, UA1 = FLD == 34 ? 4 : 3;
     constexpr int PL = planes_for(24 * 4);          // counter planes of four quads (<= 96)
+    constexpr int PLM = planes_for(32);             // up spins of eight quads (<= 32)
     int32_t *const energy_log = LOG ? a.energy_log : nullptr;
     uint32_t *const swap_log = LOG ? a.swap_log : nullptr;
     const int NT = (int)a.NT;
-    const WaveLayout lay(N, NT, a.swap_len, swap_in_smem != 0);
+    const WaveLayout lay(N, NT, a.swap_len, swap_in_smem != 0, F);
     uint32_t *S = base + lay.s;
     uint32_t *Js = base + lay.js;
-    int *Eo = reinterpret_cast<int *>(base + lay.eo);
-    int *Cur = reinterpret_cast<int *>(base + lay.cur);
+    int *Eo = reinterpret_cast<int *>(base + lay.eo);          // [3][NT][32]: Et, E, M of slot 2k
+    int *Cur = reinterpret_cast<int *>(base + lay.cur);        // [3][nw][32]: the carry's Et, E, M
     uint64_t *bar_e = reinterpret_cast<uint64_t *>(base + lay.bar_e);
     uint64_t *bar_h = reinterpret_cast<uint64_t *>(base + lay.bar_h);
     volatile uint32_t *abort = base + lay.abort;
+    const int nw = (NT + 1) / 2;
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, k = tid >> 5;
     const int c = (int)(unit % a.C);
@@ -358,14 +496,24 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         for (int w = tid; w < (NT - 1) * (int)a.swap_len; w += nthr) Tsw[w] = a.swapt[w];
         swt = Tsw;
     }
-    for (int i = tid; i < (NT + 1) / 2; i += nthr) {
+    for (int i = tid; i < nw; i += nthr) {
         mbar_init(&bar_e[i], kLanes);
         mbar_init(&bar_h[i], kLanes);
     }
     if (tid == 0) *abort = 0u;
-    const uint64_t t0 = 0ull - (uint64_t)a.metro[ls * 3 + 0];
-    const uint64_t t1 = 0ull - (uint64_t)a.metro[ls * 3 + 1];
-    const uint64_t t2 = 0ull - (uint64_t)a.metro[ls * 3 + 2];
+    // Metropolis thresholds of my slot as 2^64 - T (see below_mask)
+    uint64_t t0 = 0, t1 = 0, t2 = 0;
+    uint64_t n0[UA0], n1[UA1];
+    if constexpr (F) {
+#pragma unroll
+        for (int u = 0; u < UA0; ++u) n0[u] = 0ull - a.metro_f[((size_t)ls * 2 + 0) * 7 + u];
+#pragma unroll
+        for (int u = 0; u < UA1; ++u) n1[u] = 0ull - a.metro_f[((size_t)ls * 2 + 1) * 7 + u];
+    } else {
+        t0 = 0ull - (uint64_t)a.metro[ls * 3 + 0];
+        t1 = 0ull - (uint64_t)a.metro[ls * 3 + 1];
+        t2 = 0ull - (uint64_t)a.metro[ls * 3 + 2];
+    }
     uint32_t *mine = S + (size_t)ls * N;
     WaveQuad wq[4];
 #pragma unroll
@@ -373,6 +521,8 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     const uint32_t tag0 = ((uint32_t)c << 8) | (uint32_t)ls;
     const uint32_t tag1 = (1u << 16) | tag0;
     const uint32_t len = a.swap_len;
+    const int step = F ? a.step : 4;
+    const int hn = a.h_num, hd = a.h_den;
     __syncthreads();   // staged lattices, bonds, table and flags are complete; no CTA barrier after this
     if (2 * k >= NT) return;                            // warps beyond the slots (wider CTAs of a batch)
     // rows of the warp's pairs 2k and 2k+1 (clamped into range; unused when the pair does not exist)
@@ -383,8 +533,10 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     uint64_t P = a.P0;
     uint32_t pass_local = a.pass_local0;
     int bA = 0, bB = 0;
-    if (NT > 1 && a.swap_every != 0 && hasB) wave_bounds(rowa, rowb, len, sa, sb, k, c, P, gr, a.rk, lane, bA, bB);
-    int EA = 0, EB = 0;                                 // energies of slots 2k, 2k+1 (lane = realization)
+    if (NT > 1 && a.swap_every != 0 && hasB)
+        wave_bounds(rowa, rowb, len, sa, sb, k, c, P, gr, a.rk, lane, step, bA, bB);
+    // energies (and in a field magnetisations) of slots 2k, 2k+1; lane = realization
+    int EA = 0, EB = 0, MA = 0, MB = 0;
     bool ok_run = true;
     uint32_t ph_e = 0, ph_h = 0;                        // parity of the next phase this warp waits for
 
@@ -394,38 +546,76 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         const bool swap_s = swap_cd.step();             // a pass follows sweep s
         const bool swap_now = swap_s && NT > 1;
         const bool needE = swap_now || energy_log != nullptr || (n + 1 == a.n_sweeps);
-        uint32_t acc[PL];
+        uint32_t acc[PL], accM[PLM];
 #pragma unroll
         for (int p = 0; p < PL; ++p) acc[p] = 0;
-        if (act) wave_half<0, false, PL>(wq, (uint32_t)s, tag0, a.rk, t0, t1, t2, acc);
-        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < PLM; ++p) accM[p] = 0;
+        if constexpr (F) {
+            if (needE) {
+                if (act) wave_half_field<0, false, true, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, accM);
+                __syncwarp();
+                if (act) wave_half_field<1, true, true, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, accM);
+            } else {
+                if (act) wave_half_field<0, false, false, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, accM);
+                __syncwarp();
+                if (act) wave_half_field<1, false, false, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, accM);
+            }
+        } else {
+            if (act) wave_half<0, false, PL>(wq, (uint32_t)s, tag0, a.rk, t0, t1, t2, acc);
+            __syncwarp();
+            if (needE) {
+                if (act) wave_half<1, true, PL>(wq, (uint32_t)s, tag1, a.rk, t0, t1, t2, acc);
+            } else if (act) {
+                wave_half<1, false, PL>(wq, (uint32_t)s, tag1, a.rk, t0, t1, t2, acc);
+            }
+        }
         if (needE) {
-            if (act) wave_half<1, true, PL>(wq, (uint32_t)s, tag1, a.rk, t0, t1, t2, acc);
             int UA, UB;
             wave_reduce<PL>(acc, lane, UA, UB);          // also orders the colour-1 stores (shuffles)
             EA = 2 * UA - 3 * N;
             EB = 2 * UB - 3 * N;
-        } else if (act) {
-            wave_half<1, false, PL>(wq, (uint32_t)s, tag1, a.rk, t0, t1, t2, acc);
+            if constexpr (F) {
+                int upA, upB;
+                wave_reduce<PLM>(accM, lane, upA, upB);
+                MA = 2 * upA - N;
+                MB = 2 * upB - N;
+            }
         }
         __syncwarp();
         if (swap_now) {
-            // publish E_{2k} (pre-exchange) for pair 2k-1 of warp k-1
-            Eo[2 * k * kLanes + lane] = EA;
+            // decisions on Et = h_den E - h_num M (E itself without a field)
+            const int etA = F ? hd * EA - hn * MA : EA, etB = F ? hd * EB - hn * MB : EB;
+            // publish slot 2k (pre-exchange) for pair 2k-1 of warp k-1
+            Eo[2 * k * kLanes + lane] = etA;
+            if constexpr (F) {
+                Eo[(NT + 2 * k) * kLanes + lane] = EA;
+                Eo[(2 * NT + 2 * k) * kLanes + lane] = MA;
+            }
             if (k > 0) mbar_arrive(&bar_e[k - 1]);
-            int cur = EA;
+            int cur = etA, curE = EA, curM = MA;        // the carried configuration
             if (k > 0) {
                 if (!wave_wait(&bar_h[k - 1], ph_h, abort, a.err)) { ok_run = false; break; }
                 ph_h ^= 1u;
                 cur = Cur[(k - 1) * kLanes + lane];
+                if constexpr (F) {
+                    curE = Cur[(nw + k - 1) * kLanes + lane];
+                    curM = Cur[(2 * nw + k - 1) * kLanes + lane];
+                }
             }
             uint32_t mA = 0, mB = 0;
             if (hasB) {
                 // pair 2k: slot 2k holds the carried configuration (energy cur)
-                const bool okA = cur - EB >= bA;
+                const bool okA = cur - etB >= bA;
                 mA = __ballot_sync(kFull, okA);
-                const int nEA = okA ? EB : cur;
-                cur = okA ? cur : EB;
+                const int nEA = okA ? EB : (F ? curE : cur), nMA = okA ? MB : curM;
+                if (!okA) {
+                    cur = etB;
+                    if constexpr (F) {
+                        curE = EB;
+                        curM = MB;
+                    }
+                }
                 uint4 *pa = reinterpret_cast<uint4 *>(S + (size_t)(2 * k) * N);
                 uint4 *pb = reinterpret_cast<uint4 *>(S + (size_t)(2 * k + 1) * N);
                 uint4 xb[N / 128];                      // slot 2k+1 after pair 2k (the carry)
@@ -436,15 +626,27 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
                                                    mux(x.w, y.w, mA));
                     xb[j] = make_uint4(mux(y.x, x.x, mA), mux(y.y, x.y, mA), mux(y.z, x.z, mA), mux(y.w, x.w, mA));
                 }
-                int nEB;
+                int nEB, nMB;
                 if (hasC) {
                     if (!wave_wait(&bar_e[k], ph_e, abort, a.err)) { ok_run = false; break; }
                     ph_e ^= 1u;
                     const int e2 = Eo[(2 * k + 2) * kLanes + lane];
+                    int e2E = e2, e2M = 0;
+                    if constexpr (F) {
+                        e2E = Eo[(NT + 2 * k + 2) * kLanes + lane];
+                        e2M = Eo[(2 * NT + 2 * k + 2) * kLanes + lane];
+                    }
                     const bool okB = cur - e2 >= bB;
                     mB = __ballot_sync(kFull, okB);
-                    nEB = okB ? e2 : cur;
-                    cur = okB ? cur : e2;
+                    nEB = okB ? e2E : (F ? curE : cur);
+                    nMB = okB ? e2M : curM;
+                    if (!okB) {
+                        cur = e2;
+                        if constexpr (F) {
+                            curE = e2E;
+                            curM = e2M;
+                        }
+                    }
                     uint4 *pc = reinterpret_cast<uint4 *>(S + (size_t)(2 * k + 2) * N);
 #pragma unroll
                     for (int j = 0; j < N / 128; ++j) {
@@ -455,16 +657,24 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
                                                        mux(y.w, x.w, mB));
                     }
                     Cur[k * kLanes + lane] = cur;
+                    if constexpr (F) {
+                        Cur[(nw + k) * kLanes + lane] = curE;
+                        Cur[(2 * nw + k) * kLanes + lane] = curM;
+                    }
                     mbar_arrive(&bar_h[k]);
                 } else {
 #pragma unroll
                     for (int j = 0; j < N / 128; ++j) pb[lane + 32 * j] = xb[j];
-                    nEB = cur;                          // slot 2k+1 is the last
+                    nEB = F ? curE : cur;               // slot 2k+1 is the last
+                    nMB = curM;
                 }
                 EA = nEA;
                 EB = nEB;
+                MA = nMA;
+                MB = nMB;
             } else {
-                EA = cur;                               // slot 2k is the last (odd NT)
+                EA = F ? curE : cur;                    // slot 2k is the last (odd NT)
+                MA = curM;
             }
             __syncwarp();
             if (swap_log != nullptr && lane == 0) {
@@ -474,7 +684,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
             }
             ++P;
             ++pass_local;
-            if (hasB) wave_bounds(rowa, rowb, len, sa, sb, k, c, P, gr, a.rk, lane, bA, bB);
+            if (hasB) wave_bounds(rowa, rowb, len, sa, sb, k, c, P, gr, a.rk, lane, step, bA, bB);
         } else if (swap_s) {
             ++P;                                        // NT == 1: passes count, nothing to exchange
             ++pass_local;
@@ -490,6 +700,11 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     int32_t *gE = a.energy + (size_t)unit * NT * kLanes;
     gE[(2 * k) * kLanes + lane] = EA;
     if (hasB) gE[(2 * k + 1) * kLanes + lane] = EB;
+    if constexpr (F) {
+        int32_t *gM = a.mag + (size_t)unit * NT * kLanes;
+        gM[(2 * k) * kLanes + lane] = MA;
+        if (hasB) gM[(2 * k + 1) * kLanes + lane] = MB;
+    }
     // this warp's slots are final (no later pass step touches them)
     const int nslot = hasB ? 2 : 1;
     for (int w = lane; w < nslot * N / 4; w += 32)

@@ -123,3 +123,21 @@ def test_batch_rejects_field_contexts():
     b = ea.Batch()
     with pytest.raises(ea.EAError):
         b.add(gpu)
+
+
+@pytest.mark.parametrize("NT,C,h_num,h_den,swap_every", [
+    (12, 2, 1, 2, 1), (7, 2, -1, 2, 1), (24, 2, 3, 2, 1), (5, 1, -5, 4, 3), (2, 2, 1, 3, 1), (31, 2, 19, 10, 2),
+])
+def test_field_wavefront_kernel_matches_oracle(NT, C, h_num, h_den, swap_every):
+    """L = 8 fields with always-accept boundaries u >= 3 / u >= 4 for the two spin
+    values (0 < |h| < 2) run the wavefront kernel by default: energies,
+    magnetisations, swap masks and spins equal to the oracle's, calls continued."""
+    inst = W.Instance(L=8, G=2, NT=NT, C=C, seed=700 + NT, tmin=0.8, tmax=2.0, input_seed=NT + 11)
+    gpu, sim = field_pair(inst, h_num, h_den)
+    assert gpu.plans()[gpu.plan]["form"] == "unit-wave"
+    tag = f"wave NT={NT} h={h_num}/{h_den}"
+    compare(gpu, sim, 9, swap_every, tag)
+    compare(gpu, sim, 7, swap_every, tag + " (continued)")
+    # a field outside that range keeps to the generic forms
+    other, _ = field_pair(W.Instance(L=8, G=1, NT=4, C=2, seed=1, tmin=0.8, tmax=2.0, input_seed=2), 2, 1)
+    assert all(p["form"] != "unit-wave" for p in other.plans())
