@@ -157,8 +157,11 @@ int ea_build_tables_field(const double *beta, uint32_t n_temps, uint32_t n_sites
                           uint32_t *swap_len_out);
 
 /* ea_create in the field `field` (NULL: none, as ea_create).  Contexts with a
- * field run the generic unit and chunked kernel forms; batches and the server
- * do not take them (EA_EINVAL). */
+ * field run the generic unit and chunked kernel forms, and at L = 8 the
+ * wavefront form when the field's always-accept boundaries are u >= 3 for one
+ * spin value and u >= 4 for the other (0 < |h| < 2 with the builder's tables).
+ * A batch takes members all in a field or all field-free (EA_EINVAL when
+ * mixed); its field members run in a field kernel of 384-thread CTAs. */
 int ea_create_field(const ea_config *cfg, const ea_field *field, void *stream, ea_ctx **out);
 
 /* Magnetisations M = sum_i S_i of every lattice by slot, recomputed from the
@@ -349,13 +352,22 @@ int ea_server_create(const ea_server_opts *opts, ea_server **out);   /* opts may
 typedef struct {
     uint32_t n_sweeps, swap_every;
     uint32_t *spins_out;       /* HOST [G][NT][C][N] final spins (slot order), or NULL */
-    int32_t *energies_out;     /* HOST [G][NT][C][32] final energies, or NULL */
+    int32_t *energies_out;     /* HOST [G][NT][C][32] final energies E (Eq. 1, bonds), or NULL */
+    int32_t *magnetisations_out;   /* HOST [G][NT][C][32] final M, or NULL; requests in a
+                                      field only (ea_submit_field with h_num != 0) */
 } ea_request;
 /* Copies cfg's host inputs and queues the request; *ticket identifies it.
  * The output buffers must stay valid until ea_poll reports it finished.
  * Shape errors return at once (EA_EINVAL / EA_EUNSUPPORTED); table errors
  * and a request larger than the whole budget (EA_ENOMEM) finish the ticket. */
 int ea_submit(ea_server *server, const ea_config *cfg, const ea_request *req, uint64_t *ticket);
+/* ea_submit in the external field `field` (as ea_create_field; cfg->metro may
+ * then be NULL).  Requests in a field advance in the server's field batches
+ * (one persistent launch per round for them, beside the field-free one); the
+ * field's tables are copied.  Each result is exactly what ea_create_field +
+ * ea_sweep would give alone. */
+int ea_submit_field(ea_server *server, const ea_config *cfg, const ea_field *field, const ea_request *req,
+                    uint64_t *ticket);
 /* Waits up to timeout_us for the ticket: EA_PENDING if unfinished; else the
  * request's status (EA_OK: outputs written), after which the ticket is
  * retired and polling it again is EA_EINVAL. */
@@ -470,7 +482,7 @@ int ea_tp_info(const ea_tp *tp, uint64_t *sweep_index, uint64_t *pass_index, uin
  * its own slots up to the next pass and a merge launch then combines the groups
  * and runs the pass.  Results do not depend on k.  ea_tp_create picks the
  * largest k <= 8 with R * C * k CTAs within one per SM (1 when R * C fills
- * the GPU).  May allocate device memory (k more copies of the spins, one a group);
+ * the GPU).  May allocate device memory (k more copies of the spins, one per group);
  * synchronises the stream when it frees some.  EA_EINVAL for another k. */
 int ea_tp_set_split(ea_tp *tp, uint32_t k);
 /* Synchronises the context's stream and frees its device memory. */

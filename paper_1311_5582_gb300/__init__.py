@@ -53,7 +53,8 @@ class _ServerOpts(ctypes.Structure):
 
 class _Request(ctypes.Structure):
     _fields_ = [("n_sweeps", ctypes.c_uint32), ("swap_every", ctypes.c_uint32),
-                ("spins_out", ctypes.c_void_p), ("energies_out", ctypes.c_void_p)]
+                ("spins_out", ctypes.c_void_p), ("energies_out", ctypes.c_void_p),
+                ("magnetisations_out", ctypes.c_void_p)]
 
 
 class _TpConfig(ctypes.Structure):
@@ -97,7 +98,8 @@ EXPORTS = ["ea_build_tables", "ea_build_tables_field", "ea_supported_L", "ea_cre
            "ea_batch_set_plan", "ea_batch_set_width", "ea_batch_set_wait_limit", "ea_batch_inject_stall",
            "ea_batch_set_segment", "ea_batch_sweep",
            "ea_batch_sweep_each", "ea_batch_sync", "ea_batch_autotune", "ea_batch_launch_count", "ea_batch_destroy",
-           "ea_server_create", "ea_submit", "ea_poll", "ea_server_stats_get", "ea_server_destroy",
+           "ea_server_create", "ea_submit", "ea_submit_field", "ea_poll", "ea_server_stats_get",
+           "ea_server_destroy",
            "ea_run",
            "ea_pt_swap_static", "ea_tp_create", "ea_tp_sweep", "ea_tp_read", "ea_tp_info",
            "ea_tp_set_split", "ea_tp_destroy", "ea_strerror"]
@@ -552,15 +554,28 @@ class Server:
         self._out = {}          # ticket -> (outputs dict, inputs kept alive)
 
     def submit(self, L, G, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every,
-               want_spins=True, want_energies=True, group_base=0) -> int:
+               want_spins=True, want_energies=True, group_base=0, field=None) -> int:
+        """field=(h_num, h_den, metro_field) submits the request in that external
+        field (ea_submit_field); its outputs then include "magnetisations"."""
         cfg, keep = _config(L, G, NT, C, seed, bonds, spins, metro, swapt, group_base)
         N = int(L) ** 3
+        in_field = field is not None and int(field[0]) != 0
         out = {"spins": np.zeros((G, NT, C, N), np.uint32) if want_spins else None,
-               "energies": np.zeros((G, NT, C, 32), np.int32) if want_energies else None}
-        req = _Request(int(n_sweeps), int(swap_every), _ptr(out["spins"]), _ptr(out["energies"]))
+               "energies": np.zeros((G, NT, C, 32), np.int32) if want_energies else None,
+               "magnetisations": np.zeros((G, NT, C, 32), np.int32) if in_field else None}
+        req = _Request(int(n_sweeps), int(swap_every), _ptr(out["spins"]), _ptr(out["energies"]),
+                       _ptr(out["magnetisations"]))
         t = ctypes.c_uint64(0)
-        _check(self.lib.ea_submit(self.s, ctypes.byref(cfg), ctypes.byref(req), ctypes.byref(t)),
-               "ea_submit")
+        if field is None:
+            _check(self.lib.ea_submit(self.s, ctypes.byref(cfg), ctypes.byref(req), ctypes.byref(t)),
+                   "ea_submit")
+        else:
+            h_num, h_den, mf = field
+            mf = np.ascontiguousarray(mf, np.uint64)
+            assert mf.shape == (NT, 2, 7)
+            fld = _Field(int(h_num), int(h_den), mf.ctypes.data)
+            _check(self.lib.ea_submit_field(self.s, ctypes.byref(cfg), ctypes.byref(fld), ctypes.byref(req),
+                                            ctypes.byref(t)), "ea_submit_field")
         self._out[t.value] = out
         return t.value
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libea.so")
-SOURCES = ["ea_kernels.cu", "ea_field.cu", "ea_unit_fast.cu", "ea_unit_wave.cu", "ea_batch.cu", "ea_batch_k384.cu", "ea_batch_k512.cu", "ea_server.cu", "ea_api.cu", "ea_static.cu", "ea_tpack.cu"]
+SOURCES = ["ea_kernels.cu", "ea_field.cu", "ea_unit_fast.cu", "ea_unit_wave.cu", "ea_batch.cu", "ea_batch_k384.cu", "ea_batch_k512.cu", "ea_batch_field.cu", "ea_server.cu", "ea_api.cu", "ea_static.cu", "ea_tpack.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

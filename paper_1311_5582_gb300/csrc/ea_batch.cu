@@ -54,10 +54,11 @@ struct BatchShape {
     uint64_t total;
     size_t smem;
     int threads;
+    bool field;
     bool operator==(const BatchShape &o) const
     {
         return ninst == o.ninst && ninit == o.ninit && total == o.total && smem == o.smem &&
-               threads == o.threads;
+               threads == o.threads && field == o.field;
     }
 };
 
@@ -89,21 +90,30 @@ std::vector<BPlan> batch_candidates(const ea_ctx *c, size_t optin)
     const uint32_t units = c->G * c->C;
     const int tpl_min = pow2_ceil((Q + kMaxQuadsPerThread - 1) / kMaxQuadsPerThread);
     const int tpl_max = pow2_ceil(Q);
+    // a member in a field runs in the field kernel (384 threads): the field
+    // bodies keep their thresholds and magnetisation counts in shared memory
+    const bool field = c->h_num != 0;
+    const int maxthr = field ? kBatchSmallThreads : kBatchMaxThreads;
+    const size_t mbytes = field ? (size_t)kMaxTemps * kLanes * 4 : 0;
     auto add = [&](const BPlan &p) {
-        if (p.threads < 1 || p.threads > kBatchMaxThreads) return;
+        if (p.threads < 1 || p.threads > maxthr) return;
         if ((p.smem > swap_scratch_bytes() ? p.smem : swap_scratch_bytes()) > optin) return;
         for (const BPlan &q : out)
             if (q.form == p.form && q.p1 == p.p1 && q.p2 == p.p2) return;
         out.push_back(p);
     };
-    // wavefront unit body (L = 8)
-    if (wave_unit_threads(L, NT) != 0) {
-        const bool sw = wave_unit_smem(L, NT, c->swap_len, true) <= optin;
-        add({kBWave, 16, 0, wave_unit_threads(L, NT), sw, true, wave_unit_smem(L, NT, c->swap_len, sw)});
+    // wavefront unit body (L = 8; in a field, the fields it takes)
+    int fkind = 0;
+    for (const Plan &p : c->plans)
+        if (p.form == kFormUnitWave) fkind = p.field_kind;
+    if (wave_unit_threads(L, NT) != 0 && (!field || fkind != 0)) {
+        const bool sw = wave_unit_smem(L, NT, c->swap_len, true, field) <= optin;
+        add({kBWave, 16, fkind, wave_unit_threads(L, NT), sw, true, wave_unit_smem(L, NT, c->swap_len, sw, field)});
     }
-    // specialised unit kernel (variants compiled into the batch kernel)
+    // specialised unit kernel (variants compiled into the batch kernel; field-free)
     const int fast[][2] = {{8, 8}, {8, 4}, {16, 32}, {16, 64}};
     for (const auto &v : fast) {
+        if (field) break;
         if (v[0] != L) continue;
         const int t = fast_unit_threads(L, v[1], NT);
         if (t == 0 || t > kBatchMaxThreads) continue;
@@ -117,7 +127,7 @@ std::vector<BPlan> batch_candidates(const ea_ctx *c, size_t optin)
             if (m > kMaxTemps / NT) m = kMaxTemps / NT;
             if ((uint32_t)m > units) m = (int)units;
             for (; m >= 1; --m) {
-                size_t smem = UnitSmem::base_bytes(N, NT, m);
+                size_t smem = UnitSmem::base_bytes(N, NT, m) + mbytes;
                 if (smem > optin) continue;
                 const size_t sw = UnitSmem::swap_bytes(NT, c->swap_len);
                 const bool sws = smem + sw <= optin;
@@ -126,9 +136,10 @@ std::vector<BPlan> batch_candidates(const ea_ctx *c, size_t optin)
             }
         }
     // slot chunks: nlat lattices per CTA, as few CTAs per unit as fit, balanced
-    const size_t lat = (size_t)N * 4, jb = (size_t)3 * N * 4, eb = (size_t)kMaxTemps * kLanes * 4;
-    for (int tpl = tpl_min; tpl <= tpl_max && tpl <= kBatchMaxThreads; tpl *= 2)
+    const size_t lat = (size_t)N * 4, jb = (size_t)3 * N * 4, eb = (size_t)kMaxTemps * kLanes * 4 + mbytes;
+    for (int tpl = tpl_min; tpl <= tpl_max && tpl <= maxthr; tpl *= 2)
         for (int maxt : {kBatchSmallThreads, kBatchMaxThreads}) {
+            if (maxt > maxthr) continue;
             const bool js = jb + lat + eb <= optin;
             const size_t budget = optin - (js ? jb : 0) - eb;
             int nlat = maxt / tpl;
@@ -212,6 +223,7 @@ struct ea_batch {
     cudaEvent_t done;
     bool pending;
     uint64_t launches;
+    int field_mode = -1;                        // -1 no member yet; 1: members in a field (field kernel)
 };
 
 namespace {
@@ -274,11 +286,12 @@ std::vector<int> resolve(const ea_batch *b)
     return pick(ea::kBatchSmallThreads);
 }
 
-// Dynamic shared memory granted to the 384- and 512-thread batch kernels.
+// Dynamic shared memory granted to the 384- and 512-thread batch kernels and
+// the field kernel.
 // The attribute belongs to the kernel, not to a batch object, so every batch
 // of the process raises it through this one record and never lowers it.
 std::mutex g_smem_mu;
-size_t g_smem_granted[2] = {0, 0};
+size_t g_smem_granted[3] = {0, 0, 0};
 
 cudaError_t grant_batch_smem(const void *kern, int which, size_t smem)
 {
@@ -336,7 +349,9 @@ int ea_batch_add(ea_batch *b, ea_ctx *ctx)
 {
     if (!b || !ctx) return EA_EINVAL;
     if (ctx->device != b->device) return EA_EINVAL;
-    if (ctx->h_num != 0) return EA_EINVAL;   // the batch kernel runs the field-free bodies
+    // one kernel per call: members all field-free, or all in a field
+    const int mode = ctx->h_num != 0 ? 1 : 0;
+    if (b->field_mode >= 0 && b->field_mode != mode) return EA_EINVAL;
     for (const ea_ctx *m : b->ctxs)
         if (m == ctx) return EA_EINVAL;      // a member runs once per call
     std::vector<ea::BPlan> c = ea::batch_candidates(ctx, b->optin);
@@ -344,6 +359,7 @@ int ea_batch_add(ea_batch *b, ea_ctx *ctx)
     b->ctxs.push_back(ctx);
     b->cands.push_back(std::move(c));
     b->choice.push_back(-1);
+    b->field_mode = mode;
     return EA_OK;
 }
 
@@ -353,6 +369,7 @@ int ea_batch_clear(ea_batch *b)
     b->ctxs.clear();
     b->cands.clear();
     b->choice.clear();
+    b->field_mode = -1;
     return EA_OK;
 }
 
@@ -437,6 +454,8 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
     for (int r : plan_of)
         if (r < 0) return EA_EUNSUPPORTED;
     const int threads = kernel_width(b, plan_of);
+    const bool field = b->field_mode == 1;
+    if (field && threads != kBatchSmallThreads) return EA_EUNSUPPORTED;   // the field kernel is 384 wide
     std::vector<size_t> members;
     for (size_t i = 0; i < b->ctxs.size(); ++i)
         if (n_of[i] > 0) members.push_back(i);
@@ -473,6 +492,11 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
         I.a.rk = c->rk;
         I.a.err = c->d_err;
         I.a.g_base = c->g_base;
+        I.a.metro_f = c->d_metro_f;
+        I.a.mag = c->d_mag;
+        I.a.h_num = c->h_num;
+        I.a.h_den = c->h_den;
+        I.a.step = c->step;
         I.a.s0 = c->sweep;
         I.a.n_sweeps = n_sweeps;
         I.a.swap_every = swap_every;
@@ -484,6 +508,7 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
         I.units = c->G * c->C;
         I.swap_smem = p.swap_smem ? 1 : 0;
         I.j_smem = p.j_smem ? 1 : 0;
+        I.field_kind = p.form == kBWave ? p.p2 : 0;
         passes[ii] = swaps_between(c->sweep, c->sweep + n_sweeps, swap_every);
         const uint64_t unit_work = (uint64_t)n_sweeps * c->N * c->NT;
         if (p.form == kBChunk) {
@@ -532,8 +557,9 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
     hdr->spin_limit = b->wait_limit ? b->wait_limit : kSpinLimit;
     b->stall_next = false;
 
-    const void *kern = threads == kBatchSmallThreads ? batch_kernel_384() : batch_kernel_512();
-    const BatchShape shape{ninst, init.size(), total, smem, threads};
+    const void *kern = field ? batch_kernel_field_384()
+                             : threads == kBatchSmallThreads ? batch_kernel_384() : batch_kernel_512();
+    const BatchShape shape{ninst, init.size(), total, smem, threads, field};
     const bool replay = b->have_graph && b->g_shape == shape;
     if (!replay) {
         if (b->have_graph) {
@@ -564,7 +590,7 @@ int batch_sweep_impl(ea_batch *b, const uint32_t *n_of, const uint32_t *k_of)
                 return cuda_err(e);
             b->joins_dirty = false;
         }
-        e = grant_batch_smem(kern, threads == kBatchSmallThreads ? 0 : 1, smem);
+        e = grant_batch_smem(kern, field ? 2 : threads == kBatchSmallThreads ? 0 : 1, smem);
         if (e != cudaSuccess) return cuda_err(e);
         int per_sm = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
@@ -664,7 +690,7 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
     // save every member's state; each probe starts from it and is undone
     const size_t n = b->ctxs.size();
     std::vector<uint32_t *> sp(n, nullptr);
-    std::vector<int32_t *> en(n, nullptr);
+    std::vector<int32_t *> en(n, nullptr), mg(n, nullptr);   // mg: magnetisations of field members
     std::vector<uint64_t> sw(n), ps(n), ln(n);
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaError_t e = cudaEventCreate(&t0);
@@ -678,6 +704,9 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
         if (e == cudaSuccess) e = cudaMalloc(&en[i], bytes_e(i));
         if (e == cudaSuccess) e = cudaMemcpyAsync(sp[i], c->d_spins, bytes_s(i), cudaMemcpyDeviceToDevice, b->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(en[i], c->d_energy, bytes_e(i), cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess && c->d_mag) e = cudaMalloc(&mg[i], bytes_e(i));
+        if (e == cudaSuccess && c->d_mag)
+            e = cudaMemcpyAsync(mg[i], c->d_mag, bytes_e(i), cudaMemcpyDeviceToDevice, b->stream);
     }
     auto restore = [&]() -> int {
         int r = wait_pending(b);
@@ -685,6 +714,8 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
             ea_ctx *c = b->ctxs[i];
             cudaError_t x = cudaMemcpyAsync(c->d_spins, sp[i], bytes_s(i), cudaMemcpyDeviceToDevice, b->stream);
             if (x == cudaSuccess) x = cudaMemcpyAsync(c->d_energy, en[i], bytes_e(i), cudaMemcpyDeviceToDevice, b->stream);
+            if (x == cudaSuccess && mg[i])
+                x = cudaMemcpyAsync(c->d_mag, mg[i], bytes_e(i), cudaMemcpyDeviceToDevice, b->stream);
             if (x != cudaSuccess && r == EA_OK) r = cuda_err(x);
             c->sweep = sw[i]; c->pass = ps[i]; c->launches = ln[i];
         }
@@ -714,6 +745,7 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
     // coordinate descent over each member's candidates, per kernel width
     for (int width : {kBatchSmallThreads, kBatchMaxThreads}) {
         if (rc != EA_OK) break;
+        if (b->field_mode == 1 && width != kBatchSmallThreads) continue;   // the field kernel is 384 wide
         b->force_threads = width;
         std::vector<int> cur(n, -1);
         bool ok = true;
@@ -747,6 +779,7 @@ int ea_batch_autotune(ea_batch *b, uint32_t probe_sweeps, uint32_t swap_every, f
     for (size_t i = 0; i < n; ++i) {
         cudaFree(sp[i]);
         cudaFree(en[i]);
+        cudaFree(mg[i]);
     }
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);

@@ -21,6 +21,7 @@ struct BatchInst {
     int32_t L, form, p1, p2;    // p1: threads per lattice (unit, chunk), HP (fast), 16 (wave);
                                 // p2: units per task (unit) or lattices per chunk (chunked)
     int32_t swap_smem, j_smem;
+    int32_t field_kind;     // field members of the field kernel, wave form: 34 or 43 (else 0)
     uint32_t units;         // G * C; a unit task starts at unit `task.unit`
     uint32_t pieces;        // unit forms: sweep segments; chunked: swap intervals
     uint32_t seg;           // unit forms: sweeps per segment
@@ -84,11 +85,12 @@ __host__ __device__ inline uint32_t intervals_of(uint64_t s_begin, uint32_t n, u
 
 namespace {
 
+template <bool FIELD>
 __device__ __forceinline__ void run_unit(int L, uint32_t *base, const SweepLaunch &a, uint32_t unit,
                                          int tpl, int swap_smem, int m)
 {
     switch (L) {
-#define EA_U(X) case X: unit_body<X, false>(base, a, unit, tpl, 0, swap_smem, m); break;
+#define EA_U(X) case X: unit_body<X, false, FIELD>(base, a, unit, tpl, 0, swap_smem, m); break;
         EA_U(4) EA_U(6) EA_U(8) EA_U(10) EA_U(12) EA_U(14) EA_U(16) EA_U(20) EA_U(24) EA_U(32)
 #undef EA_U
     default: break;
@@ -104,14 +106,15 @@ __device__ __forceinline__ void run_fast(int L, int HP, uint32_t *base, const Sw
     else if (L == 16 && HP == 64) unit_fast_body<16, 64, false>(base, a, unit, 0, swap_smem, 0, 0);
 }
 
+template <bool FIELD>
 __device__ __forceinline__ void run_chunk(int L, int j_smem, uint32_t *base, const SweepLaunch &a,
                                           uint32_t unit, int chunk, int tpl, int nlat)
 {
     switch (L) {
 #define EA_C(X)                                                                          \
     case X:                                                                              \
-        if (j_smem) chunk_body<X, true, false>(base, a, unit, chunk, tpl, nlat);         \
-        else chunk_body<X, false, false>(base, a, unit, chunk, tpl, nlat);               \
+        if (j_smem) chunk_body<X, true, false, FIELD>(base, a, unit, chunk, tpl, nlat);  \
+        else chunk_body<X, false, false, FIELD>(base, a, unit, chunk, tpl, nlat);        \
         break;
         EA_C(4) EA_C(6) EA_C(8) EA_C(10) EA_C(12) EA_C(14) EA_C(16) EA_C(20) EA_C(24) EA_C(32)
 #undef EA_C
@@ -136,7 +139,10 @@ __device__ __forceinline__ void publish(BatchTask *tasks, uint32_t *ready, Batch
     }
 }
 
-template <int MAXT>
+// FIELD = true: the kernel for batches of ensembles in an external field (its
+// members run the field bodies: the generic unit and chunk forms, the
+// wavefront form for the fields it takes).
+template <int MAXT, bool FIELD = false>
 __global__ void __launch_bounds__(MAXT, 1)
 k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tasks, uint32_t *ready,
         uint32_t *join, BatchCtl *ctl)
@@ -204,14 +210,19 @@ k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tas
         const BatchTask t = s_t;
         const BatchInst &I = insts[t.inst];
         if (I.form == kBUnit)
-            run_unit(I.L, base, s_a, t.unit, I.p1, I.swap_smem,
-                     (int)min((uint32_t)I.p2, I.units - t.unit));
-        else if (I.form == kBFast) run_fast(I.L, I.p1, base, s_a, t.unit, I.swap_smem);
-        else if (I.form == kBWave) unit_wave_body<false>(base, s_a, t.unit, I.swap_smem);
-        else run_chunk(I.L, I.j_smem, base, s_a, t.unit, (int)t.chunk, I.p1, I.p2);
+            run_unit<FIELD>(I.L, base, s_a, t.unit, I.p1, I.swap_smem,
+                            (int)min((uint32_t)I.p2, I.units - t.unit));
+        else if (I.form == kBChunk) run_chunk<FIELD>(I.L, I.j_smem, base, s_a, t.unit, (int)t.chunk, I.p1, I.p2);
+        else if constexpr (FIELD) {
+            if (I.form == kBWave && I.field_kind == 34) unit_wave_body<false, 34>(base, s_a, t.unit, I.swap_smem);
+            else if (I.form == kBWave && I.field_kind == 43) unit_wave_body<false, 43>(base, s_a, t.unit, I.swap_smem);
+        } else {
+            if (I.form == kBFast) run_fast(I.L, I.p1, base, s_a, t.unit, I.swap_smem);
+            else if (I.form == kBWave) unit_wave_body<false>(base, s_a, t.unit, I.swap_smem);
+        }
         __syncthreads();
         if (I.form == kBWave) {
-            wave_release(base, (int)I.a.NT, false);
+            wave_release(base, (int)I.a.NT, FIELD);
             __syncthreads();
         }
         if (I.form != kBChunk) {
@@ -254,5 +265,6 @@ k_batch(const BatchHdr *hdr, const BatchInst *__restrict__ insts, BatchTask *tas
 // Kernel entry points of one instantiation (defined in ea_batch_k*.cu).
 const void *batch_kernel_384();
 const void *batch_kernel_512();
+const void *batch_kernel_field_384();
 
 }  // namespace ea

@@ -420,7 +420,25 @@ __device__ __forceinline__ void swap_unit_body(uint32_t *base, const SweepLaunch
                               swap_uniform(a.rk, p, b, P, g + a.g_base, c));
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && a.h_num != 0) {
+        // field: decisions on Et = h_den E - h_num M in steps of a.step; E and M travel together
+        int32_t *E = a.energy + (size_t)unit * NT * kLanes;
+        int32_t *M = a.mag + (size_t)unit * NT * kLanes;
+        int ce = __ldcg(E + lane), cm = __ldcg(M + lane);
+        for (int p = 0; p + 1 < NT; ++p) {
+            const int ne = __ldcg(E + (p + 1) * kLanes + lane), nm = __ldcg(M + (p + 1) * kLanes + lane);
+            const int xc = a.h_den * ce - a.h_num * cm, xn = a.h_den * ne - a.h_num * nm;
+            const bool ok = (xc - xn) >= (bnd[p * kLanes + lane] / 4) * a.step;
+            const uint32_t m = __ballot_sync(kFull, ok);
+            E[p * kLanes + lane] = ok ? ne : ce;
+            M[p * kLanes + lane] = ok ? nm : cm;
+            ce = ok ? ce : ne;
+            cm = ok ? cm : nm;
+            if (lane == 0) msk[p] = m;
+        }
+        E[(NT - 1) * kLanes + lane] = ce;
+        M[(NT - 1) * kLanes + lane] = cm;
+    } else if (warp == 0) {
         int32_t *E = a.energy + (size_t)unit * NT * kLanes;
         int cur = __ldcg(E + lane);
         for (int p = 0; p + 1 < NT; ++p) {

@@ -55,6 +55,11 @@ struct Request {
     uint32_t n_sweeps = 0, swap_every = 0;
     uint32_t *spins_out = nullptr;
     int32_t *energies_out = nullptr;
+    int32_t *mags_out = nullptr;
+    bool field = false;                           // in an external field (runs in the field batches)
+    bool has_fld = false;                         // submitted with ea_submit_field (h_num may be 0)
+    ea_field fld{};                               // points into metro_f
+    std::vector<uint64_t> metro_f;
     size_t bytes = 0;                             // device bytes while resident
     Clock::time_point t_submit;
     ea_ctx *ctx = nullptr;
@@ -62,7 +67,7 @@ struct Request {
     uint64_t words = 0;                           // site-words of one sweep (N * NT * C * G)
     uint32_t waited = 0;                          // consecutive rounds left out
     uint32_t *d_spins = nullptr;                  // export scratch (pool) of a finishing request
-    int32_t *d_energies = nullptr;
+    int32_t *d_energies = nullptr, *d_mags = nullptr;
     int status = EA_OK;                           // of the export
 };
 
@@ -88,6 +93,7 @@ struct ea_server {
     cudaEvent_t admitted = nullptr;
     cudaMemPool_t pool = nullptr;
     ea_batch *batch[2] = {nullptr, nullptr};      // rounds alternate between the two
+    ea_batch *batch_f[2] = {nullptr, nullptr};    // the same for requests in a field (own kernel)
     Round rounds_ring[2];
     uint64_t round_index = 0;
     std::thread worker;
@@ -153,7 +159,7 @@ void admit(ea_server *s)
             continue;
         }
         ea_ctx *ctx = nullptr;
-        const int rc = ea::create_ctx(&r->cfg, s->admit, s->pool, &ctx);
+        const int rc = ea::create_ctx(&r->cfg, s->admit, s->pool, &ctx, r->has_fld ? &r->fld : nullptr);
         if (rc == EA_ENOMEM && !s->live.empty()) {
             // the budget was optimistic: retry once resident requests finish
             std::lock_guard<std::mutex> lk(s->mu);
@@ -199,6 +205,10 @@ void enqueue_export(ea_server *s, Request &r)
         e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.d_spins), nsp * 4, s->pool, s->compute);
         if (e == cudaSuccess) rc = ea_read_spins(c, r.d_spins);
     }
+    if (e == cudaSuccess && rc == EA_OK && r.mags_out) {
+        e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.d_mags), nen * 4, s->pool, s->compute);
+        if (e == cudaSuccess) rc = ea_magnetisations(c, r.d_mags);
+    }
     r.status = e != cudaSuccess ? (e == cudaErrorMemoryAllocation ? EA_ENOMEM : EA_ECUDA) : rc;
 }
 
@@ -223,6 +233,9 @@ void deliver(ea_server *s, Round &rd)
         if (st == EA_OK && e == cudaSuccess && r.spins_out)
             e = cudaMemcpyAsync(r.spins_out, r.d_spins, (size_t)c->G * c->NT * c->C * c->N * 4,
                                 cudaMemcpyDeviceToHost, s->copy);
+        if (st == EA_OK && e == cudaSuccess && r.mags_out)
+            e = cudaMemcpyAsync(r.mags_out, r.d_mags, (size_t)c->G * c->NT * c->C * ea::kLanes * 4,
+                                cudaMemcpyDeviceToHost, s->copy);
         if (e != cudaSuccess) st = EA_ECUDA;
         status[j] = st;
     }
@@ -231,8 +244,10 @@ void deliver(ea_server *s, Round &rd)
         Request &r = *rd.finishing[j];
         if (r.d_spins) cudaFreeAsync(r.d_spins, s->copy);
         if (r.d_energies) cudaFreeAsync(r.d_energies, s->copy);
+        if (r.d_mags) cudaFreeAsync(r.d_mags, s->copy);
         r.d_spins = nullptr;
         r.d_energies = nullptr;
+        r.d_mags = nullptr;
         ea::destroy_ctx(r.ctx, s->compute);      // after every round already queued
         r.ctx = nullptr;
         s->used -= r.bytes;
@@ -273,20 +288,29 @@ void run_round(ea_server *s, uint64_t k)
     }
     const double qd = s->round_ms * s->rate / (words > 0 ? words : 1.0);
     const uint32_t q = (uint32_t)std::max(1.0, std::min(qd, 1048576.0));
+    // requests in a field run in the field batch kernel: one call per kind
+    ea_batch *bf = s->batch_f[k & 1];
     ea_batch_clear(b);
-    std::vector<uint32_t> nsw(n), kev(n);
+    ea_batch_clear(bf);
+    std::vector<uint32_t> nsw[2], kev[2];
     int rc = EA_OK;
+    double work = 0.0, kind_work[2] = {0.0, 0.0};
+    std::vector<uint32_t> nsw_all(n);
     for (size_t i = 0; i < n && rc == EA_OK; ++i) {
         Request &r = *s->live[i];
-        rc = ea_batch_add(b, r.ctx);
-        nsw[i] = in_round[i] ? std::min(q, r.left) : 0u;
+        const int kd = r.field ? 1 : 0;
+        rc = ea_batch_add(kd ? bf : b, r.ctx);
+        nsw_all[i] = in_round[i] ? std::min(q, r.left) : 0u;
+        nsw[kd].push_back(nsw_all[i]);
+        kev[kd].push_back(r.swap_every);
         r.waited = in_round[i] ? 0u : r.waited + 1u;
-        kev[i] = r.swap_every;
+        const double w = (double)nsw_all[i] * (double)r.words;
+        work += w;
+        kind_work[kd] += w;
     }
-    double work = 0.0;
-    for (size_t i = 0; i < n; ++i) work += (double)nsw[i] * (double)s->live[i]->words;
     cudaEventRecord(rd.start, s->compute);
-    if (rc == EA_OK && work > 0.0) rc = ea_batch_sweep_each(b, nsw.data(), kev.data());
+    if (rc == EA_OK && kind_work[0] > 0.0) rc = ea_batch_sweep_each(b, nsw[0].data(), kev[0].data());
+    if (rc == EA_OK && kind_work[1] > 0.0) rc = ea_batch_sweep_each(bf, nsw[1].data(), kev[1].data());
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->rounds += 1;
@@ -311,7 +335,7 @@ void run_round(ea_server *s, uint64_t k)
     std::vector<std::unique_ptr<Request>> keep;
     for (size_t i = 0; i < n; ++i) {
         std::unique_ptr<Request> &r = s->live[i];
-        r->left -= nsw[i];
+        r->left -= nsw_all[i];
         if (r->left == 0) {
             enqueue_export(s, *r);
             rd.finishing.push_back(std::move(r));
@@ -367,6 +391,7 @@ void worker_main(ea_server *s)
         for (auto &r : rd.finishing) {
             if (r->d_spins) cudaFreeAsync(r->d_spins, s->compute);
             if (r->d_energies) cudaFreeAsync(r->d_energies, s->compute);
+            if (r->d_mags) cudaFreeAsync(r->d_mags, s->compute);
             ea::destroy_ctx(r->ctx, s->compute);
             r->ctx = nullptr;
         }
@@ -386,6 +411,8 @@ void release_server(ea_server *s)
 {
     for (ea_batch *b : s->batch)
         if (b) ea_batch_destroy(b);
+    for (ea_batch *b : s->batch_f)
+        if (b) ea_batch_destroy(b);
     for (Round &rd : s->rounds_ring) {
         if (rd.start) cudaEventDestroy(rd.start);
         if (rd.done) cudaEventDestroy(rd.done);
@@ -399,14 +426,14 @@ void release_server(ea_server *s)
 }
 
 // Up-front checks of a request (the tables are validated at admission).
-int check_request(const ea_config *cfg)
+int check_request(const ea_config *cfg, bool need_metro)
 {
     if (cfg->L < 4 || (cfg->L & 1u)) return EA_EINVAL;
     if (!ea::supported_L((int)cfg->L)) return EA_EUNSUPPORTED;
     if (cfg->n_groups == 0 || cfg->n_temps == 0 || cfg->n_temps > (uint32_t)ea::kMaxTemps) return EA_EINVAL;
     if (cfg->n_copies < 1 || cfg->n_copies > 2) return EA_EINVAL;
     if ((uint64_t)cfg->group_base + cfg->n_groups > (1ull << 32)) return EA_EINVAL;
-    if (!cfg->bonds || !cfg->spins0 || !cfg->metro) return EA_EINVAL;
+    if (!cfg->bonds || !cfg->spins0 || (need_metro && !cfg->metro)) return EA_EINVAL;
     if (cfg->n_temps > 1 && cfg->swap_len > 0 && !cfg->swapt) return EA_EINVAL;
     return EA_OK;
 }
@@ -453,6 +480,8 @@ int ea_server_create(const ea_server_opts *opts, ea_server **out)
     int rc = e == cudaSuccess ? EA_OK : EA_ECUDA;
     if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch[0]);
     if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch[1]);
+    if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch_f[0]);
+    if (rc == EA_OK) rc = ea_batch_create(s->compute, &s->batch_f[1]);
     if (rc == EA_OK) {
         try {
             s->worker = std::thread(worker_main, s);
@@ -470,8 +499,16 @@ int ea_server_create(const ea_server_opts *opts, ea_server **out)
 
 int ea_submit(ea_server *s, const ea_config *cfg, const ea_request *req, uint64_t *ticket)
 {
+    return ea_submit_field(s, cfg, nullptr, req, ticket);
+}
+
+int ea_submit_field(ea_server *s, const ea_config *cfg, const ea_field *field, const ea_request *req,
+                    uint64_t *ticket)
+{
     if (!s || !cfg || !req || !ticket) return EA_EINVAL;
-    const int chk = check_request(cfg);
+    const bool in_field = field != nullptr && field->h_num != 0;
+    if (field && (!field->metro || field->h_den < 1)) return EA_EINVAL;
+    const int chk = check_request(cfg, field == nullptr);
     if (chk != EA_OK) return chk;
     auto r = std::unique_ptr<Request>(new (std::nothrow) Request());
     if (!r) return EA_ENOMEM;
@@ -482,24 +519,34 @@ int ea_submit(ea_server *s, const ea_config *cfg, const ea_request *req, uint64_
     try {
         r->bonds.assign(cfg->bonds, cfg->bonds + nbo);
         r->spins0.assign(cfg->spins0, cfg->spins0 + nsp);
-        r->metro.assign(cfg->metro, cfg->metro + (size_t)cfg->n_temps * 3);
+        if (cfg->metro) r->metro.assign(cfg->metro, cfg->metro + (size_t)cfg->n_temps * 3);
         if (nsw) r->swapt.assign(cfg->swapt, cfg->swapt + nsw);
+        if (field) r->metro_f.assign(field->metro, field->metro + (size_t)cfg->n_temps * 14);
     } catch (...) {
         return EA_ENOMEM;
     }
     r->cfg = *cfg;
     r->cfg.bonds = r->bonds.data();
     r->cfg.spins0 = r->spins0.data();
-    r->cfg.metro = r->metro.data();
+    r->cfg.metro = cfg->metro ? r->metro.data() : nullptr;
     r->cfg.swapt = nsw ? r->swapt.data() : nullptr;
+    if (field) {
+        // the field's tables (h_num == 0 gives the field-free method, as ea_create_field)
+        r->has_fld = true;
+        r->field = in_field;
+        r->fld = *field;
+        r->fld.metro = r->metro_f.data();
+    }
+    r->mags_out = in_field ? req->magnetisations_out : nullptr;
     r->n_sweeps = req->n_sweeps;
     r->swap_every = req->swap_every;
     r->spins_out = req->spins_out;
     r->energies_out = req->energies_out;
     r->words = (uint64_t)nsp;
     // resident state plus the output scratch taken at completion
-    r->bytes = ea::ctx_device_bytes(cfg) + (r->spins_out ? nsp * 4 : 0) +
-               (r->energies_out ? (size_t)cfg->n_groups * cfg->n_temps * cfg->n_copies * ea::kLanes * 4 : 0);
+    const size_t nen = (size_t)cfg->n_groups * cfg->n_temps * cfg->n_copies * ea::kLanes;
+    r->bytes = ea::ctx_device_bytes(cfg) + (r->spins_out ? nsp * 4 : 0) + (r->energies_out ? nen * 4 : 0) +
+               (r->field ? nen * 4 * (r->mags_out ? 2 : 1) + (size_t)cfg->n_temps * 14 * 8 : 0);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);

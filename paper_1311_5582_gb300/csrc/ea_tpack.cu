@@ -683,8 +683,9 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     cudaFree(staging);
     staging = nullptr;
     // slot groups while R * C is small: the most groups (at most eight) that keep
-    // the CTAs within one wave, one a SM (a second wave costs more than the
-    // groups gain: 2.40 against 1.74 ps per flip at L = 16 with 32 realizations)
+    // the CTAs within one wave, at most one CTA per SM (a second wave costs more
+    // than the extra groups gain: 2.40 against 1.74 ps per flip at L = 16 with
+    // 32 realizations)
     int dev = 0, sms = 0;
     EA_TP_TRY(cudaGetDevice(&dev));
     EA_TP_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -117,12 +117,52 @@ def test_magnetisations_of_known_states():
     assert np.all(M[0, 2, 1] == -N)
 
 
-def test_batch_rejects_field_contexts():
+def test_batch_keeps_field_and_field_free_members_apart():
+    """One call runs one kernel: a batch takes members all in a field or all without."""
     inst = W.Instance(L=4, G=1, NT=4, C=2, seed=3, tmin=1.0, tmax=2.0, input_seed=4)
     gpu, _ = field_pair(inst, 1, 2)
-    b = ea.Batch()
+    inp = W.draw_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    plain = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
+    b = ea.Batch([gpu])
+    with pytest.raises(ea.EAError):
+        b.add(plain)
+    b.clear()
+    b.add(plain)
     with pytest.raises(ea.EAError):
         b.add(gpu)
+
+
+FIELD_MIX = [  # (L, G, NT, C, h_num, h_den): wavefront (L = 8), generic unit, chunked (L = 16 x 32)
+    (8, 2, 24, 2, 1, 2), (8, 1, 9, 2, -3, 4), (6, 2, 7, 2, 2, 1), (10, 1, 12, 1, 1, 3), (16, 1, 32, 2, 1, 2),
+]
+
+
+def test_field_batch_matches_members_alone_and_oracle():
+    """Ensembles in different fields advanced by one persistent launch of the
+    field batch kernel: each member exactly as ea_sweep alone, and as the oracle."""
+    made = []
+    for i, (L, G, NT, C, hn, hd) in enumerate(FIELD_MIX):
+        inst = W.Instance(L=L, G=G, NT=NT, C=C, seed=900 + i, tmin=0.8, tmax=2.0, input_seed=40 + i)
+        made.append((inst, hn, hd, field_pair(inst, hn, hd), field_pair(inst, hn, hd)[0]))
+    batch = ea.Batch([m[3][0] for m in made])
+    forms = [batch.plans(i)[batch.plan(i)]["form"] for i in range(len(made))]
+    assert forms[0] == "unit-wave" and "chunked" in forms
+    schedule = [(23, 1), (17, 3), (10, 10)]
+    for n, k in schedule:
+        batch.sweep(n, k)
+    batch.sync()
+    for inst, hn, hd, (gpu, sim), alone in made:
+        for n, k in schedule:
+            alone.sweep(n, k)
+            sim.sweep(n, k, threads=8)
+        tag = f"L={inst.L} h={hn}/{hd}"
+        sp = gpu.read_spins().cpu().numpy().view(np.uint32)
+        np.testing.assert_array_equal(sp, alone.read_spins().cpu().numpy().view(np.uint32), err_msg=tag)
+        np.testing.assert_array_equal(sp, sim.spins(), err_msg=tag)
+        np.testing.assert_array_equal(gpu.measure()[0].cpu().numpy(), sim.energies(), err_msg=tag)
+        np.testing.assert_array_equal(gpu.magnetisations().cpu().numpy(), sim.magnetisations(), err_msg=tag)
+        assert gpu.counters == alone.counters
 
 
 @pytest.mark.parametrize("NT,C,h_num,h_den,swap_every", [
@@ -141,3 +181,31 @@ def test_field_wavefront_kernel_matches_oracle(NT, C, h_num, h_den, swap_every):
     # a field outside that range keeps to the generic forms
     other, _ = field_pair(W.Instance(L=8, G=1, NT=4, C=2, seed=1, tmin=0.8, tmax=2.0, input_seed=2), 2, 1)
     assert all(p["form"] != "unit-wave" for p in other.plans())
+
+
+def test_server_serves_field_and_field_free_requests_together():
+    """Requests in fields and without share the server's rounds (a field batch and
+    a field-free batch per round); each result equals the request run alone."""
+    srv = ea.Server(round_ms=2)
+    reqs = []
+    for i, (L, G, NT, C, hn, hd) in enumerate(FIELD_MIX[:4] + [(8, 2, 10, 2, 0, 1), (12, 1, 6, 2, 0, 1)]):
+        inst = W.Instance(L=L, G=G, NT=NT, C=C, seed=950 + i, tmin=0.8, tmax=2.0, input_seed=60 + i)
+        inp = W.draw_inputs(inst)
+        n, k = 30 + 7 * i, 1 + i % 3
+        if hn:
+            mf, sw = ea.ea_build_tables_field(inp["betas"], inst.N, hn, hd)
+            t = srv.submit(L, G, NT, C, inst.seed, inp["bonds"], inp["spins"], None, sw, n, k, field=(hn, hd, mf))
+            alone = ea.Ensemble(L, G, NT, C, inst.seed, inp["bonds"], inp["spins"], None, sw, field=(hn, hd, mf))
+        else:
+            metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+            t = srv.submit(L, G, NT, C, inst.seed, inp["bonds"], inp["spins"], metro, swapt, n, k)
+            alone = ea.Ensemble(L, G, NT, C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
+        alone.sweep(n, k)
+        reqs.append((t, alone, hn))
+    for t, alone, hn in reqs:
+        out = srv.wait(t)
+        np.testing.assert_array_equal(out["spins"], alone.read_spins_host())
+        np.testing.assert_array_equal(out["energies"], alone.measure()[0].cpu().numpy())
+        if hn:
+            np.testing.assert_array_equal(out["magnetisations"], alone.magnetisations().cpu().numpy())
+    srv.close()
