@@ -50,14 +50,35 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return make_uint4(c0, c1, c2, c3);
 }
 
-__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c)
+// One three-input logic operation with the truth table LUT over the operand
+// patterns a = 0xF0, b = 0xCC, c = 0xAA, written out so that the compiler
+// keeps the bit-sliced expressions in the form given here.
+template <uint32_t LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c)
 {
-    return (a & b) | (c & (a | b));
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+    return d;
 }
+constexpr uint32_t kXor3 = 0x96u;                   // a ^ b ^ c
+constexpr uint32_t kMaj3 = 0xE8u;                   // majority
+constexpr uint32_t kOr3 = 0xFEu;                    // a | b | c
+constexpr uint32_t kAndOr = 0xEAu;                  // (a & b) | c
+constexpr uint32_t kXorOr = 0x1Eu;                  // a ^ (b | c)
+constexpr uint32_t kAndOr2 = 0xE0u;                 // a & (b | c)
+constexpr uint32_t kOrAnd = 0xF8u;                  // a | (b & c)
+constexpr uint32_t kXorAndN = 0xB4u;                // a ^ (b & ~c)
+static_assert(((0xF0u ^ 0xCCu ^ 0xAAu) & 0xFFu) == kXor3 && (((0xF0u & 0xCCu) | (0xAAu & (0xF0u | 0xCCu))) & 0xFFu) == kMaj3 &&
+              ((0xF0u | 0xCCu | 0xAAu) & 0xFFu) == kOr3 && (((0xF0u & 0xCCu) | 0xAAu) & 0xFFu) == kAndOr &&
+              ((0xF0u ^ (0xCCu | 0xAAu)) & 0xFFu) == kXorOr && ((0xF0u & (0xCCu | 0xAAu)) & 0xFFu) == kAndOr2 &&
+              ((0xF0u | (0xCCu & 0xAAu)) & 0xFFu) == kOrAnd && ((0xF0u ^ (0xCCu & ~0xAAu)) & 0xFFu) == kXorAndN,
+              "truth tables");
+
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return lop3<kMaj3>(a, b, c); }
 __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &cy)
 {
-    s = a ^ b ^ c;
-    cy = maj3(a, b, c);
+    s = lop3<kXor3>(a, b, c);
+    cy = lop3<kMaj3>(a, b, c);
 }
 
 // The words one quad update reads: own spins, the six neighbour spins and the
@@ -173,12 +194,12 @@ __device__ __forceinline__ void unsat_count(uint32_t s, const uint32_t (&nb)[6][
                                             const uint32_t (&jb)[6][4], int j, uint32_t &u0,
                                             uint32_t &u1, uint32_t &u2)
 {
-    const uint32_t e0 = s ^ nb[0][j] ^ jb[0][j];
-    const uint32_t e1 = s ^ nb[1][j] ^ jb[1][j];
-    const uint32_t e2 = s ^ nb[2][j] ^ jb[2][j];
-    const uint32_t e3 = s ^ nb[3][j] ^ jb[3][j];
-    const uint32_t e4 = s ^ nb[4][j] ^ jb[4][j];
-    const uint32_t e5 = s ^ nb[5][j] ^ jb[5][j];
+    const uint32_t e0 = lop3<kXor3>(s, nb[0][j], jb[0][j]);
+    const uint32_t e1 = lop3<kXor3>(s, nb[1][j], jb[1][j]);
+    const uint32_t e2 = lop3<kXor3>(s, nb[2][j], jb[2][j]);
+    const uint32_t e3 = lop3<kXor3>(s, nb[3][j], jb[3][j]);
+    const uint32_t e4 = lop3<kXor3>(s, nb[4][j], jb[4][j]);
+    const uint32_t e5 = lop3<kXor3>(s, nb[5][j], jb[5][j]);
     uint32_t a0, a1, b0, b1;
     full_add(e0, e1, e2, a0, a1);
     full_add(e3, e4, e5, b0, b1);
@@ -188,8 +209,8 @@ __device__ __forceinline__ void unsat_count(uint32_t s, const uint32_t (&nb)[6][
 }
 
 // All-ones iff r < T, for a threshold T <= 2^32 held as 2^64 - T: the high
-// word of r + 2^64 - T, formed by one wide multiply-add that issues to the FMA
-// pipe and leaves the integer ALU pipe to the bit-sliced logic.
+// word of r + 2^64 - T, formed by one wide multiply-add (an add with carry
+// after assembly: one ALU and one FMA-pipe instruction).
 __device__ __forceinline__ uint32_t below_wide(uint32_t r, uint64_t neg_t)
 {
     uint64_t d;
@@ -203,10 +224,10 @@ __device__ __forceinline__ uint32_t below_wide(uint32_t r, uint64_t neg_t)
 __device__ __forceinline__ uint32_t flip_mask(uint32_t u0, uint32_t u1, uint32_t u2, uint32_t r,
                                               uint64_t n0, uint64_t n1, uint64_t n2)
 {
-    const uint32_t ge2 = u2 | u1;
-    const uint32_t ge1 = ge2 | u0;
-    const uint32_t ge3 = u2 | (u1 & u0);
-    return ge3 | (ge2 & below_wide(r, n2)) | (ge1 & below_wide(r, n1)) | below_wide(r, n0);
+    // the masks are nested (m0 => m1 => m2), so
+    //   [u>=3] | m2 [u>=2] | m1 [u>=1] | m0 = u2 | u1 (u0 | m2) | u0 m1 | m0
+    const uint32_t m0 = below_wide(r, n0), m1 = below_wide(r, n1), m2 = below_wide(r, n2);
+    return lop3<kOrAnd>(lop3<kOr3>(lop3<kAndOr2>(u1, u0, m2), u2, m0), u0, m1);
 }
 
 // Sum of four 3-bit lane values (x2 x1 x0)[j] into a 5-bit value A.

@@ -87,8 +87,8 @@ __device__ __forceinline__ QuadRow quad_row(int par, int i)
 __device__ __forceinline__ uint4 ld4(const uint32_t *p) { return *reinterpret_cast<const uint4 *>(p); }
 
 // All-ones iff r < t: the high word of r - t in 64-bit arithmetic, formed as
-// r * 1 + (2^64 - t) by one wide multiply-add, which issues to the FMA pipe
-// and leaves the integer ALU pipe to the bit-sliced logic.
+// r * 1 + (2^64 - t) by one wide multiply-add (the assembler makes it an add
+// with carry: one ALU and one FMA-pipe instruction).
 __device__ __forceinline__ uint32_t below_mask(uint32_t r, uint64_t neg_t)
 {
     uint64_t d;
@@ -136,6 +136,109 @@ __device__ __forceinline__ void acc_add_sum5(uint32_t (&acc)[PL], const uint32_t
     }
 }
 
+// Adds the post-update counts (x2 x1 x0)[j] of one quad to a ripple counter
+// of PL planes: the quad's 5-bit sum, then a ripple add.
+template <int PL>
+struct RippleAcc {
+    uint32_t (&acc)[PL];
+    template <int Q>
+    __device__ __forceinline__ void add(const uint32_t (&x0)[4], const uint32_t (&x1)[4], const uint32_t (&x2)[4])
+    {
+        uint32_t A[5];
+        quad_sum(x0, x1, x2, A);
+        acc_add_sum5<PL>(acc, A);
+    }
+};
+
+// Carry-save counter of the post-update counts of the NQ quads a lane updates
+// in one half-sweep (values up to 24 NQ <= 127).  Plane S[w] holds one bit
+// of weight 2^w per lane; each full adder S[w] + b + b' -> S[w] + 2 c moves
+// one carry up, and a bit left over at a weight waits in P[w] for the next
+// quad.  Which weights hold a waiting bit before quad Q is fixed by the
+// number of input bits (four each at weights 1, 2, 4 per quad), so the whole
+// schedule is resolved at compile time: ~45 full adders for four quads
+// against 128 LOP3s for four 5-bit quad sums each rippled into the counter.
+__host__ __device__ constexpr uint32_t csa_pending(int Q)
+{
+    uint32_t pend = 0;
+    for (int q = 0; q < Q; ++q) {
+        int carry = 0;
+        for (int w = 0; w < 7; ++w) {
+            const int n = (w < 3 ? 4 : 0) + carry + (int)((pend >> w) & 1u);
+            carry = n / 2;
+            pend = (pend & ~(1u << w)) | ((uint32_t)(n & 1) << w);
+        }
+    }
+    return pend;
+}
+
+struct CsaAcc {
+    uint32_t S[7], P[7];
+
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int w = 0; w < 7; ++w) S[w] = P[w] = 0u;
+    }
+
+    template <int Q, int W, int NC>
+    __device__ __forceinline__ void weight(const uint32_t (&x0)[4], const uint32_t (&x1)[4], const uint32_t (&x2)[4],
+                                           const uint32_t (&cin)[NC > 0 ? NC : 1])
+    {
+        constexpr bool pend = ((csa_pending(Q) >> W) & 1u) != 0;
+        constexpr int NIN = W < 3 ? 4 : 0;
+        constexpr int N = NIN + NC + (pend ? 1 : 0);
+        constexpr int NF = N / 2;
+        uint32_t bag[N > 0 ? N : 1];
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) bag[i] = W == 0 ? x0[i] : W == 1 ? x1[i] : x2[i];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) bag[NIN + i] = cin[i];
+        if constexpr (pend) bag[N - 1] = P[W];
+        uint32_t cout[NF > 0 ? NF : 1];
+#pragma unroll
+        for (int i = 0; i < NF; ++i) {
+            const uint32_t sw = S[W];
+            S[W] = lop3<kXor3>(sw, bag[2 * i], bag[2 * i + 1]);
+            cout[i] = lop3<kMaj3>(sw, bag[2 * i], bag[2 * i + 1]);
+        }
+        if constexpr ((N & 1) != 0) P[W] = bag[N - 1];
+        if constexpr (W + 1 < 7) weight<Q, W + 1, NF>(x0, x1, x2, cout);
+    }
+
+    template <int Q>
+    __device__ __forceinline__ void add(const uint32_t (&x0)[4], const uint32_t (&x1)[4], const uint32_t (&x2)[4])
+    {
+        const uint32_t none[1] = {0u};
+        weight<Q, 0, 0>(x0, x1, x2, none);
+    }
+
+    // The binary counter after NQ quads: the waiting bits rippled into S.
+    template <int NQ, int PL>
+    __device__ __forceinline__ void resolve(uint32_t (&acc)[PL])
+    {
+        static_assert(PL == 7, "seven planes hold the count of four quads");
+        constexpr uint32_t pend = csa_pending(NQ);
+        uint32_t cy = 0u;
+        bool has_cy = false;
+#pragma unroll
+        for (int w = 0; w < 7; ++w) {
+            const bool p = ((pend >> w) & 1u) != 0;
+            if (p && has_cy) {
+                const uint32_t sw = S[w];
+                S[w] = lop3<kXor3>(sw, P[w], cy);
+                cy = lop3<kMaj3>(sw, P[w], cy);
+            } else if (p || has_cy) {
+                const uint32_t b = p ? P[w] : cy;
+                cy = S[w] & b;
+                S[w] ^= b;
+                has_cy = true;
+            }
+            acc[w] = S[w];
+        }
+    }
+};
+
 // Metropolis update of the four sites of one quad whose rows have x parity
 // PX, from its loaded words: own spins, the other colour's words at the same
 // class index (xo) and in the rows y +- 1, z +- 1, the bonds of the own colour
@@ -143,12 +246,12 @@ __device__ __forceinline__ void acc_add_sum5(uint32_t (&acc)[PL], const uint32_t
 // row, -z at the z - 1 row).  Valid for rows of four class indices (L = 8),
 // where the x neighbour across the quad edge is in xo itself, and through
 // xe_s / xe_j otherwise.  Returns the new own spins; with WITH_E adds the
-// post-update unsatisfied-bond counts to acc.
-template <int PX, bool WITH_E, int PL>
+// post-update unsatisfied-bond counts to acc (as quad Q of its half-sweep).
+template <int PX, bool WITH_E, int Q, typename Acc>
 __device__ __forceinline__ uint4 quad_core(uint4 own, uint4 xo, uint4 vyp, uint4 vym, uint4 vzp, uint4 vzm,
                                            uint4 jcx, uint4 jcy, uint4 jcz, uint4 jox, uint4 joy, uint4 joz,
                                            uint32_t xe_s, uint32_t xe_j, const uint4 r, uint64_t t0,
-                                           uint64_t t1, uint64_t t2, uint32_t (&acc)[PL])
+                                           uint64_t t1, uint64_t t2, Acc &acc)
 {
     uint32_t nxp[4], nxm[4], jxm[4];
     if constexpr (PX == 0) {
@@ -172,41 +275,38 @@ __device__ __forceinline__ uint4 quad_core(uint4 own, uint4 xo, uint4 vyp, uint4
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t sj = sv[j];
-        const uint32_t e0 = sj ^ nxp[j] ^ jx[j];
-        const uint32_t e1 = sj ^ nxm[j] ^ jxm[j];
-        const uint32_t e2 = sj ^ ny[j] ^ jy[j];
-        const uint32_t e3 = sj ^ my[j] ^ jym[j];
-        const uint32_t e4 = sj ^ nz[j] ^ jz[j];
-        const uint32_t e5 = sj ^ mz[j] ^ jzm[j];
-        uint32_t a0, a1, b0, b1;
-        full_add(e0, e1, e2, a0, a1);                   // u = (a0 + 2 a1) + (b0 + 2 b1)
-        full_add(e3, e4, e5, b0, b1);
+        const uint32_t e0 = lop3<kXor3>(sj, nxp[j], jx[j]);
+        const uint32_t e1 = lop3<kXor3>(sj, nxm[j], jxm[j]);
+        const uint32_t e2 = lop3<kXor3>(sj, ny[j], jy[j]);
+        const uint32_t e3 = lop3<kXor3>(sj, my[j], jym[j]);
+        const uint32_t e4 = lop3<kXor3>(sj, nz[j], jz[j]);
+        const uint32_t e5 = lop3<kXor3>(sj, mz[j], jzm[j]);
+        // u = (a0 + 2 a1) + (b0 + 2 b1)
+        const uint32_t a0 = lop3<kXor3>(e0, e1, e2), a1 = lop3<kMaj3>(e0, e1, e2);
+        const uint32_t b0 = lop3<kXor3>(e3, e4, e5), b1 = lop3<kMaj3>(e3, e4, e5);
         const uint32_t m0 = below_mask(rr[j], t0), m1 = below_mask(rr[j], t1), m2 = below_mask(rr[j], t2);
         if constexpr (WITH_E) {
             // the energy counters need u itself: u0, u1, u2, then the mask
-            const uint32_t u0 = a0 ^ b0;
-            uint32_t u1, u2;
-            full_add(a1, b1, a0 & b0, u1, u2);
-            const uint32_t f = flip_mask_part(u0, u1, u2, m1, m2) | m0;
+            //   f = u2 | u1 (u0 | m2) | u0 m1 | m0
+            const uint32_t u0 = a0 ^ b0, c0 = a0 & b0;
+            const uint32_t u1 = lop3<kXor3>(a1, b1, c0), u2 = lop3<kMaj3>(a1, b1, c0);
+            const uint32_t f = lop3<kOrAnd>(lop3<kOr3>(lop3<kAndOr2>(u1, u0, m2), u2, m0), u0, m1);
             ns[j] = sj ^ f;
+            // post-flip counts: u -> 6 - u where f (u0 unchanged)
             x0[j] = u0;
-            x1[j] = u1 ^ (f & ~u0);
-            x2[j] = u2 ^ (f & ~(u0 & u1));
+            x1[j] = lop3<kXorAndN>(u1, f, u0);
+            x2[j] = lop3<kXorAndN>(u2, f, u0 & u1);
         } else {
             // the mask straight from the two partial sums (m0 => m1 => m2):
             //   [u>=3] | m2 [u>=2] | m1 [u>=1] | m0
             //     = maj(a1, b1, a0 | b0 | m2) | (m2 & maj(a0, b0, m1)) | m0,
             // four LOP3s and the flip folded into the last
-            const uint32_t v = a0 | b0 | m2;
-            const uint32_t t = maj3(a1, b1, v) | (m2 & maj3(a0, b0, m1));
-            ns[j] = sj ^ (t | m0);
+            const uint32_t v = lop3<kOr3>(a0, b0, m2);
+            const uint32_t t = lop3<kAndOr>(m2, lop3<kMaj3>(a0, b0, m1), lop3<kMaj3>(a1, b1, v));
+            ns[j] = lop3<kXorOr>(sj, t, m0);
         }
     }
-    if constexpr (WITH_E) {
-        uint32_t A[5];
-        quad_sum(x0, x1, x2, A);
-        acc_add_sum5<PL>(acc, A);
-    }
+    if constexpr (WITH_E) acc.template add<Q>(x0, x1, x2);
     return make_uint4(ns[0], ns[1], ns[2], ns[3]);
 }
 
@@ -236,8 +336,9 @@ __device__ __forceinline__ void quad_fast(uint32_t *S, const uint32_t *J, const 
         xe_s = So[ie];
         xe_j = Jo[ie];
     }
-    *reinterpret_cast<uint4 *>(Sc + d.k0) = quad_core<PX, WITH_E, PL>(
-        own, xo, vyp, vym, vzp, vzm, jcx, jcy, jcz, jox, joy, joz, xe_s, xe_j, r, t0, t1, t2, acc);
+    RippleAcc<PL> ra{acc};
+    *reinterpret_cast<uint4 *>(Sc + d.k0) = quad_core<PX, WITH_E, 0>(
+        own, xo, vyp, vym, vzp, vzm, jcx, jcy, jcz, jox, joy, joz, xe_s, xe_j, r, t0, t1, t2, ra);
 }
 
 template <int L, int HP, int QPER, int COL, int PX, bool WITH_E, int PL>

@@ -187,9 +187,9 @@ __device__ __forceinline__ uint32_t opaque_zero()
 }
 
 // Metropolis update of one quad of colour COL with x parity PX (L = 8).
-template <int COL, int PX, bool WITH_E, int PL>
+template <int COL, int PX, bool WITH_E, int Q, typename Acc>
 __device__ __forceinline__ void wave_quad(const WaveQuad &q, uint4 r, uint64_t t0, uint64_t t1, uint64_t t2,
-                                          uint32_t (&acc)[PL], uint32_t dep)
+                                          Acc &acc, uint32_t dep)
 {
     constexpr int H4 = 256 * 4, N4 = 512 * 4;           // bytes of a colour half and of a bond direction
     constexpr int C4 = COL * H4, O4 = (1 - COL) * H4;
@@ -199,14 +199,16 @@ __device__ __forceinline__ void wave_quad(const WaveQuad &q, uint4 r, uint64_t t
     const uint4 jcx = lds4<C4>(q.j, dep), jcy = lds4<N4 + C4>(q.j, dep), jcz = lds4<2 * N4 + C4>(q.j, dep);
     const uint4 jox = lds4<O4>(q.j, dep), joy = lds4<N4 + O4>(q.jym, dep), joz = lds4<2 * N4 + O4>(q.jzm, dep);
     const uint32_t xe_s = PX ? xo.x : xo.w;             // x neighbour across the row's edge (R = 4)
-    sts4<C4>(q.s, quad_core<PX, WITH_E, PL>(own, xo, vyp, vym, vzp, vzm, jcx, jcy, jcz, jox, joy, joz, xe_s,
-                                             jox.w, r, t0, t1, t2, acc));
+    sts4<C4>(q.s, quad_core<PX, WITH_E, Q>(own, xo, vyp, vym, vzp, vzm, jcx, jcy, jcz, jox, joy, joz, xe_s,
+                                            jox.w, r, t0, t1, t2, acc));
 }
 
 // Half-sweep of colour COL over the lane's four quads (quad j: row parity
 // j >> 1, x parity ((j >> 1) + COL) & 1).  The sweep- and colour-only parts
 // of the first two Philox rounds are formed once; the uniforms of the next
-// quad are drawn while the current one is updated.
+// quad are drawn while the current one is updated.  With WITH_E, acc
+// receives the lane's sum of the post-update counts u' of its 16 sites (a
+// carry-save counter over the four quads, resolved at the end).
 template <int COL, bool WITH_E, int PL>
 __device__ __forceinline__ void wave_half(const WaveQuad (&wq)[4], uint32_t s, uint32_t ctag,
                                           const RoundKeys &rk, uint64_t t0, uint64_t t1, uint64_t t2,
@@ -218,14 +220,17 @@ __device__ __forceinline__ void wave_half(const WaveQuad (&wq)[4], uint32_t s, u
     auto draw = [&](const WaveQuad &q) {
         return philox_from2(q.phi1 ^ lo1 ^ rk.k[2], q.plo1, hi0b ^ q.plo0 ^ rk.k[3], lo0b, rk);
     };
+    CsaAcc cs;
+    cs.clear();
     uint4 r0 = draw(wq[0]);
     uint4 r1 = draw(wq[1]);
-    wave_quad<COL, COL, WITH_E, PL>(wq[0], r0, t0, t1, t2, acc, dep);
+    wave_quad<COL, COL, WITH_E, 0>(wq[0], r0, t0, t1, t2, cs, dep);
     r0 = draw(wq[2]);
-    wave_quad<COL, COL, WITH_E, PL>(wq[1], r1, t0, t1, t2, acc, dep);
+    wave_quad<COL, COL, WITH_E, 1>(wq[1], r1, t0, t1, t2, cs, dep);
     r1 = draw(wq[3]);
-    wave_quad<COL, 1 - COL, WITH_E, PL>(wq[2], r0, t0, t1, t2, acc, dep);
-    wave_quad<COL, 1 - COL, WITH_E, PL>(wq[3], r1, t0, t1, t2, acc, dep);
+    wave_quad<COL, 1 - COL, WITH_E, 2>(wq[2], r0, t0, t1, t2, cs, dep);
+    wave_quad<COL, 1 - COL, WITH_E, 3>(wq[3], r1, t0, t1, t2, cs, dep);
+    if constexpr (WITH_E) cs.resolve<4, PL>(acc);
 }
 
 // External field h = h_num / h_den (Eq. 1 with the field term; the field runs
