@@ -68,10 +68,12 @@ constexpr uint32_t kXorOr = 0x1Eu;                  // a ^ (b | c)
 constexpr uint32_t kAndOr2 = 0xE0u;                 // a & (b | c)
 constexpr uint32_t kOrAnd = 0xF8u;                  // a | (b & c)
 constexpr uint32_t kXorAndN = 0xB4u;                // a ^ (b & ~c)
+constexpr uint32_t kSelNot = 0x3Au;                 // a ? ~b : c
 static_assert(((0xF0u ^ 0xCCu ^ 0xAAu) & 0xFFu) == kXor3 && (((0xF0u & 0xCCu) | (0xAAu & (0xF0u | 0xCCu))) & 0xFFu) == kMaj3 &&
               ((0xF0u | 0xCCu | 0xAAu) & 0xFFu) == kOr3 && (((0xF0u & 0xCCu) | 0xAAu) & 0xFFu) == kAndOr &&
               ((0xF0u ^ (0xCCu | 0xAAu)) & 0xFFu) == kXorOr && ((0xF0u & (0xCCu | 0xAAu)) & 0xFFu) == kAndOr2 &&
-              ((0xF0u | (0xCCu & 0xAAu)) & 0xFFu) == kOrAnd && ((0xF0u ^ (0xCCu & ~0xAAu)) & 0xFFu) == kXorAndN,
+              ((0xF0u | (0xCCu & 0xAAu)) & 0xFFu) == kOrAnd && ((0xF0u ^ (0xCCu & ~0xAAu)) & 0xFFu) == kXorAndN &&
+              (((0xF0u & ~0xCCu) | (~0xF0u & 0xAAu)) & 0xFFu) == kSelNot,
               "truth tables");
 
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return lop3<kMaj3>(a, b, c); }

@@ -142,29 +142,30 @@ template <int PL>
 struct RippleAcc {
     uint32_t (&acc)[PL];
     template <int Q>
-    __device__ __forceinline__ void add(const uint32_t (&x0)[4], const uint32_t (&x1)[4], const uint32_t (&x2)[4])
+    __device__ __forceinline__ void add(const uint32_t (&x)[3][4])
     {
         uint32_t A[5];
-        quad_sum(x0, x1, x2, A);
+        quad_sum(x[0], x[1], x[2], A);
         acc_add_sum5<PL>(acc, A);
     }
 };
 
-// Carry-save counter of the post-update counts of the NQ quads a lane updates
-// in one half-sweep (values up to 24 NQ <= 127).  Plane S[w] holds one bit
-// of weight 2^w per lane; each full adder S[w] + b + b' -> S[w] + 2 c moves
-// one carry up, and a bit left over at a weight waits in P[w] for the next
-// quad.  Which weights hold a waiting bit before quad Q is fixed by the
-// number of input bits (four each at weights 1, 2, 4 per quad), so the whole
-// schedule is resolved at compile time: ~45 full adders for four quads
-// against 128 LOP3s for four 5-bit quad sums each rippled into the counter.
-__host__ __device__ constexpr uint32_t csa_pending(int Q)
+// Carry-save counter of per-lane sums over the quads a lane updates: each quad
+// brings four bits at each of the weights 2^0 .. 2^(NIN-1) (NIN = 3 for the
+// post-update counts u' of four sites, NIN = 1 for four spin bits), and NP
+// planes hold the largest total.  Plane S[w] holds one bit of weight 2^w per
+// lane; each full adder S[w] + b + b' -> S[w] + 2 c moves one carry up, and a
+// bit left over at a weight waits in P[w] for the next quad.  Which weights
+// hold a waiting bit before quad Q follows from the bit counts alone, so the
+// whole schedule is resolved at compile time (for four quads of u': ~45 full
+// adders, against 128 LOP3s for four 5-bit quad sums rippled into a counter).
+__host__ __device__ constexpr uint32_t csa_pending(int Q, int NIN, int NP)
 {
     uint32_t pend = 0;
     for (int q = 0; q < Q; ++q) {
         int carry = 0;
-        for (int w = 0; w < 7; ++w) {
-            const int n = (w < 3 ? 4 : 0) + carry + (int)((pend >> w) & 1u);
+        for (int w = 0; w < NP; ++w) {
+            const int n = (w < NIN ? 4 : 0) + carry + (int)((pend >> w) & 1u);
             carry = n / 2;
             pend = (pend & ~(1u << w)) | ((uint32_t)(n & 1) << w);
         }
@@ -172,28 +173,28 @@ __host__ __device__ constexpr uint32_t csa_pending(int Q)
     return pend;
 }
 
+template <int NIN, int NP>
 struct CsaAcc {
-    uint32_t S[7], P[7];
+    uint32_t S[NP], P[NP];
 
     __device__ __forceinline__ void clear()
     {
 #pragma unroll
-        for (int w = 0; w < 7; ++w) S[w] = P[w] = 0u;
+        for (int w = 0; w < NP; ++w) S[w] = P[w] = 0u;
     }
 
     template <int Q, int W, int NC>
-    __device__ __forceinline__ void weight(const uint32_t (&x0)[4], const uint32_t (&x1)[4], const uint32_t (&x2)[4],
-                                           const uint32_t (&cin)[NC > 0 ? NC : 1])
+    __device__ __forceinline__ void weight(const uint32_t (&x)[NIN][4], const uint32_t (&cin)[NC > 0 ? NC : 1])
     {
-        constexpr bool pend = ((csa_pending(Q) >> W) & 1u) != 0;
-        constexpr int NIN = W < 3 ? 4 : 0;
-        constexpr int N = NIN + NC + (pend ? 1 : 0);
+        constexpr bool pend = ((csa_pending(Q, NIN, NP) >> W) & 1u) != 0;
+        constexpr int NI = W < NIN ? 4 : 0;
+        constexpr int N = NI + NC + (pend ? 1 : 0);
         constexpr int NF = N / 2;
         uint32_t bag[N > 0 ? N : 1];
 #pragma unroll
-        for (int i = 0; i < NIN; ++i) bag[i] = W == 0 ? x0[i] : W == 1 ? x1[i] : x2[i];
+        for (int i = 0; i < NI; ++i) bag[i] = x[W < NIN ? W : 0][i];
 #pragma unroll
-        for (int i = 0; i < NC; ++i) bag[NIN + i] = cin[i];
+        for (int i = 0; i < NC; ++i) bag[NI + i] = cin[i];
         if constexpr (pend) bag[N - 1] = P[W];
         uint32_t cout[NF > 0 ? NF : 1];
 #pragma unroll
@@ -203,26 +204,26 @@ struct CsaAcc {
             cout[i] = lop3<kMaj3>(sw, bag[2 * i], bag[2 * i + 1]);
         }
         if constexpr ((N & 1) != 0) P[W] = bag[N - 1];
-        if constexpr (W + 1 < 7) weight<Q, W + 1, NF>(x0, x1, x2, cout);
+        if constexpr (W + 1 < NP) weight<Q, W + 1, NF>(x, cout);    // a carry out of the top plane is 0
     }
 
+    // Adds quad Q of the sequence (Q counts from 0 after clear()).
     template <int Q>
-    __device__ __forceinline__ void add(const uint32_t (&x0)[4], const uint32_t (&x1)[4], const uint32_t (&x2)[4])
+    __device__ __forceinline__ void add(const uint32_t (&x)[NIN][4])
     {
         const uint32_t none[1] = {0u};
-        weight<Q, 0, 0>(x0, x1, x2, none);
+        weight<Q, 0, 0>(x, none);
     }
 
     // The binary counter after NQ quads: the waiting bits rippled into S.
-    template <int NQ, int PL>
-    __device__ __forceinline__ void resolve(uint32_t (&acc)[PL])
+    template <int NQ>
+    __device__ __forceinline__ void resolve(uint32_t (&acc)[NP])
     {
-        static_assert(PL == 7, "seven planes hold the count of four quads");
-        constexpr uint32_t pend = csa_pending(NQ);
+        constexpr uint32_t pend = csa_pending(NQ, NIN, NP);
         uint32_t cy = 0u;
         bool has_cy = false;
 #pragma unroll
-        for (int w = 0; w < 7; ++w) {
+        for (int w = 0; w < NP; ++w) {
             const bool p = ((pend >> w) & 1u) != 0;
             if (p && has_cy) {
                 const uint32_t sw = S[w];
@@ -238,6 +239,9 @@ struct CsaAcc {
         }
     }
 };
+
+// Post-update counts of four quads per lane (<= 96): seven planes.
+using CountAcc = CsaAcc<3, 7>;
 
 // Metropolis update of the four sites of one quad whose rows have x parity
 // PX, from its loaded words: own spins, the other colour's words at the same
@@ -306,7 +310,11 @@ __device__ __forceinline__ uint4 quad_core(uint4 own, uint4 xo, uint4 vyp, uint4
             ns[j] = lop3<kXorOr>(sj, t, m0);
         }
     }
-    if constexpr (WITH_E) acc.template add<Q>(x0, x1, x2);
+    if constexpr (WITH_E) {
+        const uint32_t x[3][4] = {{x0[0], x0[1], x0[2], x0[3]}, {x1[0], x1[1], x1[2], x1[3]},
+                                  {x2[0], x2[1], x2[2], x2[3]}};
+        acc.template add<Q>(x);
+    }
     return make_uint4(ns[0], ns[1], ns[2], ns[3]);
 }
 

@@ -220,7 +220,7 @@ __device__ __forceinline__ void wave_half(const WaveQuad (&wq)[4], uint32_t s, u
     auto draw = [&](const WaveQuad &q) {
         return philox_from2(q.phi1 ^ lo1 ^ rk.k[2], q.plo1, hi0b ^ q.plo0 ^ rk.k[3], lo0b, rk);
     };
-    CsaAcc cs;
+    CountAcc cs;
     cs.clear();
     uint4 r0 = draw(wq[0]);
     uint4 r1 = draw(wq[1]);
@@ -230,7 +230,7 @@ __device__ __forceinline__ void wave_half(const WaveQuad (&wq)[4], uint32_t s, u
     r1 = draw(wq[3]);
     wave_quad<COL, 1 - COL, WITH_E, 2>(wq[2], r0, t0, t1, t2, cs, dep);
     wave_quad<COL, 1 - COL, WITH_E, 3>(wq[3], r1, t0, t1, t2, cs, dep);
-    if constexpr (WITH_E) cs.resolve<4, PL>(acc);
+    if constexpr (WITH_E) cs.resolve<4>(acc);
 }
 
 // External field h = h_num / h_den (Eq. 1 with the field term; the field runs
@@ -249,33 +249,28 @@ __device__ __forceinline__ uint32_t field_mask(uint32_t a0, uint32_t a1, uint32_
                                                const uint32_t (&m)[UA])
 {
     if constexpr (UA == 3) {
-        const uint32_t v = a0 | b0 | m[2];
-        return maj3(a1, b1, v) | (m[2] & maj3(a0, b0, m[1])) | m[0];
+        const uint32_t v = lop3<kOr3>(a0, b0, m[2]);
+        return lop3<kOr3>(lop3<kMaj3>(a1, b1, v), m[2] & lop3<kMaj3>(a0, b0, m[1]), m[0]);
     } else {
         static_assert(UA == 4, "always-accept boundary 3 or 4");
-        const uint32_t z = maj3(a0, b0, m[3]);
-        return maj3(a1, b1, z) | (m[2] & (a1 | b1 | maj3(a0, b0, m[1]))) | m[0];
+        const uint32_t z = lop3<kMaj3>(a0, b0, m[3]);
+        const uint32_t w = lop3<kOr3>(a1, b1, lop3<kMaj3>(a0, b0, m[1]));
+        return lop3<kOr3>(lop3<kMaj3>(a1, b1, z), m[2] & w, m[0]);
     }
 }
 
-// acc += number of set bits per lane among four words (both counters bit-sliced).
-template <int PL>
-__device__ __forceinline__ void acc_add_count4(uint32_t (&acc)[PL], uint32_t w0, uint32_t w1, uint32_t w2,
-                                               uint32_t w3)
-{
-    uint32_t s1, c1;
-    full_add(w0, w1, w2, s1, c1);
-    uint32_t A[5] = {s1 ^ w3, c1 ^ (s1 & w3), c1 & (s1 & w3), 0u, 0u};
-    acc_add_sum5<PL>(acc, A);
-}
+// Up-spin counts of the eight quads a lane updates in one sweep (<= 32).
+constexpr int kPlanesM = 6;
+using UpAcc = CsaAcc<1, kPlanesM>;
 
 // Metropolis update of one quad in the field (L = 8): the flip mask per spin
 // value from field_mask, selected per lane by the spin bit; WITH_E adds the
-// post-update unsatisfied-bond counts to acc, WITH_M the up spins to accM.
-template <int COL, int PX, bool WITH_E, bool WITH_M, int UA0, int UA1, int PL, int PLM>
+// post-update unsatisfied-bond counts to ce (as quad Q of the half), WITH_M
+// the new spins to cm (as quad QM of the sweep).
+template <int COL, int PX, bool WITH_E, bool WITH_M, int UA0, int UA1, int Q, int QM>
 __device__ __forceinline__ void wave_quad_field(const WaveQuad &q, uint4 r, const uint64_t (&n0)[UA0],
-                                                const uint64_t (&n1)[UA1], uint32_t (&acc)[PL],
-                                                uint32_t (&accM)[PLM], uint32_t dep)
+                                                const uint64_t (&n1)[UA1], CountAcc &ce, UpAcc &cm,
+                                                uint32_t dep)
 {
     constexpr int H4 = 256 * 4, N4 = 512 * 4;
     constexpr int C4 = COL * H4, O4 = (1 - COL) * H4;
@@ -302,50 +297,49 @@ __device__ __forceinline__ void wave_quad_field(const WaveQuad &q, uint4 r, cons
     const uint32_t jy[4] = {jcy.x, jcy.y, jcy.z, jcy.w}, jym[4] = {joy.x, joy.y, joy.z, joy.w};
     const uint32_t jz[4] = {jcz.x, jcz.y, jcz.z, jcz.w}, jzm[4] = {joz.x, joz.y, joz.z, joz.w};
     const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-    uint32_t ns[4], x0[4], x1[4], x2[4];
+    uint32_t ns[4], x[3][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t sj = sv[j];
-        const uint32_t e0 = sj ^ nxp[j] ^ jx[j];
-        const uint32_t e1 = sj ^ nxm[j] ^ jxm[j];
-        const uint32_t e2 = sj ^ ny[j] ^ jy[j];
-        const uint32_t e3 = sj ^ my[j] ^ jym[j];
-        const uint32_t e4 = sj ^ nz[j] ^ jz[j];
-        const uint32_t e5 = sj ^ mz[j] ^ jzm[j];
-        uint32_t a0, a1, b0, b1;
-        full_add(e0, e1, e2, a0, a1);
-        full_add(e3, e4, e5, b0, b1);
+        const uint32_t e0 = lop3<kXor3>(sj, nxp[j], jx[j]);
+        const uint32_t e1 = lop3<kXor3>(sj, nxm[j], jxm[j]);
+        const uint32_t e2 = lop3<kXor3>(sj, ny[j], jy[j]);
+        const uint32_t e3 = lop3<kXor3>(sj, my[j], jym[j]);
+        const uint32_t e4 = lop3<kXor3>(sj, nz[j], jz[j]);
+        const uint32_t e5 = lop3<kXor3>(sj, mz[j], jzm[j]);
+        const uint32_t a0 = lop3<kXor3>(e0, e1, e2), a1 = lop3<kMaj3>(e0, e1, e2);
+        const uint32_t b0 = lop3<kXor3>(e3, e4, e5), b1 = lop3<kMaj3>(e3, e4, e5);
         uint32_t m0[UA0], m1[UA1];
 #pragma unroll
         for (int u = 0; u < UA0; ++u) m0[u] = below_mask(rr[j], n0[u]);
 #pragma unroll
         for (int u = 0; u < UA1; ++u) m1[u] = below_mask(rr[j], n1[u]);
         const uint32_t F0 = field_mask<UA0>(a0, a1, b0, b1, m0), F1 = field_mask<UA1>(a0, a1, b0, b1, m1);
-        ns[j] = (sj & ~F1) | (~sj & F0);                // s ^ f with f = S > 0 ? F1 : F0
+        ns[j] = lop3<kSelNot>(sj, F1, F0);              // s ^ f with f = S > 0 ? F1 : F0
         if constexpr (WITH_E) {
             const uint32_t f = sj ^ ns[j];
-            const uint32_t u0 = a0 ^ b0;
-            uint32_t u1, u2;
-            full_add(a1, b1, a0 & b0, u1, u2);
-            x0[j] = u0;
-            x1[j] = u1 ^ (f & ~u0);
-            x2[j] = u2 ^ (f & ~(u0 & u1));
+            const uint32_t u0 = a0 ^ b0, c0 = a0 & b0;
+            const uint32_t u1 = lop3<kXor3>(a1, b1, c0), u2 = lop3<kMaj3>(a1, b1, c0);
+            x[0][j] = u0;
+            x[1][j] = lop3<kXorAndN>(u1, f, u0);
+            x[2][j] = lop3<kXorAndN>(u2, f, u0 & u1);
         }
     }
     sts4<C4>(q.s, make_uint4(ns[0], ns[1], ns[2], ns[3]));
-    if constexpr (WITH_E) {
-        uint32_t A[5];
-        quad_sum(x0, x1, x2, A);
-        acc_add_sum5<PL>(acc, A);
+    if constexpr (WITH_E) ce.template add<Q>(x);
+    if constexpr (WITH_M) {
+        const uint32_t up[1][4] = {{ns[0], ns[1], ns[2], ns[3]}};
+        cm.template add<QM>(up);
     }
-    if constexpr (WITH_M) acc_add_count4<PLM>(accM, ns[0], ns[1], ns[2], ns[3]);
 }
 
-template <int COL, bool WITH_E, bool WITH_M, int UA0, int UA1, int PL, int PLM>
+// Half-sweep of colour COL in the field.  With WITH_E, acc receives the lane's
+// post-update counts of its 16 sites; with WITH_M the new spins go to cm as
+// quads 4 COL .. 4 COL + 3 of the sweep.
+template <int COL, bool WITH_E, bool WITH_M, int UA0, int UA1>
 __device__ __forceinline__ void wave_half_field(const WaveQuad (&wq)[4], uint32_t s, uint32_t ctag,
                                                 const RoundKeys &rk, const uint64_t (&n0)[UA0],
-                                                const uint64_t (&n1)[UA1], uint32_t (&acc)[PL],
-                                                uint32_t (&accM)[PLM])
+                                                const uint64_t (&n1)[UA1], uint32_t (&acc)[7], UpAcc &cm)
 {
     const uint32_t dep = opaque_zero();
     const uint32_t lo1 = kM1 * s, n0r = __umulhi(kM1, s) ^ ctag ^ rk.k[0];
@@ -353,14 +347,18 @@ __device__ __forceinline__ void wave_half_field(const WaveQuad (&wq)[4], uint32_
     auto draw = [&](const WaveQuad &q) {
         return philox_from2(q.phi1 ^ lo1 ^ rk.k[2], q.plo1, hi0b ^ q.plo0 ^ rk.k[3], lo0b, rk);
     };
+    constexpr int QB = 4 * COL;
+    CountAcc ce;
+    ce.clear();
     uint4 r0 = draw(wq[0]);
     uint4 r1 = draw(wq[1]);
-    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[0], r0, n0, n1, acc, accM, dep);
+    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, 0, QB + 0>(wq[0], r0, n0, n1, ce, cm, dep);
     r0 = draw(wq[2]);
-    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[1], r1, n0, n1, acc, accM, dep);
+    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, 1, QB + 1>(wq[1], r1, n0, n1, ce, cm, dep);
     r1 = draw(wq[3]);
-    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[2], r0, n0, n1, acc, accM, dep);
-    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, PL, PLM>(wq[3], r1, n0, n1, acc, accM, dep);
+    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, 2, QB + 2>(wq[2], r0, n0, n1, ce, cm, dep);
+    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, 3, QB + 3>(wq[3], r1, n0, n1, ce, cm, dep);
+    if constexpr (WITH_E) ce.resolve<4>(acc);
 }
 
 // Unsatisfied-bond totals of the warp's two slots: each half-warp sums its
@@ -466,6 +464,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     constexpr int UA0 = FLD == 43 ? 4 : 3, UA1 = FLD == 34 ? 4 : 3;
     constexpr int PL = planes_for(24 * 4);          // counter planes of four quads (<= 96)
     constexpr int PLM = planes_for(32);             // up spins of eight quads (<= 32)
+    static_assert(PL == 7 && PLM == kPlanesM, "counter planes of the carry-save counters");
     int32_t *const energy_log = LOG ? a.energy_log : nullptr;
     uint32_t *const swap_log = LOG ? a.swap_log : nullptr;
     const int NT = (int)a.NT;
@@ -557,14 +556,17 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
 #pragma unroll
         for (int p = 0; p < PLM; ++p) accM[p] = 0;
         if constexpr (F) {
+            UpAcc cm;
+            cm.clear();
             if (needE) {
-                if (act) wave_half_field<0, false, true, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, accM);
+                if (act) wave_half_field<0, false, true, UA0, UA1>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, cm);
                 __syncwarp();
-                if (act) wave_half_field<1, true, true, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, accM);
+                if (act) wave_half_field<1, true, true, UA0, UA1>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, cm);
+                cm.resolve<8>(accM);
             } else {
-                if (act) wave_half_field<0, false, false, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, accM);
+                if (act) wave_half_field<0, false, false, UA0, UA1>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, cm);
                 __syncwarp();
-                if (act) wave_half_field<1, false, false, UA0, UA1, PL, PLM>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, accM);
+                if (act) wave_half_field<1, false, false, UA0, UA1>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, cm);
             }
         } else {
             if (act) wave_half<0, false, PL>(wq, (uint32_t)s, tag0, a.rk, t0, t1, t2, acc);
