@@ -113,7 +113,8 @@ __device__ __forceinline__ bool wave_wait(uint64_t *bar, uint32_t parity, volati
 }
 
 // (a & ~m) | (b & m): one LOP3.
-__device__ __forceinline__ uint32_t mux(uint32_t a, uint32_t b, uint32_t m) { return (a & ~m) | (b & m); }
+__device__ __forceinline__ uint32_t mux(uint32_t a, uint32_t b, uint32_t m) { return lop3<0xD8u>(a, b, m); }
+static_assert((((0xF0u & ~0xAAu) | (0xCCu & 0xAAu)) & 0xFFu) == 0xD8u, "mux truth table");
 
 // Per-quad constants of the lane: shared-window byte addresses of the words
 // the quad reads (the colour and direction of each word are immediate offsets
@@ -376,15 +377,18 @@ __device__ __forceinline__ void wave_reduce(const uint32_t (&acc)[PL], int lane,
     for (int p = 0; p < PT; ++p) v[p] = p < PL ? acc[p] : 0u;
 #pragma unroll
     for (int lv = 0; lv < 4; ++lv) {
+        // planes 0 .. PL + lv - 1 hold the partial sums; the next one is zero
+        // in both lanes and receives only the carry
         uint32_t cy = 0;
 #pragma unroll
-        for (int p = 0; p < PL + lv + 1; ++p) {
+        for (int p = 0; p < PL + lv; ++p) {
             const uint32_t o = __shfl_xor_sync(kFull, v[p], 1 << lv);
             uint32_t s2, c2;
             full_add(v[p], o, cy, s2, c2);
             v[p] = s2;
             cy = c2;
         }
+        v[PL + lv] = cy;
     }
     const int t = lane & 15;
     uint32_t x = 0;
