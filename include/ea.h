@@ -442,11 +442,13 @@ typedef struct ea_tp ea_tp;
 typedef struct {
     uint32_t L;               /* as ea_config (ea_supported_L) */
     uint32_t n_real;          /* R >= 1 realizations */
-    uint32_t n_temps;         /* 1 <= NT <= 32 */
+    uint32_t n_temps;         /* 1 <= NT <= 64: W = ceil(NT / 32) words per site */
     uint32_t n_copies;        /* C in {1, 2} */
     uint64_t seed;            /* Philox key */
     const uint8_t *bonds;     /* host [R][3][N]: nonzero <=> J = -1 on bond (i, i + e_d); copied */
-    const uint32_t *spins0;   /* host [R][C][N]: bit t <=> S = +1 in slot t; bits >= NT ignored; copied */
+    const uint32_t *spins0;   /* host [R][C][W][N]: bit b of word w <=> S = +1 in slot 32 w + b (the
+                                 paper's several integer cubes, Sec. 3.2); bits of slots >= NT ignored;
+                                 copied */
     const uint32_t *metro;    /* host [NT][3] as ea_config; copied */
     const uint32_t *swapt;    /* host [NT-1][swap_len] as ea_config; copied */
     uint32_t swap_len;
@@ -464,26 +466,32 @@ int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out);
 /* n_sweeps sweeps, each followed by a swap pass iff swap_every > 0 and
  * (s + 1) % swap_every == 0 (s global), in one kernel launch.  DEVICE outputs,
  * each may be NULL: energy_log [n_sweeps][R][NT][C] int32 (energies by slot
- * after each sweep and its pass), swap_log [passes][R][C] uint32 (bit p =
- * pair p accepted).  Asynchronous on the context's stream. */
+ * after each sweep and its pass), swap_log [passes][R][C][W] uint32 (bit b of
+ * word w = pair 32 w + b accepted).  One launch for the whole call when W = 1
+ * and the unit is not split into slot groups; otherwise two launches per swap
+ * interval (the groups' sweeps, then the merge with the pass).  Asynchronous
+ * on the context's stream. */
 int ea_tp_sweep(ea_tp *tp, uint32_t n_sweeps, uint32_t swap_every, int32_t *energy_log,
                 uint32_t *swap_log);
-/* Copies the state to DEVICE buffers, each may be NULL: spins [R][C][N] (bit t
- * = slot t, bits >= NT zero), energies [R][NT][C] int32.  Asynchronous. */
+/* Copies the state to DEVICE buffers, each may be NULL: spins [R][C][W][N]
+ * (bit b of word w = slot 32 w + b, bits of slots >= NT zero), energies
+ * [R][NT][C] int32.  Asynchronous. */
 int ea_tp_read(ea_tp *tp, uint32_t *spins, int32_t *energies);
 /* Global sweep and pass indices, the number of kernels launched so far and
  * the number of slot groups per (realization, copy) unit (each pointer may be
  * NULL). */
 int ea_tp_info(const ea_tp *tp, uint64_t *sweep_index, uint64_t *pass_index, uint64_t *launches,
                uint32_t *split);
-/* Splits each (realization, copy) unit into k slot groups (k a power of two,
- * 1 <= k <= min(32, NT); groups of ceil(NT / k) slots, empty ones dropped), one
- * CTA each: slots do not interact between swap passes, so every group sweeps
- * its own slots up to the next pass and a merge launch then combines the groups
- * and runs the pass.  Results do not depend on k.  ea_tp_create picks the
- * largest k <= 8 with R * C * k CTAs within one per SM (1 when R * C fills
- * the GPU).  May allocate device memory (k more copies of the spins, one per group);
- * synchronises the stream when it frees some.  EA_EINVAL for another k. */
+/* Splits each word of each (realization, copy) unit into k slot groups (k a
+ * power of two, 1 <= k <= min(32, NT); groups of ceil(min(NT, 32) / k) slots,
+ * the ones empty in the first word dropped), one CTA each: slots do not
+ * interact between swap passes, so every group sweeps its own slots up to the
+ * next pass and a merge launch then combines the groups and runs the pass.
+ * Results do not depend on k.  ea_tp_create picks the largest k <= 8 with
+ * R * C * W * k CTAs within one per SM (1 when R * C * W fills the GPU).  May
+ * allocate device memory (one word per site and group); synchronises the
+ * stream when it frees some.  EA_EINVAL for another k.  ea_tp_info reports the
+ * groups in use per unit (W times the groups per word). */
 int ea_tp_set_split(ea_tp *tp, uint32_t k);
 /* Synchronises the context's stream and frees its device memory. */
 void ea_tp_destroy(ea_tp *tp);

@@ -680,26 +680,28 @@ def ea_pt_swap_static(spins, energies, swapt, L, n_groups, n_temps, n_copies, se
 
 class TPEnsemble:
     """Temperature-packed ensemble (an ea_tp): R realizations x C copies of an L^3
-    lattice, one word per (realization, copy, site) with bit t = temperature slot t
-    (NT <= 32).  Realization r draws the random numbers of word-group r of the
-    realization-packed form (its bit 0), so it follows the trajectory of
-    realization 32r of an Ensemble with the same inputs.
+    lattice, W = ceil(NT / 32) words per (realization, copy, site) with bit b of
+    word w = temperature slot 32 w + b (NT <= 64).  Realization r draws the random
+    numbers of word-group r of the realization-packed form (its bit 0), so it
+    follows the trajectory of realization 32r of an Ensemble with the same inputs.
 
-    bonds: [R][3][N] uint8 (1 <=> J = -1); spins: [R][C][N] uint32 (bit t = slot t).
-    real_base: global index of realization 0 in the random-number counters."""
+    bonds: [R][3][N] uint8 (1 <=> J = -1); spins: [R][C][N] uint32 (bit t = slot t)
+    when W = 1, [R][C][W][N] otherwise.  real_base: global index of realization 0
+    in the random-number counters."""
 
     def __init__(self, L, R, NT, C, seed, bonds, spins, metro, swapt, stream=None, real_base=0):
         import torch
         self.lib = load_library()
         self.L, self.R, self.NT, self.C = int(L), int(R), int(NT), int(C)
         self.N = self.L ** 3
+        self.W = max(1, -(-self.NT // 32))
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.handle, self.stream = _stream_handle(stream)
         b = np.ascontiguousarray(bonds, np.uint8)
         sp = np.ascontiguousarray(spins, np.uint32)
         m = np.ascontiguousarray(metro, np.uint32)
         w = np.ascontiguousarray(swapt, np.uint32)
-        assert b.shape == (self.R, 3, self.N) and sp.shape == (self.R, self.C, self.N)
+        assert b.shape == (self.R, 3, self.N) and sp.shape == self._spin_shape()
         assert m.shape == (self.NT, 3)
         self.swap_len = w.shape[1] if w.ndim == 2 else 0
         cfg = _TpConfig(self.L, self.R, self.NT, self.C, int(seed), b.ctypes.data, sp.ctypes.data,
@@ -708,6 +710,9 @@ class TPEnsemble:
         h = ctypes.c_void_p(None)
         _check(self.lib.ea_tp_create(ctypes.byref(cfg), self.handle, ctypes.byref(h)), "ea_tp_create")
         self.ctx = h
+
+    def _spin_shape(self):
+        return (self.R, self.C, self.N) if self.W == 1 else (self.R, self.C, self.W, self.N)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -728,11 +733,11 @@ class TPEnsemble:
 
     @property
     def split(self) -> int:
-        """Slot groups (CTAs) per (realization, copy) unit."""
+        """Slot groups (CTAs) per (realization, copy) unit, over all its words."""
         return self._info()[3]
 
     def set_split(self, k: int):
-        """ea_tp_set_split: k slot groups per unit (a power of two <= min(32, NT))."""
+        """ea_tp_set_split: k slot groups per word of a unit (a power of two <= min(32, NT))."""
         _check(self.lib.ea_tp_set_split(self.ctx, int(k)), "ea_tp_set_split")
 
     @property
@@ -755,7 +760,8 @@ class TPEnsemble:
 
     def sweep(self, n_sweeps: int, swap_every: int, energy_log=False, swap_log=False) -> dict:
         """ea_tp_sweep; returns the requested logs as device tensors:
-        energy_log [n][R][NT][C] int32, swap_log [passes][R][C] int32 (bit p = pair p)."""
+        energy_log [n][R][NT][C] int32, swap_log [passes][R][C] int32 (bit p = pair p)
+        when W = 1, [passes][R][C][W] (bit b of word w = pair 32 w + b) otherwise."""
         import torch
         out = {}
         el = sl = None
@@ -763,17 +769,18 @@ class TPEnsemble:
             el = torch.empty((n_sweeps, self.R, self.NT, self.C), dtype=torch.int32, device=self.device)
             out["energy_log"] = el
         if swap_log:
-            sl = torch.zeros((self.n_passes(n_sweeps, swap_every), self.R, self.C), dtype=torch.int32,
-                             device=self.device)
+            shape = (self.n_passes(n_sweeps, swap_every), self.R, self.C) + ((self.W,) if self.W > 1 else ())
+            sl = torch.zeros(shape, dtype=torch.int32, device=self.device)
             out["swap_log"] = sl
         _check(self.lib.ea_tp_sweep(self.ctx, int(n_sweeps), int(swap_every), _ptr(el),
                                     _ptr(sl) if sl is not None and sl.numel() else None), "ea_tp_sweep")
         return out
 
     def read(self):
-        """(spins [R][C][N] int32 view of the words, energies [R][NT][C] int32), device tensors."""
+        """(spins [R][C][N] ([R][C][W][N] when W > 1) int32 view of the words,
+        energies [R][NT][C] int32), device tensors."""
         import torch
-        sp = torch.empty((self.R, self.C, self.N), dtype=torch.int32, device=self.device)
+        sp = torch.empty(self._spin_shape(), dtype=torch.int32, device=self.device)
         en = torch.empty((self.R, self.NT, self.C), dtype=torch.int32, device=self.device)
         _check(self.lib.ea_tp_read(self.ctx, _ptr(sp), _ptr(en)), "ea_tp_read")
         return sp, en

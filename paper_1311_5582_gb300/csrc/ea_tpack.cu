@@ -31,6 +31,12 @@
 // split into slot groups (slots do not interact between swap passes): one CTA
 // per group sweeps only its slots' bits up to the next pass and stores them in
 // its slice, and k_tp_merge ORs the slices and runs the pass.
+//
+// More than 32 temperatures take several words per site (the paper's several
+// integer cubes, Sec. 3.2): word w holds slots 32w .. 32w + 31.  Slot groups
+// then never straddle a word, every group sweeps its word as above, and the
+// merge runs the pass over all words: the bit permutation above is a shift and
+// an addition of 32W-bit integers, whose carries cross the words.
 #include <new>
 
 #include "../../include/ea.h"
@@ -39,16 +45,17 @@
 namespace ea {
 namespace {
 
-constexpr int kTpMaxTemps = 32;
+constexpr int kTpMaxTemps = 64;      // two words per site
+constexpr int kTpMaxWords = kTpMaxTemps / 32;
 constexpr int kTpThreads = 1024;   // at most 64 registers a thread
 
 struct TpLaunch {
-    uint32_t *spins;            // [R][C][2][H] by slot bit
+    uint32_t *spins;            // [R][C][W][2][H]: word w, bit b = slot 32 w + b
     const uint32_t *bonds;      // [R][3][2][H], words 0 (J = +1) or ~0 (J = -1)
     const uint64_t *nthr;       // [NT][3]: 2^64 - metro threshold
     const uint32_t *swapt;      // [NT-1][swap_len]
     uint32_t swap_len;
-    int32_t *energy;            // [R][C][32] by slot
+    int32_t *energy;            // [R][C][32 W] by slot
     uint32_t R, NT, C;
     RoundKeys rk;
     uint64_t s0;                // global index of the first sweep
@@ -56,12 +63,15 @@ struct TpLaunch {
     uint64_t P0;                // global index of the first swap pass of this call
     uint32_t pass_local0;       // row of swap_log for that pass
     int32_t *energy_log;        // [n_sweeps][R][NT][C] or null
-    uint32_t *swap_log;         // [passes][R][C] or null
-    // slot split: CTA (unit, blockIdx.y) owns slots [y * spg, (y + 1) * spg) and
-    // writes them to slices[y]; null = one CTA per unit owning every slot
+    uint32_t *swap_log;         // [passes][R][C][W] (bit b of word w = pair 32 w + b) or null
+    // slot split: CTA (unit, y) owns slots [32 w + j spg, 32 w + (j + 1) spg) of
+    // word w = y / gpw (j = y % gpw, clipped to the word's slots) and writes them
+    // to slices[y]; null = one CTA per unit owning every slot (W = 1)
     uint32_t *slices;           // [nsplit][R][C][2][H]
     uint32_t spg;               // slots per group
-    uint32_t nsplit;            // groups (gridDim.y)
+    uint32_t gpw;               // groups per word
+    uint32_t nsplit;            // groups (gridDim.y) = W gpw
+    uint32_t W;                 // words per site = ceil(NT / 32)
     uint32_t r_base;            // global index of realization 0 in the random-number counters
 };
 
@@ -146,17 +156,18 @@ __device__ __forceinline__ void tp_mask_bits(uint32_t (&m0)[4], uint32_t (&m1)[4
     }
 }
 
-// One half-sweep (colour col) of one unit, slots [t_lo, t_hi) (omask = their
-// bits; the other bits of the words are left as they are).  Thread (quad group
+// One half-sweep (colour col) of one word of a unit, slots [t_lo, t_hi) of the
+// word whose bit 0 is slot wb (omask = their bits; the other bits of the words
+// are left as they are).  Thread (quad group
 // qg, site i) takes quads qg, qg + nqg, ...; the trip count qper is the same
 // for every thread so that the whole warp takes part in each shuffle.  MODE 0: update
 // without counting; 1: update and count the post-update unsatisfied bonds of
 // the (colour-1) sites; 2: count the current unsatisfied bonds, no update.
 template <int L, int MODE>
 __device__ __forceinline__ void tp_half(uint32_t *S, const uint32_t *J, const uint64_t *nthr, int col,
-                                        int qg, int nqg, int qper, int i, int t_lo, int t_hi, uint32_t omask,
-                                        uint32_t s, uint32_t r, uint32_t ctag, const RoundKeys &rk,
-                                        uint32_t (&acc)[kPlanes])
+                                        int qg, int nqg, int qper, int i, int t_lo, int t_hi, int wb,
+                                        uint32_t omask, uint32_t s, uint32_t r, uint32_t ctag,
+                                        const RoundKeys &rk, uint32_t (&acc)[kPlanes])
 {
     constexpr int Q = Geo<L>::Q, H = Geo<L>::H;
     for (int j = 0; j < qper; ++j) {
@@ -169,7 +180,7 @@ __device__ __forceinline__ void tp_half(uint32_t *S, const uint32_t *J, const ui
             if (inq) {
                 for (int t = t_lo + i; t < t_hi; t += 4) {
                     const uint4 v = philox((uint32_t)q, ctag | (uint32_t)t, s, r, rk);
-                    tp_mask_bits(m0, m1, m2, v, nthr + 3 * t, t);
+                    tp_mask_bits(m0, m1, m2, v, nthr + 3 * t, t - wb);
                 }
             }
 #pragma unroll
@@ -254,7 +265,7 @@ k_tp_sweep(TpLaunch a, int recompute_only)
     constexpr int N = Gm::N, Q = Gm::Q;
     extern __shared__ __align__(16) uint32_t tp_smem[];
     __shared__ uint64_t nthr[kTpMaxTemps * 3];
-    __shared__ int E[kTpMaxTemps];
+    __shared__ int E[32];                               // by bit of the word this CTA updates
     __shared__ uint32_t smask;
     uint32_t *S = tp_smem;
     const uint32_t unit = blockIdx.x;
@@ -264,13 +275,24 @@ k_tp_sweep(TpLaunch a, int recompute_only)
     const int tid = threadIdx.x, nthr_cta = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int i = tid & 3, qg = tid >> 2, nqg = nthr_cta >> 2;
     const int qper = (Q + nqg - 1) / nqg;
-    const uint32_t valid = NT >= 32 ? kFull : ((1u << NT) - 1u);
-    // slots this CTA updates
-    const int t_lo = a.slices ? (int)(blockIdx.y * a.spg) : 0;
-    const int t_hi = a.slices ? min(NT, t_lo + (int)a.spg) : NT;
-    const uint32_t own = (t_hi >= 32 ? kFull : ((1u << t_hi) - 1u)) & ~((1u << t_lo) - 1u);
+    // the word of the unit this CTA updates (bit 0 = slot wb) and its slots [t_lo, t_hi)
+    int w = 0, t_lo = 0, t_hi = NT;
+    if (a.slices) {
+        w = (int)(blockIdx.y / a.gpw);
+        t_lo = 32 * w + (int)((blockIdx.y % a.gpw) * a.spg);
+        t_hi = max(t_lo, min(min(NT, 32 * w + 32), t_lo + (int)a.spg));
+    } else if (recompute_only) {
+        w = (int)blockIdx.y;
+        t_lo = 32 * w;
+        t_hi = min(NT, t_lo + 32);
+    }
+    const int wb = 32 * w, nw = min(32, NT - wb);
+    const uint32_t valid = nw >= 32 ? kFull : ((1u << nw) - 1u);
+    const int b_lo = t_lo - wb, b_hi = t_hi - wb;       // bits of the word, 0 <= b_lo <= b_hi <= 32
+    const uint32_t own = (b_hi >= 32 ? kFull : ((1u << b_hi) - 1u)) & ~((1u << b_lo) - 1u);
+    int32_t *const gE = a.energy + (size_t)unit * kLanes * a.W + wb;
 
-    uint32_t *gS = a.spins + (size_t)unit * N;
+    uint32_t *gS = a.spins + ((size_t)unit * a.W + w) * N;
     const uint32_t *gJ = a.bonds + (size_t)r * 3 * N;
     for (int w = tid; w < N / 4; w += nthr_cta)
         reinterpret_cast<uint4 *>(S)[w] = __ldcg(reinterpret_cast<const uint4 *>(gS) + w);
@@ -282,17 +304,17 @@ k_tp_sweep(TpLaunch a, int recompute_only)
         J = Js;
     }
     for (int x = tid; x < NT * 3; x += nthr_cta) nthr[x] = a.nthr[x];
-    if (tid < kTpMaxTemps) E[tid] = -3 * N;
+    if (tid < 32) E[tid] = -3 * N;
     __syncthreads();
 
     uint32_t acc[kPlanes];
     if (recompute_only) {
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-        tp_half<L, 2>(S, J, nthr, 1, qg, nqg, qper, i, 0, NT, valid, 0u, rr, 0u, a.rk, acc);
-        tp_reduce_energy(acc, E, lane, 0, NT);
+        tp_half<L, 2>(S, J, nthr, 1, qg, nqg, qper, i, 0, 0, wb, valid, 0u, rr, 0u, a.rk, acc);
+        tp_reduce_energy(acc, E, lane, 0, nw);
         __syncthreads();
-        if (tid < kTpMaxTemps) a.energy[(size_t)unit * kLanes + tid] = tid < NT ? E[tid] : 0;
+        if (tid < 32) gE[tid] = tid < nw ? E[tid] : 0;
         return;
     }
 
@@ -305,19 +327,19 @@ k_tp_sweep(TpLaunch a, int recompute_only)
         const bool swap_s = swap_cd.step();             // a pass follows sweep s
         const bool swap_now = swap_s && NT > 1;
         const bool needE = swap_now || a.energy_log != nullptr || (n + 1 == a.n_sweeps);
-        if (needE && tid < kTpMaxTemps) E[tid] = -3 * N;
-        tp_half<L, 0>(S, J, nthr, 0, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, rr, tag0, a.rk, acc);
+        if (needE && tid < 32) E[tid] = -3 * N;
+        tp_half<L, 0>(S, J, nthr, 0, qg, nqg, qper, i, t_lo, t_hi, wb, own, (uint32_t)s, rr, tag0, a.rk, acc);
         __syncthreads();
         if (needE) {
 #pragma unroll
             for (int p = 0; p < kPlanes; ++p) acc[p] = 0;
-            tp_half<L, 1>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, rr, tag1, a.rk, acc);
-            tp_reduce_energy(acc, E, lane, t_lo, t_hi);
+            tp_half<L, 1>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, wb, own, (uint32_t)s, rr, tag1, a.rk, acc);
+            tp_reduce_energy(acc, E, lane, b_lo, b_hi);
         } else {
-            tp_half<L, 0>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, own, (uint32_t)s, rr, tag1, a.rk, acc);
+            tp_half<L, 0>(S, J, nthr, 1, qg, nqg, qper, i, t_lo, t_hi, wb, own, (uint32_t)s, rr, tag1, a.rk, acc);
         }
         __syncthreads();
-        if (swap_now) {
+        if (swap_now) {                                 // one word (W = 1): the pass in this kernel
             if (warp == 0) {
                 // lane t: energy of slot t and the acceptance bound of pair t
                 const int e = lane < NT ? E[lane] : 0;
@@ -359,8 +381,8 @@ k_tp_sweep(TpLaunch a, int recompute_only)
             ++P;
             ++pass_local;
         }
-        if (a.energy_log != nullptr && tid >= t_lo && tid < t_hi)
-            a.energy_log[(((size_t)n * a.R + r) * NT + tid) * a.C + c] = E[tid];
+        if (a.energy_log != nullptr && tid >= b_lo && tid < b_hi)
+            a.energy_log[(((size_t)n * a.R + r) * NT + wb + tid) * a.C + c] = E[tid];
         // E is rewritten at the top of the next sweep only by the thread that logged it
     }
     __syncthreads();
@@ -375,72 +397,123 @@ k_tp_sweep(TpLaunch a, int recompute_only)
         for (int w = tid; w < N / 4; w += nthr_cta)
             __stcg(reinterpret_cast<uint4 *>(gS) + w, reinterpret_cast<const uint4 *>(S)[w]);
     }
-    if (tid >= t_lo && tid < t_hi) a.energy[(size_t)unit * kLanes + tid] = E[tid];
-    else if (!a.slices && tid < kTpMaxTemps) a.energy[(size_t)unit * kLanes + tid] = 0;
+    if (tid >= b_lo && tid < b_hi) gE[tid] = E[tid];
+    else if (!a.slices && tid < 32) gE[tid] = 0;
 }
 
 // Slot-split form: merges the groups' slices into the unit's words and, with
 // do_swap, runs the swap pass on them (one CTA per unit): warp 0 takes the
-// decision chain as in k_tp_sweep, then every word gets the pass's bit
-// permutation.  elog_row (or null): the energy-log row of the interval's last
-// sweep, rewritten with the energies after the pass.
+// decision chain as in k_tp_sweep (lane t holds slots t and t + 32), then
+// every site gets the pass's bit permutation over its W words.  elog_row (or
+// null): the energy-log row of the interval's last sweep, rewritten with the
+// energies after the pass.
 __global__ void __launch_bounds__(256)
 k_tp_merge(TpLaunch a, int N, int do_swap, uint64_t P, uint32_t pass_local, int32_t *elog_row)
 {
-    __shared__ uint32_t smask;
+    static_assert(kTpMaxWords == 2, "the chain holds two slots a lane");
+    __shared__ uint32_t smask[kTpMaxWords];
     const uint32_t unit = blockIdx.x;
     const uint32_t c = unit % a.C, r = unit / a.C;
     const uint32_t rr = r + a.r_base;                   // realization index of the random numbers
-    const int NT = (int)a.NT, tid = threadIdx.x, lane = tid & 31;
-    const uint32_t valid = NT >= 32 ? kFull : ((1u << NT) - 1u);
+    const int NT = (int)a.NT, W = (int)a.W, tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
-        int32_t *Eg = a.energy + (size_t)unit * kLanes;
-        const int e = lane < NT ? Eg[lane] : 0;
-        uint32_t m = 0;
-        int mine = e;
+        int32_t *Eg = a.energy + (size_t)unit * kLanes * W;
+        const int e0 = lane < NT ? Eg[lane] : 0;
+        const int e1 = lane + 32 < NT ? Eg[lane + 32] : 0;
+        uint32_t m0 = 0, m1 = 0;
+        int mine0 = e0, mine1 = e1;
         if (do_swap) {
-            int bnd = 0;
+            int bnd0 = 0, bnd1 = 0;
             if (lane + 1 < NT) {
                 const uint4 v = philox((uint32_t)lane << 3, (1u << 24) | (c << 8), (uint32_t)P, rr, a.rk);
-                bnd = accept_bound(a.swapt + (size_t)lane * a.swap_len, a.swap_len, v.x);
+                bnd0 = accept_bound(a.swapt + (size_t)lane * a.swap_len, a.swap_len, v.x);
             }
-            int cur = __shfl_sync(kFull, e, 0);
+            if (lane + 33 < NT) {
+                const uint4 v = philox((uint32_t)(lane + 32) << 3, (1u << 24) | (c << 8), (uint32_t)P, rr, a.rk);
+                bnd1 = accept_bound(a.swapt + (size_t)(lane + 32) * a.swap_len, a.swap_len, v.x);
+            }
+            // sequential pairs 0..NT-2 on the energies carried upward (the word of
+            // a slot is the same for every lane, so each shuffle is warp-wide)
+            int cur = __shfl_sync(kFull, e0, 0);
             for (int p = 0; p + 1 < NT; ++p) {
-                const int nx = __shfl_sync(kFull, e, p + 1);
-                const int bp = __shfl_sync(kFull, bnd, p);
+                const int q = p + 1;
+                const int nx = q < 32 ? __shfl_sync(kFull, e0, q) : __shfl_sync(kFull, e1, q - 32);
+                const int bp = p < 32 ? __shfl_sync(kFull, bnd0, p) : __shfl_sync(kFull, bnd1, p - 32);
                 const bool ok = cur - nx >= bp;
-                if (lane == p) mine = ok ? nx : cur;
+                if (p < 32) {
+                    if (lane == p) mine0 = ok ? nx : cur;
+                    m0 |= (uint32_t)ok << p;
+                } else {
+                    if (lane == p - 32) mine1 = ok ? nx : cur;
+                    m1 |= (uint32_t)ok << (p - 32);
+                }
                 cur = ok ? cur : nx;
-                m |= (uint32_t)ok << p;
             }
-            if (lane == NT - 1) mine = cur;
-            if (lane < NT) Eg[lane] = mine;
-            if (lane == 0 && a.swap_log) a.swap_log[((size_t)pass_local * a.R + r) * a.C + c] = m;
-            if (elog_row && lane < NT) elog_row[((size_t)r * NT + lane) * a.C + c] = mine;
+            if (NT - 1 < 32) {
+                if (lane == NT - 1) mine0 = cur;
+            } else if (lane == NT - 33) {
+                mine1 = cur;
+            }
+            if (lane < NT) Eg[lane] = mine0;
+            if (lane + 32 < NT) Eg[lane + 32] = mine1;
+            if (lane == 0 && a.swap_log) {
+                uint32_t *sl = a.swap_log + (((size_t)pass_local * a.R + r) * a.C + c) * W;
+                sl[0] = m0;
+                if (W > 1) sl[1] = m1;
+            }
+            if (elog_row) {
+                if (lane < NT) elog_row[((size_t)r * NT + lane) * a.C + c] = mine0;
+                if (lane + 32 < NT) elog_row[((size_t)r * NT + lane + 32) * a.C + c] = mine1;
+            }
         }
-        if (lane == 0) smask = m;
+        if (lane == 0) {
+            smask[0] = m0;
+            smask[1] = m1;
+        }
     }
     __syncthreads();
-    const uint32_t M = smask, ends = ~M & valid, starts = ((~M << 1) | 1u) & valid;
+    // the pass on the 32W-bit integer of a site's words: bit t <- bit t + 1 where
+    // pair t was accepted, else the bit at the start of the run of accepted pairs
+    // ending at t (M + (starts & x) carries each run's start bit to its end)
+    const uint32_t M0 = smask[0], M1 = W > 1 ? smask[1] : 0u;
+    const uint32_t valid0 = NT >= 32 ? kFull : ((1u << NT) - 1u);
+    const uint32_t valid1 = W < 2 ? 0u : (NT >= 64 ? kFull : ((1u << (NT - 32)) - 1u));
+    const uint32_t ends0 = ~M0 & valid0, ends1 = ~M1 & valid1;
+    const uint32_t starts0 = ((~M0 << 1) | 1u) & valid0;
+    const uint32_t starts1 = ((~M1 << 1) | (~M0 >> 31)) & valid1;
     const size_t stride = (size_t)gridDim.x * N;
+    const uint32_t gpw = a.gpw;
     const uint32_t *src = a.slices + (size_t)unit * N;
-    uint32_t *dst = a.spins + (size_t)unit * N;
+    uint32_t *dst = a.spins + (size_t)unit * W * N;
     for (int w = tid; w < N; w += blockDim.x) {
-        uint32_t x = 0;
-        for (uint32_t g = 0; g < a.nsplit; ++g) x |= __ldcg(src + g * stride + w);
-        if (do_swap) x = ((x >> 1) & M) | ((M + (starts & x)) & ends);
-        dst[w] = x;
+        uint32_t x0 = 0, x1 = 0;
+        for (uint32_t g = 0; g < gpw; ++g) x0 |= __ldcg(src + g * stride + w);
+        if (W > 1)
+            for (uint32_t g = gpw; g < 2 * gpw; ++g) x1 |= __ldcg(src + g * stride + w);
+        if (do_swap) {
+            const uint32_t sh0 = (x0 >> 1) | (x1 << 31), sh1 = x1 >> 1;
+            const uint32_t s0 = M0 + (starts0 & x0);
+            const uint32_t cy = s0 < M0 ? 1u : 0u;      // carry into slot 32
+            const uint32_t s1 = M1 + (starts1 & x1) + cy;
+            x0 = (sh0 & M0) | (s0 & ends0);
+            x1 = (sh1 & M1) | (s1 & ends1);
+        }
+        dst[w] = x0;
+        if (W > 1) dst[N + w] = x1;
     }
 }
 
-// spins: API [R][C][N] (site order) <-> device [R][C][2][H] (colour-split), bits >= NT cleared on import.
-__global__ void k_tp_import_spins(const uint32_t *api, uint32_t *dev, int L, size_t total, uint32_t valid)
+// spins: API [R][C][W][N] (site order) <-> device [R][C][W][2][H] (colour-split),
+// bits of slots >= NT cleared on import.
+__global__ void k_tp_import_spins(const uint32_t *api, uint32_t *dev, int L, size_t total, int NT, int W)
 {
     const int N = L * L * L, H = N / 2, R = L / 2;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int w = (int)(idx % N);
-        const size_t unit = idx / N;
+        const size_t unit = idx / N;                    // (realization, copy, word)
+        const int nw = NT - 32 * (int)(unit % W);       // slots in this word (>= 1)
+        const uint32_t valid = nw >= 32 ? kFull : ((1u << nw) - 1u);
         const int col = w / H, k = w - col * H;
         const int row = k / R, y = row % L, z = row / L;
         const int site = 2 * k + ((col + y + z) & 1);
@@ -475,15 +548,16 @@ __global__ void k_tp_import_bonds(const uint8_t *api, uint32_t *dev, int L, size
     }
 }
 
-// energies: device [R][C][32] -> API [R][NT][C]
-__global__ void k_tp_export_energy(const int32_t *dev, int32_t *api, uint32_t R, uint32_t NT, uint32_t C)
+// energies: device [R][C][32 W] -> API [R][NT][C]
+__global__ void k_tp_export_energy(const int32_t *dev, int32_t *api, uint32_t R, uint32_t NT, uint32_t C,
+                                   uint32_t W)
 {
     const size_t total = (size_t)R * NT * C;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const uint32_t c = (uint32_t)(idx % C), t = (uint32_t)((idx / C) % NT);
         const size_t r = idx / ((size_t)C * NT);
-        api[idx] = dev[(r * C + c) * kLanes + t];
+        api[idx] = dev[(r * C + c) * kLanes * W + t];
     }
 }
 
@@ -518,7 +592,7 @@ cudaError_t tp_launch_L(const TpLaunch &a, int recompute_only, cudaStream_t st)
     const cudaError_t e = cudaFuncSetAttribute(k_tp_sweep<L, JS>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const dim3 grid(a.R * a.C, a.slices ? a.nsplit : 1);
+    const dim3 grid(a.R * a.C, a.slices ? a.nsplit : (recompute_only ? a.W : 1));
     k_tp_sweep<L, JS><<<grid, tp_threads(L), smem, st>>>(a, recompute_only);
     return cudaGetLastError();
 }
@@ -539,6 +613,7 @@ cudaError_t tp_launch(int L, const TpLaunch &a, int recompute_only, cudaStream_t
 
 struct ea_tp {
     uint32_t L, R, NT, C, N, swap_len;
+    uint32_t W;                    // words per site, ceil(NT / 32)
     cudaStream_t stream;
     uint32_t *d_spins, *d_bonds, *d_swapt;
     uint64_t *d_nthr;
@@ -546,7 +621,8 @@ struct ea_tp {
     uint64_t sweep, pass, launches;
     ea::RoundKeys rk;
     uint32_t r_base;               // ea_tp_config::real_base
-    uint32_t split, spg, nsplit;   // requested groups, slots per group, groups in use
+    uint32_t split, spg, gpw, nsplit;   // requested groups per word, slots per group,
+                                        // groups per word in use, groups in use (W gpw)
     uint32_t *d_slices;            // [nsplit][R][C][N] when nsplit > 1
 };
 
@@ -566,12 +642,16 @@ void tp_free(ea_tp *t)
     delete t;
 }
 
-// Slot groups per unit: k groups of ceil(NT / k) slots (the groups in use are
-// the non-empty ones); slices for them are (re)allocated here.
+// Slot groups per word: k groups of ceil(n0 / k) slots, n0 = min(NT, 32) the
+// slots of the first word (the groups in use are the ones non-empty there; a
+// shorter last word may leave some empty); slices for them are (re)allocated
+// here.  More than one word always takes the slot-group path.
 int tp_apply_split(ea_tp *t, uint32_t k)
 {
-    const uint32_t spg = (t->NT + k - 1) / k;
-    const uint32_t nsplit = (t->NT + spg - 1) / spg;
+    const uint32_t n0 = t->NT < 32 ? t->NT : 32;
+    const uint32_t spg = (n0 + k - 1) / k;
+    const uint32_t gpw = (n0 + spg - 1) / spg;
+    const uint32_t nsplit = t->W * gpw;
     if (t->d_slices && nsplit != t->nsplit) {
         const cudaError_t e = cudaStreamSynchronize(t->stream);
         if (e != cudaSuccess) return tp_cuda_fail(e);
@@ -584,6 +664,7 @@ int tp_apply_split(ea_tp *t, uint32_t k)
     }
     t->split = k;
     t->spg = spg;
+    t->gpw = gpw;
     t->nsplit = nsplit;
     return EA_OK;
 }
@@ -636,16 +717,17 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     t->NT = NT;
     t->C = C;
     t->N = (uint32_t)N;
+    t->W = (NT + 31) / 32;
     t->swap_len = len;
     t->stream = (cudaStream_t)stream;
     t->rk = ea::make_round_keys(cfg->seed);
     t->r_base = cfg->real_base;
-    const size_t n_spin = (size_t)R * C * N, n_bond = (size_t)R * 3 * N;
+    const size_t n_spin = (size_t)R * C * t->W * N, n_bond = (size_t)R * 3 * N;
     EA_TP_TRY(cudaMalloc(&t->d_spins, n_spin * 4));
     EA_TP_TRY(cudaMalloc(&t->d_bonds, n_bond * 4));
     EA_TP_TRY(cudaMalloc(&t->d_swapt, (len ? (size_t)(NT - 1) * len : 1) * 4));
     EA_TP_TRY(cudaMalloc(&t->d_nthr, (size_t)NT * 3 * 8));
-    EA_TP_TRY(cudaMalloc(&t->d_energy, (size_t)R * C * ea::kLanes * 4));
+    EA_TP_TRY(cudaMalloc(&t->d_energy, (size_t)R * C * ea::kLanes * t->W * 4));
     std::vector<uint64_t> nthr((size_t)NT * 3);
     for (size_t x = 0; x < nthr.size(); ++x) nthr[x] = 0ull - (uint64_t)cfg->metro[x];
     cudaStream_t st = t->stream;
@@ -655,9 +737,8 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
                                   cudaMemcpyHostToDevice, st));
     EA_TP_TRY(cudaMalloc(&staging, (n_spin > n_bond ? n_spin : n_bond) * 4));
     EA_TP_TRY(cudaMemcpyAsync(staging, cfg->spins0, n_spin * 4, cudaMemcpyHostToDevice, st));
-    const uint32_t valid = NT >= 32 ? 0xFFFFFFFFu : ((1u << NT) - 1u);
     ea::k_tp_import_spins<<<ea::tp_grid(n_spin), 256, 0, st>>>((const uint32_t *)staging, t->d_spins,
-                                                                (int)L, n_spin, valid);
+                                                                (int)L, n_spin, (int)NT, (int)t->W);
     EA_TP_TRY(cudaGetLastError());
     EA_TP_TRY(cudaMemcpyAsync(staging, cfg->bonds, n_bond, cudaMemcpyHostToDevice, st));
     ea::k_tp_import_bonds<<<ea::tp_grid(n_bond), 256, 0, st>>>((const uint8_t *)staging, t->d_bonds,
@@ -676,6 +757,7 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     a.C = C;
     a.rk = t->rk;
     a.r_base = t->r_base;
+    a.W = t->W;
     EA_TP_TRY(ea::tp_launch((int)L, a, 1, st));
     t->launches = 3;
     // the staging buffer is read by the import kernels: wait before freeing it
@@ -690,7 +772,7 @@ extern "C" int ea_tp_create(const ea_tp_config *cfg, void *stream, ea_tp **out)
     EA_TP_TRY(cudaGetDevice(&dev));
     EA_TP_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     uint32_t k = 1;
-    while (k * 2 <= 8 && k * 2 <= NT && (uint64_t)R * C * (k * 2) <= (uint64_t)sms) k *= 2;
+    while (k * 2 <= 8 && k * 2 <= NT && (uint64_t)R * C * t->W * (k * 2) <= (uint64_t)sms) k *= 2;
     const int rc = tp_apply_split(t, k);
     if (rc != EA_OK) {
         tp_free(t);
@@ -718,6 +800,7 @@ extern "C" int ea_tp_sweep(ea_tp *t, uint32_t n_sweeps, uint32_t swap_every, int
     a.C = t->C;
     a.rk = t->rk;
     a.r_base = t->r_base;
+    a.W = t->W;
     if (t->nsplit <= 1) {
         // one CTA per unit: sweeps and swap passes of the whole call in one launch
         a.s0 = t->sweep;
@@ -741,6 +824,7 @@ extern "C" int ea_tp_sweep(ea_tp *t, uint32_t n_sweeps, uint32_t swap_every, int
     // of nsplit CTAs per unit, then one merge launch that runs the pass
     a.slices = t->d_slices;
     a.spg = t->spg;
+    a.gpw = t->gpw;
     a.nsplit = t->nsplit;
     a.swap_every = 0;
     a.swap_log = swap_log;
@@ -783,7 +867,7 @@ extern "C" int ea_tp_sweep(ea_tp *t, uint32_t n_sweeps, uint32_t swap_every, int
 
 extern "C" int ea_tp_set_split(ea_tp *t, uint32_t k)
 {
-    if (!t || k == 0 || k > 32 || (k & (k - 1)) != 0 || k > t->NT) return EA_EINVAL;
+    if (!t || k == 0 || k > 32 || (k & (k - 1)) != 0 || k > t->NT) return EA_EINVAL;   // k <= min(NT, 32)
     return tp_apply_split(t, k);
 }
 
@@ -791,14 +875,14 @@ extern "C" int ea_tp_read(ea_tp *t, uint32_t *spins, int32_t *energies)
 {
     if (!t) return EA_EINVAL;
     if (spins) {
-        const size_t total = (size_t)t->R * t->C * t->N;
+        const size_t total = (size_t)t->R * t->C * t->W * t->N;
         ea::k_tp_export_spins<<<ea::tp_grid(total), 256, 0, t->stream>>>(t->d_spins, spins, (int)t->L, total);
         ++t->launches;
     }
     if (energies) {
         const size_t total = (size_t)t->R * t->NT * t->C;
         ea::k_tp_export_energy<<<ea::tp_grid(total), 256, 0, t->stream>>>(t->d_energy, energies, t->R,
-                                                                           t->NT, t->C);
+                                                                           t->NT, t->C, t->W);
         ++t->launches;
     }
     return cudaGetLastError() == cudaSuccess ? EA_OK : EA_ECUDA;

@@ -164,7 +164,7 @@ def _tp_create(L=4, R=2, NT=4, C=2, metro=None, swapt=None, bonds=True, spins=Tr
 
 def test_tp_create_validates_arguments_before_touching_the_device():
     """The temperature-packed form rejects bad shapes and tables on the host."""
-    assert _tp_create(NT=33)[0] == -1                    # more slots than bits in a word
+    assert _tp_create(NT=65)[0] == -1                    # more slots than two words hold
     assert _tp_create(NT=0)[0] == -1
     assert _tp_create(R=0)[0] == -1
     assert _tp_create(C=3)[0] == -1

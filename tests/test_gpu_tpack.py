@@ -7,7 +7,8 @@ oracle is given the same bonds, spins and tables in its own layout.  Energies,
 swap masks and spins are compared bit for bit (tolerance 0) after every sweep,
 across lattice sizes with ragged quad counts (L = 6, 10, 12, 14), the
 shared-memory and global-memory bond paths (L <= 24, L = 32), one and two
-copies, 1 to 32 temperatures, and calls split at arbitrary sweeps.
+copies, 1 to 64 temperatures (two words per site above 32), and calls split
+at arbitrary sweeps.
 """
 from __future__ import annotations
 
@@ -39,12 +40,23 @@ def _oracle(inst, inp, metro, swapt):
 
 
 def _tp_from_oracle_spins(sp, NT):
-    """Oracle spins [R][NT][C][N] (bit 0) -> temperature-packed words [R][C][N]."""
+    """Oracle spins [R][NT][C][N] (bit 0) -> temperature-packed words [R][C][N]
+    ([R][C][W][N], slot 32 w + b in bit b of word w, when NT > 32)."""
     R, _, C, N = sp.shape
-    out = np.zeros((R, C, N), np.uint32)
+    nw = -(-NT // 32)
+    out = np.zeros((R, C, nw, N), np.uint32)
     for t in range(NT):
-        out |= (sp[:, t] & np.uint32(1)) << np.uint32(t)
-    return out
+        out[:, :, t // 32] |= (sp[:, t] & np.uint32(1)) << np.uint32(t % 32)
+    return out[:, :, 0] if nw == 1 else out
+
+
+def _pairs_as_words(rl, NT):
+    """Accepted-pair bits [...][NT-1] -> swap-log words [...] ([...][W] when NT > 32)."""
+    nw = -(-NT // 32)
+    want = np.zeros(rl.shape[:-1] + (nw,), np.uint32)
+    for p in range(NT - 1):
+        want[..., p // 32] |= rl[..., p] << np.uint32(p % 32)
+    return want[..., 0] if nw == 1 else want
 
 
 def _compare_calls(L, R, NT, C, calls, swap_every, seed=77, split=None):
@@ -62,10 +74,7 @@ def _compare_calls(L, R, NT, C, calls, swap_every, seed=77, split=None):
         np.testing.assert_array_equal(el, ref["energy_log"][..., 0], err_msg=f"energy log, call {k}")
         sl = out["swap_log"].cpu().numpy().view(np.uint32)
         rl = ref["swap_log"] & np.uint32(1)                          # [passes][R][C][NT-1]
-        want = np.zeros(sl.shape, np.uint32)
-        for p in range(NT - 1):
-            want |= rl[..., p] << np.uint32(p)
-        np.testing.assert_array_equal(sl, want, err_msg=f"swap log, call {k}")
+        np.testing.assert_array_equal(sl, _pairs_as_words(rl, NT), err_msg=f"swap log, call {k}")
         sp, en = gpu.read()
         np.testing.assert_array_equal(sp.cpu().numpy().view(np.uint32),
                                       _tp_from_oracle_spins(sim.spins(), NT), err_msg=f"spins, call {k}")
@@ -104,6 +113,42 @@ def test_tpack_matches_oracle(L, R, NT, C, n, swap_every, split):
 def test_tpack_slot_groups_match_oracle(L, R, NT, C, calls, swap_every, split):
     gpu = _compare_calls(L, R, NT, C, calls, swap_every, split=split)
     assert gpu.split == -(-NT // -(-NT // split))
+
+
+@pytest.mark.parametrize("L,R,NT,C,calls,swap_every,split", [
+    (8, 2, 33, 2, [12, 7], 1, None),   # slot 32 alone in the second word: pair 31 crosses
+    (6, 3, 40, 1, [20], 2, None),      # ragged second word, ragged quads
+    (8, 1, 56, 2, [9, 6], 3, 4),       # the paper's largest ladder (Sec. 5.2), groups of 8 slots
+    (10, 2, 64, 2, [10], 1, 1),        # two full words, one group per word
+    (16, 1, 48, 1, [6], 1, 32),        # one slot a group, sixteen empty groups in the second word
+    (32, 1, 64, 1, [2], 1, 8),         # bonds read from global memory
+])
+def test_tpack_two_words_match_oracle(L, R, NT, C, calls, swap_every, split):
+    """More than 32 temperatures: two words per site (slot 32 w + b in bit b of
+    word w), slot groups within each word, the pass over both words in the merge
+    (runs of accepted pairs carried across the words)."""
+    gpu = _compare_calls(L, R, NT, C, calls, swap_every, split=split)
+    assert gpu.W == 2
+    if split is not None:
+        assert gpu.split == 2 * -(-32 // -(-32 // split))
+
+
+def test_tpack_two_words_match_the_realization_packed_form():
+    """Realization r of a 48-slot temperature-packed ensemble equals realization
+    32r of the realization-packed GPU form (which holds up to 64 slots)."""
+    L, R, NT, C, n = 8, 2, 48, 2, 14
+    inst, inp, metro, swapt = _inputs(L, R, NT, C, 9)
+    tp = ea.TPEnsemble(L, R, NT, C, 9, inp["bonds"], inp["spins"], metro, swapt)
+    b, s = W.tp_as_groups(inp["bonds"], inp["spins"], NT)
+    rp = ea.Ensemble(L, R, NT, C, 9, b, s, metro, swapt)
+    o1 = tp.sweep(n, 1, energy_log=True, swap_log=True)
+    o2 = rp.sweep(n, 1, energy_log=True, swap_log=True)
+    np.testing.assert_array_equal(o1["energy_log"].cpu().numpy(), o2["energy_log"].cpu().numpy()[..., 0])
+    rl = o2["swap_log"].cpu().numpy().view(np.uint32) & np.uint32(1)
+    np.testing.assert_array_equal(o1["swap_log"].cpu().numpy().view(np.uint32), _pairs_as_words(rl, NT))
+    sp, _ = tp.read()
+    np.testing.assert_array_equal(sp.cpu().numpy().view(np.uint32),
+                                  _tp_from_oracle_spins(rp.read_spins().cpu().numpy().view(np.uint32), NT))
 
 
 def test_tpack_single_temperature_has_no_swaps():

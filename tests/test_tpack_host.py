@@ -10,7 +10,9 @@ is set; Sec. 2.4) to a word whose bit t is slot t by the closed form
 because an accepted run of pairs a..b-1 rotates slots a..b by one, and adding
 the bit at a to M carries it through the run's ones to b.  This test checks that
 identity against the pass applied pair by pair, exhaustively for NT <= 10 and
-on random words and masks for NT up to 32.
+on random words and masks for NT up to 32, and the two-word form the merge
+kernel evaluates for 33 <= NT <= 64 (slot 32 w + b in bit b of word w; the
+shift and the addition carried across the words in 32-bit arithmetic).
 """
 import numpy as np
 
@@ -68,3 +70,39 @@ def test_tp_inputs_and_their_realization_packed_layout():
     # fair coins: about half the slot bits and half the bonds are set
     frac = np.mean([(inp["spins"] >> np.uint32(t)) & 1 for t in range(inst.NT)])
     assert 0.45 < frac < 0.55 and 0.45 < inp["bonds"].mean() < 0.55
+
+
+def two_word_form(x0, x1, M0, M1, NT):
+    """The merge kernel's expression on two 32-bit words (unsigned wraparound)."""
+    F = 0xFFFFFFFF
+    valid0 = F if NT >= 32 else (1 << NT) - 1
+    valid1 = F if NT >= 64 else (1 << (NT - 32)) - 1
+    ends0, ends1 = ~M0 & valid0, ~M1 & valid1
+    starts0 = (((~M0 << 1) & F) | 1) & valid0
+    starts1 = (((~M1 << 1) & F) | ((~M0 & F) >> 31)) & valid1
+    sh0 = ((x0 >> 1) | (x1 << 31)) & F
+    sh1 = x1 >> 1
+    s0 = (M0 + (starts0 & x0)) & F
+    cy = 1 if s0 < M0 else 0
+    s1 = (M1 + (starts1 & x1) + cy) & F
+    return (sh0 & M0) | (s0 & ends0), (sh1 & M1) | (s1 & ends1)
+
+
+def test_two_words_33_to_64_slots():
+    rng = np.random.Generator(np.random.PCG64(11))
+    for NT in (33, 34, 40, 47, 56, 63, 64):
+        cases = []
+        for _ in range(3000):
+            M = int(rng.integers(0, 2**32, dtype=np.uint64)) | (int(rng.integers(0, 2**32, dtype=np.uint64)) << 32)
+            w = int(rng.integers(0, 2**32, dtype=np.uint64)) | (int(rng.integers(0, 2**32, dtype=np.uint64)) << 32)
+            cases.append((M, w & ((1 << NT) - 1)))
+        # runs that cross the word boundary, all-accepted and all-rejected ladders
+        full = (1 << (NT - 1)) - 1
+        cases += [(full, 1), (full, 1 << 31), (0, (1 << NT) - 1), (((1 << 40) - 1) ^ ((1 << 20) - 1), 1 << 20),
+                  (1 << 31, 1 << 32), (1 << 31, 1 << 31)]
+        for M, w in cases:
+            M &= (1 << (NT - 1)) - 1
+            x0, x1 = w & 0xFFFFFFFF, w >> 32
+            y0, y1 = two_word_form(x0, x1, M & 0xFFFFFFFF, M >> 32, NT)
+            assert y0 | (y1 << 32) == pair_by_pair(w, M, NT), (NT, M, w)
+

@@ -75,12 +75,21 @@ def draw_tp_inputs(inst: Instance) -> dict:
 
     bonds [R][3][N] uint8 (1 <=> J = -1), each a fair coin; spins [R][C][N]
     uint32 with bit t (t < NT) the initial spin of slot t, each a fair coin
-    (bits at or above NT zero); betas as ``draw_inputs``.  R = inst.G here:
-    one realization per entry, not 32.
+    (bits at or above NT zero) -- for NT > 32, [R][C][W][N] with W = ceil(NT/32)
+    words, bit b of word w the spin of slot 32 w + b; betas as ``draw_inputs``.
+    R = inst.G here: one realization per entry, not 32.
     """
     rng = np.random.Generator(np.random.PCG64(inst.input_seed))
     N = inst.N
     bonds = rng.integers(0, 2, size=(inst.G, 3, N), dtype=np.uint8)
+    if inst.NT > 32:
+        nw = -(-inst.NT // 32)
+        spins = rng.integers(0, 2**32, size=(inst.G, inst.C, nw, N), dtype=np.uint64).astype(np.uint32)
+        last = inst.NT - 32 * (nw - 1)
+        if last < 32:
+            spins[:, :, nw - 1] &= np.uint32((1 << last) - 1)
+        betas = geometric_ladder(inst.NT, inst.tmin, inst.tmax)
+        return {"bonds": bonds, "spins": spins, "betas": betas}
     spins = rng.integers(0, 2**32, size=(inst.G, inst.C, N), dtype=np.uint64).astype(np.uint32)
     if inst.NT < 32:
         spins &= np.uint32((1 << inst.NT) - 1)
@@ -91,12 +100,15 @@ def draw_tp_inputs(inst: Instance) -> dict:
 def tp_as_groups(bonds: np.ndarray, spins: np.ndarray, NT: int) -> tuple[np.ndarray, np.ndarray]:
     """Temperature-packed inputs rewritten in the realization-packed layout with
     realization r as bit 0 of word-group r (the other 31 bits zero): bonds
-    [R][3][N] uint32, spins [R][NT][C][N] uint32.  A pure change of layout."""
-    R, C, N = spins.shape
+    [R][3][N] uint32, spins [R][NT][C][N] uint32.  A pure change of layout
+    (spins [R][C][N], or [R][C][W][N] with slot 32 w + b in bit b of word w)."""
+    if spins.ndim == 3:
+        spins = spins[:, :, None, :]
+    R, C, _, N = spins.shape
     b = bonds.astype(np.uint32) & np.uint32(1)
     s = np.zeros((R, NT, C, N), np.uint32)
     for t in range(NT):
-        s[:, t] = (spins >> np.uint32(t)) & np.uint32(1)
+        s[:, t] = (spins[:, :, t // 32] >> np.uint32(t % 32)) & np.uint32(1)
     return b, s
 
 
