@@ -447,11 +447,17 @@ int run_sweeps(ea_ctx *c, const ea_sweep_args *args, const ea::Plan &plan)
         const bool overlaps = c->C == 2 && args->qhist != nullptr && args->measure_every != 0;
         if (plan.form == ea::kFormUnitWave) {
             const bool meas = args->measure_every != 0 && (args->qhist != nullptr || args->esum != nullptr);
+            const bool log = args->energy_log != nullptr || args->swap_log != nullptr;
             if (!meas) {
-                EA_TRY(ea::launch_sweep_unit_wave(a, plan.swap_in_smem, plan.field_kind, st, &c->launches));
+                EA_TRY(ea::launch_sweep_unit_wave(a, plan.swap_in_smem, plan.field_kind, 0, st, &c->launches));
                 return EA_OK;
             }
-            // measured calls run under the first other unit plan (same results)
+            if (plan.field_kind == 0 && !log) {
+                // field-free measured calls: energy sums, and with two copies the q histogram
+                EA_TRY(ea::launch_sweep_unit_wave(a, plan.swap_in_smem, 0, overlaps ? 2 : 1, st, &c->launches));
+                return EA_OK;
+            }
+            // measured calls with logs or in a field run under the first other unit plan (same results)
             for (const ea::Plan &q : c->plans)
                 if (q.unit && q.form != ea::kFormUnitWave) return run_sweeps(c, args, q);
             return EA_EUNSUPPORTED;

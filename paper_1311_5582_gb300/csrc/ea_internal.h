@@ -95,10 +95,12 @@ int fast_unit_threads(int L, int HP, int NT);
 // (wave_field_kind: 34 or 43; 0 for any other pair).
 constexpr int kWaveMaxTemps = 32;
 int wave_unit_threads(int L, int NT);
-size_t wave_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem, bool field = false);
+size_t wave_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem, bool field = false,
+                      bool overlaps = false);
 int wave_field_kind(int ua0, int ua1);
-cudaError_t launch_sweep_unit_wave(const SweepLaunch &a, bool swap_in_smem, int field_kind, cudaStream_t st,
-                                   uint64_t *launches);
+// meas: 0 none; 1 energy sums (esum); 2 energy sums and the q histogram (C = 2)
+cudaError_t launch_sweep_unit_wave(const SweepLaunch &a, bool swap_in_smem, int field_kind, int meas,
+                                   cudaStream_t st, uint64_t *launches);
 // Dynamic shared memory of the specialised unit kernel (with or without the
 // swap table, the measurement snapshots and the shared-memory histogram).
 size_t fast_unit_smem(int L, int NT, uint32_t swap_len, bool swap_smem, bool snap, bool hist_smem);

@@ -35,8 +35,11 @@ constexpr int kWaveWaitLimit = 1 << 22;    // suspending polls of one wait (seco
 
 // Shared-memory layout of the wavefront kernel, in 32-bit words.
 struct WaveLayout {
-    size_t s, js, eo, cur, bar_e, bar_h, abort, tsw, words;
-    __host__ __device__ WaveLayout(int N, int NT, uint32_t swap_len, bool swap_smem, bool field = false)
+    size_t s, js, eo, cur, bar_e, bar_h, bar_r, bar_d, abort, tsw, hist, words;
+    // overlaps: the copy-pair rendezvous barriers and the q histogram of the
+    // slots this CTA measures (t = c mod 2)
+    __host__ __device__ WaveLayout(int N, int NT, uint32_t swap_len, bool swap_smem, bool field = false,
+                                   bool overlaps = false)
     {
         const int nw = (NT + 1) / 2, rec = field ? 3 : 1;   // Et (and E, M in a field)
         size_t o = 0;
@@ -47,8 +50,11 @@ struct WaveLayout {
         o = (o + 1) & ~(size_t)1;                 // 8-byte alignment of the barriers
         bar_e = o; o += 2 * (size_t)nw;           // mbarrier k: E_{2k+2} of warp k+1 is published
         bar_h = o; o += 2 * (size_t)nw;           // mbarrier k: warp k applied its pass steps
+        bar_r = o; o += overlaps ? 2 * (size_t)nw : 0;   // mbarrier k: the partner's warp k slots are final
+        bar_d = o; o += overlaps ? 2 * (size_t)nw : 0;   // mbarrier k: the partner read my warp k slot
         abort = o; o += 1;
         tsw = o; o += swap_smem && NT > 1 ? (size_t)(NT - 1) * swap_len : 0;
+        hist = o; o += overlaps ? (size_t)nw * (N + 1) : 0;
         words = o;
     }
 };
@@ -73,6 +79,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Arrive (release at cluster scope) on the barrier at the same offset in the
+// shared memory of CTA `rank` of the cluster.
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t *bar, uint32_t rank)
+{
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(bar)), "r"(rank));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
+}
+// try_wait that also acquires the partner CTA's writes made before its arrive.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(ok)
                  : "r"(smem_addr(bar)), "r"(parity)
@@ -105,6 +131,18 @@ __device__ __forceinline__ bool wave_wait(uint64_t *bar, uint32_t parity, volati
 {
     for (int it = 0; it < kWaveWaitLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (*abort != 0u) return false;
+    }
+    *abort = 1u;
+    atomicExch(err, 1);
+    return false;
+}
+// The same for a barrier the partner CTA of the cluster arrives on.
+__device__ __forceinline__ bool wave_wait_cluster(uint64_t *bar, uint32_t parity, volatile uint32_t *abort,
+                                                  int *err)
+{
+    for (int it = 0; it < kWaveWaitLimit; ++it) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
         if (*abort != 0u) return false;
     }
     *abort = 1u;
@@ -451,13 +489,60 @@ __device__ __forceinline__ void wave_bounds(const uint32_t *rowa, const uint32_t
     bB = -step * (int)count_above(rowb, len, rb, sb);
 }
 
+// Number of sites where the two copies of one slot differ (the overlap of
+// Sec. 5: q = 1 - 2 n / N), per realization: lane b receives the count of
+// realization b.  A4 is the slot in this CTA, B4 the same slot of the other
+// copy (distributed shared memory).  Each lane XORs four 16-byte words of both
+// copies, counts its 16 difference words in a carry-save counter, and the warp
+// sums the counters with a butterfly of bit-sliced adders.
+__device__ __forceinline__ int wave_overlap(const uint4 *A4, const uint4 *B4, int lane)
+{
+    CsaAcc<1, 5> cd;
+    cd.clear();
+#define EA_OVQ(Q)                                                                                  \
+    {                                                                                              \
+        const uint4 x = A4[lane + 32 * (Q)], y = B4[lane + 32 * (Q)];                              \
+        const uint32_t d[1][4] = {{x.x ^ y.x, x.y ^ y.y, x.z ^ y.z, x.w ^ y.w}};                   \
+        cd.add<Q>(d);                                                                              \
+    }
+    EA_OVQ(0) EA_OVQ(1) EA_OVQ(2) EA_OVQ(3)
+#undef EA_OVQ
+    uint32_t pl[5], v[10];
+    cd.resolve<4>(pl);
+#pragma unroll
+    for (int p = 0; p < 10; ++p) v[p] = p < 5 ? pl[p] : 0u;
+#pragma unroll
+    for (int lv = 0; lv < 5; ++lv) {
+        uint32_t cy = 0;
+#pragma unroll
+        for (int p = 0; p < 5 + lv; ++p) {
+            const uint32_t o = __shfl_xor_sync(kFull, v[p], 1 << lv);
+            uint32_t s2, c2;
+            full_add(v[p], o, cy, s2, c2);
+            v[p] = s2;
+            cy = c2;
+        }
+        v[5 + lv] = cy;
+    }
+    int nd = 0;
+#pragma unroll
+    for (int p = 0; p < 10; ++p) nd |= (int)((v[p] >> lane) & 1u) << p;
+    return nd;
+}
+
 // LOG = false compiles the body without the energy and swap logs (their
 // pointers must then be null).  FLD = 0 runs the field-free method; FLD = 34
 // (43) the external field with always-accept boundaries u >= 3 (4) for S = -1
 // and u >= 4 (3) for S = +1: decisions of the pass on Et = h_den E - h_num M,
-// magnetisations M counted beside the energies.  Launches that measure (qhist
-// / esum) use another kernel.
-template <bool LOG, int FLD = 0>
+// magnetisations M counted beside the energies.  MEAS (field-free only): 0 no
+// measurement; 1 energy sums of the measured sweeps (esum); 2 also the q
+// histogram (C = 2, the two copies of a group in one 2-CTA cluster): after its
+// pass of a measured sweep, warp k of each copy meets warp k of the other copy
+// (cluster-scope mbarriers: "my slots are final"), counts the overlap of slot
+// 2k + c from its own words and the other copy's (distributed shared memory),
+// signals that it has read them, and waits for the same signal before it
+// next writes its own slots.
+template <bool LOG, int FLD = 0, int MEAS = 0>
 __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const SweepLaunch &a, uint32_t unit,
                                                int swap_in_smem)
 {
@@ -472,7 +557,8 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     int32_t *const energy_log = LOG ? a.energy_log : nullptr;
     uint32_t *const swap_log = LOG ? a.swap_log : nullptr;
     const int NT = (int)a.NT;
-    const WaveLayout lay(N, NT, a.swap_len, swap_in_smem != 0, F);
+    static_assert(MEAS == 0 || FLD == 0, "measurement in the field-free form only");
+    const WaveLayout lay(N, NT, a.swap_len, swap_in_smem != 0, F, MEAS == 2);
     uint32_t *S = base + lay.s;
     uint32_t *Js = base + lay.js;
     int *Eo = reinterpret_cast<int *>(base + lay.eo);          // [3][NT][32]: Et, E, M of slot 2k
@@ -508,6 +594,18 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         mbar_init(&bar_e[i], kLanes);
         mbar_init(&bar_h[i], kLanes);
     }
+    uint64_t *bar_r = reinterpret_cast<uint64_t *>(base + lay.bar_r);
+    uint64_t *bar_d = reinterpret_cast<uint64_t *>(base + lay.bar_d);
+    uint32_t *hist = base + lay.hist;                   // [nw][N + 1]: slot 2k + c
+    const uint32_t *S_other = nullptr;                  // the other copy's lattices (MEAS == 2)
+    if constexpr (MEAS == 2) {
+        for (int i = tid; i < nw; i += nthr) {
+            mbar_init(&bar_r[i], kLanes);
+            mbar_init(&bar_d[i], kLanes);
+        }
+        for (int i = tid; i < nw * (N + 1); i += nthr) hist[i] = 0u;
+        S_other = cg::this_cluster().map_shared_rank(S, (unsigned int)(c ^ 1));
+    }
     if (tid == 0) *abort = 0u;
     // Metropolis thresholds of my slot as 2^64 - T (see below_mask)
     uint64_t t0 = 0, t1 = 0, t2 = 0;
@@ -531,8 +629,14 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     const uint32_t len = a.swap_len;
     const int step = F ? a.step : 4;
     const int hn = a.h_num, hd = a.h_den;
-    __syncthreads();   // staged lattices, bonds, table and flags are complete; no CTA barrier after this
-    if (2 * k >= NT) return;                            // warps beyond the slots (wider CTAs of a batch)
+    if constexpr (MEAS == 2)
+        cg::this_cluster().sync();   // both copies staged, their barriers initialised
+    else
+        __syncthreads();   // staged lattices, bonds, table and flags are complete; no CTA barrier after this
+    if (2 * k >= NT) {                                  // warps beyond the slots (wider CTAs of a batch)
+        if constexpr (MEAS == 2) cg::this_cluster().sync();
+        return;
+    }
     // rows of the warp's pairs 2k and 2k+1 (clamped into range; unused when the pair does not exist)
     const uint32_t *rowa = swt + (size_t)max(min(2 * k, NT - 2), 0) * len;
     const uint32_t *rowb = swt + (size_t)max(min(2 * k + 1, NT - 2), 0) * len;
@@ -547,13 +651,25 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     int EA = 0, EB = 0, MA = 0, MB = 0;
     bool ok_run = true;
     uint32_t ph_e = 0, ph_h = 0;                        // parity of the next phase this warp waits for
+    uint32_t ph_r = 0, ph_d = 0;                        // (MEAS == 2) the copy-pair rendezvous
+    bool pend_d = false;                                // the other copy may still read my slots
+    long long esA = 0, esB = 0;                         // energy sums of the measured sweeps (MEAS)
 
     SwapCountdown swap_cd(a.s0, a.swap_every);
+    MeasureCountdown meas_cd(a.s0, a.measure_from, MEAS != 0 ? a.measure_every : 0u);
     for (uint32_t n = 0; n < a.n_sweeps && ok_run; ++n) {
         const uint64_t s = a.s0 + n;
         const bool swap_s = swap_cd.step();             // a pass follows sweep s
         const bool swap_now = swap_s && NT > 1;
-        const bool needE = swap_now || energy_log != nullptr || (n + 1 == a.n_sweeps);
+        const bool meas = MEAS != 0 && meas_cd.step();
+        const bool needE = swap_now || energy_log != nullptr || meas || (n + 1 == a.n_sweeps);
+        if constexpr (MEAS == 2) {
+            if (pend_d) {                               // before this sweep writes my slots
+                if (!wave_wait_cluster(&bar_d[k], ph_d, abort, a.err)) { ok_run = false; break; }
+                ph_d ^= 1u;
+                pend_d = false;
+            }
+        }
         uint32_t acc[PL], accM[PLM];
 #pragma unroll
         for (int p = 0; p < PL; ++p) acc[p] = 0;
@@ -706,8 +822,46 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
             el[(size_t)(2 * k) * a.C * kLanes + lane] = EA;
             if (hasB) el[(size_t)(2 * k + 1) * a.C * kLanes + lane] = EB;
         }
+        if constexpr (MEAS != 0) {
+            if (meas) {
+                esA += EA;                              // slots 2k, 2k+1 after the sweep and its pass
+                esB += hasB ? EB : 0;
+                if constexpr (MEAS == 2) {
+                    mbar_arrive_remote(&bar_r[k], (uint32_t)(c ^ 1));   // my slots are final
+                    if (!wave_wait_cluster(&bar_r[k], ph_r, abort, a.err)) { ok_run = false; break; }
+                    ph_r ^= 1u;
+                    const int t = 2 * k + c;
+                    if (t < NT) {
+                        const int nd = wave_overlap(reinterpret_cast<const uint4 *>(S + (size_t)t * N),
+                                                    reinterpret_cast<const uint4 *>(S_other + (size_t)t * N),
+                                                    lane);
+                        atomicAdd(&hist[(size_t)k * (N + 1) + nd], 1u);
+                    }
+                    __syncwarp();
+                    mbar_arrive_remote(&bar_d[k], (uint32_t)(c ^ 1));   // done reading the other copy
+                    pend_d = true;
+                }
+            }
+        }
     }
-    if (!ok_run) return;                                // the error flag is raised; state is not written
+    if constexpr (MEAS != 0) {
+        if (ok_run && a.esum != nullptr) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                esA += __shfl_xor_sync(kFull, esA, o);
+                esB += __shfl_xor_sync(kFull, esB, o);
+            }
+            if (lane == 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.esum + 2 * k), (unsigned long long)esA);
+                if (hasB)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.esum + 2 * k + 1), (unsigned long long)esB);
+            }
+        }
+    }
+    if (!ok_run) {                                      // the error flag is raised; state is not written
+        if constexpr (MEAS == 2) cg::this_cluster().sync();
+        return;
+    }
     int32_t *gE = a.energy + (size_t)unit * NT * kLanes;
     gE[(2 * k) * kLanes + lane] = EA;
     if (hasB) gE[(2 * k + 1) * kLanes + lane] = EB;
@@ -721,6 +875,19 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     for (int w = lane; w < nslot * N / 4; w += 32)
         reinterpret_cast<uint4 *>(gS + (size_t)(2 * k) * N)[w] =
             reinterpret_cast<const uint4 *>(S + (size_t)(2 * k) * N)[w];
+    if constexpr (MEAS == 2) {
+        // every warp of both copies is done: the histogram is complete and no
+        // read of this CTA's shared memory is pending
+        cg::this_cluster().sync();
+        if (a.qhist != nullptr)
+            for (int i = tid; i < nw * (N + 1); i += nthr) {
+                const int j = i / (N + 1), bin = i - j * (N + 1);
+                const int t = 2 * j + c;
+                if (t < NT && hist[i] != 0u)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.qhist + (size_t)t * (N + 1) + bin),
+                              (unsigned long long)hist[i]);
+            }
+    }
 }
 
 }  // namespace

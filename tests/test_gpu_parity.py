@@ -259,9 +259,10 @@ def test_wavefront_plan_edge_cases(NT, C, swap_every):
         compare(gpu, sims, n, swap_every)
 
 
-def test_wavefront_plan_measured_calls_fall_back_exactly():
-    """Calls that measure (q histogram, energy sums) run under the specialised
-    plan; before and after them the wavefront plan continues the same chain."""
+def test_wavefront_plan_measured_calls_continue_the_chain():
+    """Calls that measure (q histogram, energy sums) run the measuring
+    instantiation of the wavefront kernel (copy pairs as 2-CTA clusters); before
+    and after them the plain one continues the same chain."""
     inst = W.Instance(L=8, G=3, NT=12, C=2, seed=4, tmin=0.9, tmax=2.0, input_seed=77)
     gpu, sims, _ = pair(inst)
     compare(gpu, sims, 5, 1)
@@ -275,6 +276,36 @@ def test_wavefront_plan_measured_calls_fall_back_exactly():
     np.testing.assert_array_equal(qh.cpu().numpy().view(np.uint64), qh_o)
     np.testing.assert_array_equal(es.cpu().numpy(), es_o)
     compare(gpu, sims, 6, 1)
+
+
+@pytest.mark.parametrize("G,NT,C,n,swap_every,mfrom,mevery,want_q,want_e", [
+    (2, 13, 2, 17, 2, 3, 3, True, True),      # odd NT: the last warp holds one slot
+    (3, 24, 2, 12, 1, 0, 1, True, False),     # histogram only, from the first sweep
+    (2, 24, 2, 10, 1, 4, 2, False, True),     # energy sums only (no cluster)
+    (2, 9, 1, 14, 3, 5, 1, False, True),      # one copy: energy sums
+    (1, 32, 2, 8, 1, 2, 1, True, True),       # 32 slots, 512 threads
+    (2, 2, 2, 9, 1, 1, 4, True, True),        # one pair
+])
+def test_wavefront_measurement_matches_oracle(G, NT, C, n, swap_every, mfrom, mevery, want_q, want_e):
+    """The measuring wavefront kernel: per-slot energy sums and overlap histograms
+    of the measured sweeps, bit-exact against the oracle, and the chain that
+    continues after the call."""
+    inst = W.Instance(L=8, G=G, NT=NT, C=C, seed=31 + NT, tmin=0.9, tmax=2.0, input_seed=500 + NT)
+    gpu, sims, _ = pair(inst)
+    assert gpu.plans()[gpu.plan]["form"] == "unit-wave"
+    qh = torch.zeros((NT, inst.N + 1), dtype=torch.int64, device="cuda") if want_q else None
+    es = torch.zeros(NT, dtype=torch.int64, device="cuda") if want_e else None
+    gpu.sweep(n, swap_every, qhist=qh, esum=es, measure_from=mfrom, measure_every=mevery)
+    qh_o = np.zeros((NT, inst.N + 1), np.uint64) if want_q else None
+    es_o = np.zeros(NT, np.int64) if want_e else None
+    for _, sim in sims:
+        sim.sweep(n, swap_every, qhist=qh_o, esum=es_o, measure_from=mfrom, measure_every=mevery, threads=8)
+    if want_q:
+        np.testing.assert_array_equal(qh.cpu().numpy().view(np.uint64), qh_o)
+        assert int(qh_o.sum()) > 0
+    if want_e:
+        np.testing.assert_array_equal(es.cpu().numpy(), es_o)
+    compare(gpu, sims, 5, swap_every)
 
 
 @pytest.mark.parametrize("tmin,tmax,NT", [(1.5, 1.5, 6), (0.2, 50.0, 5), (0.9, 0.95, 24), (0.3, 3.0, 2)])
