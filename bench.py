@@ -76,7 +76,7 @@ def workload(name="scale", sweeps=None):
 # goes stale when one of them changes).
 KERNEL_SOURCES = {
     "scale": ["ea_unit_wave.cu", "ea_wave.cuh", "ea_fast.cuh", "ea_device.cuh", "ea_internal.h"],
-    "scale_measured": ["ea_unit_fast.cu", "ea_fast.cuh", "ea_device.cuh", "ea_internal.h"],
+    "scale_measured": ["ea_unit_wave.cu", "ea_wave.cuh", "ea_fast.cuh", "ea_device.cuh", "ea_internal.h"],
     "small": ["ea_kernels.cu", "ea_bodies.cuh", "ea_device.cuh", "ea_internal.h"],
     "large16": ["ea_kernels.cu", "ea_bodies.cuh", "ea_device.cuh", "ea_internal.h"],
     "large32": ["ea_kernels.cu", "ea_bodies.cuh", "ea_device.cuh", "ea_internal.h"],

@@ -424,7 +424,9 @@ int ea_pt_swap_static(uint32_t *spins, int32_t *energies, const uint32_t *swapt,
  * (Sec. 3.2 "Map Temperatures Replicas to Bits", Sec. 4.3.3): one 32-bit word
  * per (realization, copy, site) whose bit t is the spin of temperature slot t,
  * so the temperature replicas of one realization are updated together and a
- * replica exchange (Sec. 2.4) permutes bits inside each word.  NT <= 32.
+ * replica exchange (Sec. 2.4) permutes bits inside each word.  NT <= 32
+ * takes one word per site; 33 <= NT <= 64 takes two (slot 32 w + b in bit b
+ * of word w, the paper's several integer cubes).
  *
  * Random numbers: each realization has its own.  Realization r uses the
  * counters of word-group r of the realization-packed form above (bit 0 of
