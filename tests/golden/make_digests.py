@@ -19,9 +19,13 @@ oracle (itself pinned by tests/test_oracle_pins.py) at full length so that the
 GPU path can be compared with it where running the oracle live would take hours.
 
 Only ``oracle/`` and ``workloads/`` are called.  Jobs run in a process pool
-(spawn) and write one part file each, so an interrupted run resumes.
+(spawn); each rewrites its part file after every chunk, so a long run cut short
+still gives its completed chunks (the merge keeps the chunks every sampled
+group has finished and records that prefix as the workload's length), and a
+restarted run redoes only the jobs that had not finished.
 
 Run:  python tests/golden/make_digests.py --jobs 6 [--only scale,large16] [--parts DIR]
+      python tests/golden/make_digests.py --merge-only --parts DIR   (records so far)
 """
 from __future__ import annotations
 
@@ -70,12 +74,13 @@ def workload_table() -> dict:
         "scale": dict(inst=W.SCALE, sweeps=W.SCALE_SWEEPS, swap_every=W.SCALE_SWAP_EVERY,
                       chunk=10_000, groups=spread(W.SCALE.G, 4), energy_log=True,
                       measure=(W.SCALE_SWEEPS // 2, 1)),
-        # 3*10^4 of the 10^5 sweeps: the oracle takes ~0.13 s per sweep of one
-        # L=16 group (~3.7 h for the whole run).
-        "large16": dict(inst=W.LARGE16, sweeps=30_000, swap_every=W.LARGE_SWAP_EVERY,
+        # the whole 10^5 sweeps (~0.13 s per sweep of one L=16 group on one core,
+        # ~3.7 h a group); records after every 10^4
+        "large16": dict(inst=W.LARGE16, sweeps=W.LARGE_SWEEPS, swap_every=W.LARGE_SWAP_EVERY,
                         chunk=10_000, groups=spread(W.LARGE16.G, 4), energy_log=True, measure=None),
-        # 10^3 of the 10^5 sweeps: ~2.3 s per sweep of one L=32 group.
-        "large32": dict(inst=W.LARGE32, sweeps=1_000, swap_every=W.LARGE_SWAP_EVERY,
+        # 2*10^3 of the 10^5 sweeps: ~2.3 s per sweep of one L=32 group (the whole
+        # run would take ~63 h a group); records after every 500
+        "large32": dict(inst=W.LARGE32, sweeps=2_000, swap_every=W.LARGE_SWAP_EVERY,
                         chunk=500, groups=spread(W.LARGE32.G, 4), energy_log=True, measure=None),
     }
     for inst in W.batch_instances():
@@ -115,6 +120,22 @@ def run_job(name: str, g: int, parts: str) -> str:
     chunks = []
     t0 = time.time()
     done = 0
+    path = os.path.join(parts, f"{name}_g{g}.json")
+
+    def save(complete: bool):
+        # the record so far: a run cut short still gives its completed chunks
+        res = {"name": name, "group": g, "chunks": chunks, "complete": complete,
+               "energy_per_spin_slot0": float(sim.energies()[0][0].mean() / inst.N),
+               "cpu_seconds": round(time.time() - t0, 1),
+               "flip_attempts": int(done) * inst.N * inst.NT * inst.C * 32}
+        if qh is not None and complete:
+            res["qhist"] = digest(qh)
+            res["qhist_total"] = int(qh.sum())
+            res["esum"] = [int(x) for x in es]
+        with open(path + ".tmp", "w") as f:
+            json.dump(res, f, indent=1)
+        os.replace(path + ".tmp", path)
+
     while done < w["sweeps"]:
         n = min(w["chunk"], w["sweeps"] - done)
         out = sim.sweep(n, w["swap_every"], energy_log=w["energy_log"], swap_log=True, qhist=qh,
@@ -129,18 +150,7 @@ def run_job(name: str, g: int, parts: str) -> str:
         if w["energy_log"]:
             rec["energy_log"] = digest(out["energy_log"][:, 0])
         chunks.append(rec)
-    res = {"name": name, "group": g, "chunks": chunks,
-           "energy_per_spin_slot0": float(sim.energies()[0][0].mean() / inst.N),
-           "cpu_seconds": round(time.time() - t0, 1),
-           "flip_attempts": int(w["sweeps"]) * inst.N * inst.NT * inst.C * 32}
-    if qh is not None:
-        res["qhist"] = digest(qh)
-        res["qhist_total"] = int(qh.sum())
-        res["esum"] = [int(x) for x in es]
-    path = os.path.join(parts, f"{name}_g{g}.json")
-    with open(path + ".tmp", "w") as f:
-        json.dump(res, f, indent=1)
-    os.replace(path + ".tmp", path)
+        save(done >= w["sweeps"])
     return path
 
 
@@ -149,6 +159,8 @@ def _run_job_args(args):
 
 
 def merge(parts: str, names: list[str]) -> dict:
+    """Digests of the named workloads whose sampled groups all have a record,
+    each cut to the chunks that every group has completed."""
     import oracle
 
     table = workload_table()
@@ -157,21 +169,46 @@ def merge(parts: str, names: list[str]) -> dict:
            "workloads": {}}
     for name in names:
         w = table[name]
+        recs = {}
+        for g in w["groups"]:
+            path = os.path.join(parts, f"{name}_g{g}.json")
+            if os.path.exists(path):
+                with open(path) as f:
+                    recs[g] = json.load(f)
+        if len(recs) < len(w["groups"]) or min(len(r["chunks"]) for r in recs.values()) == 0:
+            print("not merged (groups still running or not started):", name)
+            continue
+        m = min(len(r["chunks"]) for r in recs.values())
+        complete = all(r.get("complete", True) for r in recs.values())
         inst = w["inst"]
         inp = W.draw_inputs(inst)
-        ent = {"inst": inst_dict(inst), "sweeps": w["sweeps"], "swap_every": w["swap_every"],
+        ent = {"inst": inst_dict(inst), "sweeps": recs[w["groups"][0]]["chunks"][m - 1]["end_sweep"],
+               "planned_sweeps": w["sweeps"], "swap_every": w["swap_every"],
                "chunk": w["chunk"], "energy_log": w["energy_log"],
-               "measure": list(w["measure"]) if w["measure"] else None,
+               "measure": list(w["measure"]) if (w["measure"] and complete) else None,
                "metro_table": digest(oracle.metro_table(inp["betas"])),
                "swap_table": digest(oracle.swap_table_trimmed(inp["betas"], inst.N)),
                "groups": {}}
-        for g in w["groups"]:
-            with open(os.path.join(parts, f"{name}_g{g}.json")) as f:
-                p = json.load(f)
-            p.pop("name")
-            ent["groups"][str(p.pop("group"))] = p
+        for g, r in recs.items():
+            r = dict(r)
+            r.pop("name")
+            r.pop("group")
+            r.pop("complete", None)
+            r["chunks"] = r["chunks"][:m]
+            if not complete:
+                for k in ("qhist", "qhist_total", "esum"):
+                    r.pop(k, None)
+            ent["groups"][str(g)] = r
         doc["workloads"][name] = ent
     return doc
+
+
+def _done(parts: str, name: str, g: int) -> bool:
+    path = os.path.join(parts, f"{name}_g{g}.json")
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        return json.load(f).get("complete", True)
 
 
 def main():
@@ -179,34 +216,31 @@ def main():
     ap.add_argument("--jobs", type=int, default=max(1, (os.cpu_count() or 2) - 2))
     ap.add_argument("--only", default="", help="comma-separated workload names")
     ap.add_argument("--parts", default=os.path.join(HERE, ".parts"))
-    ap.add_argument("--merge-only", action="store_true")
+    ap.add_argument("--merge-only", action="store_true",
+                    help="merge the records written so far (complete chunks only) and exit")
     a = ap.parse_args()
     table = workload_table()
     names = [n for n in table if not a.only or n in a.only.split(",")]
     os.makedirs(a.parts, exist_ok=True)
-    todo = [(n, g) for n in names for g in table[n]["groups"]
-            if not os.path.exists(os.path.join(a.parts, f"{n}_g{g}.json"))]
+    todo = [(n, g) for n in names for g in table[n]["groups"] if not _done(a.parts, n, g)]
+    # the longest full-length runs start first; the L=32 prefix runs go last,
+    # after the short jobs, since any completed prefix of theirs is usable
     cost = lambda j: table[j[0]]["sweeps"] * table[j[0]]["inst"].N * table[j[0]]["inst"].NT
-    todo.sort(key=cost, reverse=True)
+    todo.sort(key=lambda j: (j[0] == "large32", -cost(j)))
     if todo and not a.merge_only:
         print(f"{len(todo)} jobs on {a.jobs} processes", flush=True)
         with mp.get_context("spawn").Pool(a.jobs) as pool:
-            for path in pool.imap_unordered(_run_job_args, [(n, g, a.parts) for n, g in todo]):
+            for path in pool.imap_unordered(_run_job_args, [(n, g, a.parts) for n, g in todo], chunksize=1):
                 print("done", path, flush=True)
-    missing = [(n, g) for n in names for g in table[n]["groups"]
-               if not os.path.exists(os.path.join(a.parts, f"{n}_g{g}.json"))]
-    if missing:
-        print("missing parts:", missing)
-        return 1
     doc = merge(a.parts, names)
-    if a.only and os.path.exists(OUT):
+    if os.path.exists(OUT):
         with open(OUT) as f:
             old = json.load(f)
         old["workloads"].update(doc["workloads"])
         doc = old
     with open(OUT, "w") as f:
         json.dump(doc, f, indent=1, sort_keys=True)
-    print("wrote", OUT)
+    print("wrote", OUT, "with", sorted(doc["workloads"]))
     return 0
 
 
