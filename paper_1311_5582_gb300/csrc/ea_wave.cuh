@@ -42,9 +42,10 @@ struct WaveLayout {
                                    bool overlaps = false)
     {
         const int nw = (NT + 1) / 2, rec = field ? 3 : 1;   // Et (and E, M in a field)
+        const int sn = field ? 3 * N / 2 : N;     // words of a lattice: [c0][c1] ([c0][c1][c0'] in a field)
         size_t o = 0;
-        s = o; o += (size_t)NT * N;               // [NT][2][H] spins by slot
-        js = o; o += (size_t)3 * N;               // [3][2][H] bonds
+        s = o; o += (size_t)NT * sn;              // [NT][sn] spins by slot
+        js = o; o += (size_t)3 * sn;              // [3][sn] bonds
         eo = o; o += (size_t)rec * NT * kLanes;   // slot 2k after the sweep, for warp k-1
         cur = o; o += (size_t)rec * nw * kLanes;  // the carried configuration, warp k to warp k+1
         o = (o + 1) & ~(size_t)1;                 // 8-byte alignment of the barriers
@@ -298,37 +299,51 @@ __device__ __forceinline__ uint32_t field_mask(uint32_t a0, uint32_t a1, uint32_
     }
 }
 
-// Up-spin counts of the eight quads a lane updates in one sweep (<= 32).
+// Up-spin counts: the four quads of one half-sweep (<= 16) and their sum over
+// the sweep's two halves (<= 32).
 constexpr int kPlanesM = 6;
-using UpAcc = CsaAcc<1, kPlanesM>;
+constexpr int kPlanesHalfM = 5;
+using HalfUpAcc = CsaAcc<1, kPlanesHalfM>;
 
-// Metropolis update of one quad in the field (L = 8): the flip mask per spin
-// value from field_mask, selected per lane by the spin bit; WITH_E adds the
-// post-update unsatisfied-bond counts to ce (as quad Q of the half), WITH_M
-// the new spins to cm (as quad QM of the sweep).
-template <int COL, int PX, bool WITH_E, bool WITH_M, int UA0, int UA1, int Q, int QM>
-__device__ __forceinline__ void wave_quad_field(const WaveQuad &q, uint4 r, const uint64_t (&n0)[UA0],
-                                                const uint64_t (&n1)[UA1], CountAcc &ce, UpAcc &cm,
-                                                uint32_t dep)
+// In a field one body serves both colours, so that the code of a sweep fits
+// the instruction cache (two colour-specialised copies of the field update
+// did not: their fetch stalls cost about a fifth of the kernel's time).  A
+// slot's lattice is held as [c0][c1][c0'] and each bond direction as
+// [c0][c1][c0'] (H words each), c0' a copy of colour 0 that the colour-0
+// half-sweep writes beside c0.  For colour col the quad's own words lie
+// col * H words beyond its colour-0 addresses and the other colour's words H
+// words beyond its own, so both colours load with the same immediate
+// offsets.  The x parity of the quad's sites is chosen at run time: with v the
+// other colour's row words rotated left by px, the +x neighbours are v and
+// the -x neighbours v rotated right (likewise the -x bonds).
+constexpr uint32_t kWaveH4 = 256u * 4u;        // bytes of a colour half (L = 8)
+constexpr int kWaveFieldD4 = 3 * 256 * 4;      // bytes of a bond direction in the field layout
+
+__device__ __forceinline__ uint4 rot_left_if(bool px, uint4 v)
 {
-    constexpr int H4 = 256 * 4, N4 = 512 * 4;
-    constexpr int C4 = COL * H4, O4 = (1 - COL) * H4;
-    const uint4 own = lds4<C4>(q.s, dep), xo = lds4<O4>(q.s, dep);
-    const uint4 vyp = lds4<O4>(q.yp, dep), vym = lds4<O4>(q.ym, dep);
-    const uint4 vzp = lds4<O4>(q.zp, dep), vzm = lds4<O4>(q.zm, dep);
-    const uint4 jcx = lds4<C4>(q.j, dep), jcy = lds4<N4 + C4>(q.j, dep), jcz = lds4<2 * N4 + C4>(q.j, dep);
-    const uint4 jox = lds4<O4>(q.j, dep), joy = lds4<N4 + O4>(q.jym, dep), joz = lds4<2 * N4 + O4>(q.jzm, dep);
-    const uint32_t xe_s = PX ? xo.x : xo.w;
-    uint32_t nxp[4], nxm[4], jxm[4];
-    if constexpr (PX == 0) {
-        nxp[0] = xo.x; nxp[1] = xo.y; nxp[2] = xo.z; nxp[3] = xo.w;
-        nxm[0] = xe_s; nxm[1] = xo.x; nxm[2] = xo.y; nxm[3] = xo.z;
-        jxm[0] = jox.w; jxm[1] = jox.x; jxm[2] = jox.y; jxm[3] = jox.z;
-    } else {
-        nxp[0] = xo.y; nxp[1] = xo.z; nxp[2] = xo.w; nxp[3] = xe_s;
-        nxm[0] = xo.x; nxm[1] = xo.y; nxm[2] = xo.z; nxm[3] = xo.w;
-        jxm[0] = jox.x; jxm[1] = jox.y; jxm[2] = jox.z; jxm[3] = jox.w;
-    }
+    return px ? make_uint4(v.y, v.z, v.w, v.x) : v;
+}
+
+// Metropolis update of one quad in the field (L = 8), colour `col` (d =
+// col * H bytes): the flip mask per spin value from field_mask, selected per
+// lane by the spin bit; WITH_E adds the post-update unsatisfied-bond counts to
+// ce in colour 1 (as quad Q of the half), WITH_M the new spins to cm.
+template <bool WITH_E, bool WITH_M, int UA0, int UA1, int Q>
+__device__ __forceinline__ void wave_quad_field(const WaveQuad &q, uint32_t d, bool px, bool col0, uint4 r,
+                                                const uint64_t (&n0)[UA0], const uint64_t (&n1)[UA1],
+                                                CountAcc &ce, HalfUpAcc &cm, uint32_t dep)
+{
+    constexpr int H4 = (int)kWaveH4, D4 = kWaveFieldD4;
+    const uint32_t sa = q.s + d, ja = q.j + d;
+    const uint4 own = lds4<0>(sa, dep), xo = lds4<H4>(sa, dep);
+    const uint4 vyp = lds4<H4>(q.yp + d, dep), vym = lds4<H4>(q.ym + d, dep);
+    const uint4 vzp = lds4<H4>(q.zp + d, dep), vzm = lds4<H4>(q.zm + d, dep);
+    const uint4 jcx = lds4<0>(ja, dep), jcy = lds4<D4>(ja, dep), jcz = lds4<2 * D4>(ja, dep);
+    const uint4 jox = lds4<H4>(ja, dep), joy = lds4<D4 + H4>(q.jym + d, dep);
+    const uint4 joz = lds4<2 * D4 + H4>(q.jzm + d, dep);
+    const uint4 v = rot_left_if(px, xo), w = rot_left_if(px, jox);
+    const uint32_t nxp[4] = {v.x, v.y, v.z, v.w}, nxm[4] = {v.w, v.x, v.y, v.z};
+    const uint32_t jxm[4] = {w.w, w.x, w.y, w.z};
     const uint32_t sv[4] = {own.x, own.y, own.z, own.w};
     const uint32_t jx[4] = {jcx.x, jcx.y, jcx.z, jcx.w};
     const uint32_t ny[4] = {vyp.x, vyp.y, vyp.z, vyp.w}, my[4] = {vym.x, vym.y, vym.z, vym.w};
@@ -336,7 +351,7 @@ __device__ __forceinline__ void wave_quad_field(const WaveQuad &q, uint4 r, cons
     const uint32_t jy[4] = {jcy.x, jcy.y, jcy.z, jcy.w}, jym[4] = {joy.x, joy.y, joy.z, joy.w};
     const uint32_t jz[4] = {jcz.x, jcz.y, jcz.z, jcz.w}, jzm[4] = {joz.x, joz.y, joz.z, joz.w};
     const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-    uint32_t ns[4], x[3][4];
+    uint32_t ns[4], A0[4], A1[4], B0[4], B1[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const uint32_t sj = sv[j];
@@ -355,30 +370,43 @@ __device__ __forceinline__ void wave_quad_field(const WaveQuad &q, uint4 r, cons
         for (int u = 0; u < UA1; ++u) m1[u] = below_mask(rr[j], n1[u]);
         const uint32_t F0 = field_mask<UA0>(a0, a1, b0, b1, m0), F1 = field_mask<UA1>(a0, a1, b0, b1, m1);
         ns[j] = lop3<kSelNot>(sj, F1, F0);              // s ^ f with f = S > 0 ? F1 : F0
-        if constexpr (WITH_E) {
-            const uint32_t f = sj ^ ns[j];
-            const uint32_t u0 = a0 ^ b0, c0 = a0 & b0;
-            const uint32_t u1 = lop3<kXor3>(a1, b1, c0), u2 = lop3<kMaj3>(a1, b1, c0);
-            x[0][j] = u0;
-            x[1][j] = lop3<kXorAndN>(u1, f, u0);
-            x[2][j] = lop3<kXorAndN>(u2, f, u0 & u1);
+        A0[j] = a0;
+        A1[j] = a1;
+        B0[j] = b0;
+        B1[j] = b1;
+    }
+    const uint4 nsv = make_uint4(ns[0], ns[1], ns[2], ns[3]);
+    sts4<0>(sa, nsv);
+    if (col0) sts4<2 * H4>(sa, nsv);                   // colour 0 also refreshes its copy c0'
+    if constexpr (WITH_E) {
+        if (!col0) {
+            uint32_t x[3][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t f = sv[j] ^ ns[j];
+                const uint32_t u0 = A0[j] ^ B0[j], c0 = A0[j] & B0[j];
+                const uint32_t u1 = lop3<kXor3>(A1[j], B1[j], c0), u2 = lop3<kMaj3>(A1[j], B1[j], c0);
+                x[0][j] = u0;
+                x[1][j] = lop3<kXorAndN>(u1, f, u0);
+                x[2][j] = lop3<kXorAndN>(u2, f, u0 & u1);
+            }
+            ce.template add<Q>(x);
         }
     }
-    sts4<C4>(q.s, make_uint4(ns[0], ns[1], ns[2], ns[3]));
-    if constexpr (WITH_E) ce.template add<Q>(x);
     if constexpr (WITH_M) {
         const uint32_t up[1][4] = {{ns[0], ns[1], ns[2], ns[3]}};
-        cm.template add<QM>(up);
+        cm.template add<Q>(up);
     }
 }
 
-// Half-sweep of colour COL in the field.  With WITH_E, acc receives the lane's
-// post-update counts of its 16 sites; with WITH_M the new spins go to cm as
-// quads 4 COL .. 4 COL + 3 of the sweep.
-template <int COL, bool WITH_E, bool WITH_M, int UA0, int UA1>
-__device__ __forceinline__ void wave_half_field(const WaveQuad (&wq)[4], uint32_t s, uint32_t ctag,
+// Half-sweep of colour col in the field.  With WITH_E, colour 1 writes the
+// lane's post-update counts of its 16 sites to acc (colour 0 leaves acc as it
+// is); with WITH_M, up receives the up-spin count of its 16 new spins.
+template <bool WITH_E, bool WITH_M, int UA0, int UA1>
+__device__ __forceinline__ void wave_half_field(const WaveQuad (&wq)[4], int col, uint32_t s, uint32_t ctag,
                                                 const RoundKeys &rk, const uint64_t (&n0)[UA0],
-                                                const uint64_t (&n1)[UA1], uint32_t (&acc)[7], UpAcc &cm)
+                                                const uint64_t (&n1)[UA1], uint32_t (&acc)[7],
+                                                uint32_t (&up)[kPlanesHalfM])
 {
     const uint32_t dep = opaque_zero();
     const uint32_t lo1 = kM1 * s, n0r = __umulhi(kM1, s) ^ ctag ^ rk.k[0];
@@ -386,18 +414,38 @@ __device__ __forceinline__ void wave_half_field(const WaveQuad (&wq)[4], uint32_
     auto draw = [&](const WaveQuad &q) {
         return philox_from2(q.phi1 ^ lo1 ^ rk.k[2], q.plo1, hi0b ^ q.plo0 ^ rk.k[3], lo0b, rk);
     };
-    constexpr int QB = 4 * COL;
+    const bool col0 = col == 0;
+    const uint32_t d = col0 ? 0u : kWaveH4;
+    const bool pxa = !col0;                            // x parity of quads 0, 1 (row parity 0); 2, 3 the other
     CountAcc ce;
     ce.clear();
+    HalfUpAcc cm;
+    cm.clear();
     uint4 r0 = draw(wq[0]);
     uint4 r1 = draw(wq[1]);
-    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, 0, QB + 0>(wq[0], r0, n0, n1, ce, cm, dep);
+    wave_quad_field<WITH_E, WITH_M, UA0, UA1, 0>(wq[0], d, pxa, col0, r0, n0, n1, ce, cm, dep);
     r0 = draw(wq[2]);
-    wave_quad_field<COL, COL, WITH_E, WITH_M, UA0, UA1, 1, QB + 1>(wq[1], r1, n0, n1, ce, cm, dep);
+    wave_quad_field<WITH_E, WITH_M, UA0, UA1, 1>(wq[1], d, pxa, col0, r1, n0, n1, ce, cm, dep);
     r1 = draw(wq[3]);
-    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, 2, QB + 2>(wq[2], r0, n0, n1, ce, cm, dep);
-    wave_quad_field<COL, 1 - COL, WITH_E, WITH_M, UA0, UA1, 3, QB + 3>(wq[3], r1, n0, n1, ce, cm, dep);
-    if constexpr (WITH_E) ce.resolve<4>(acc);
+    wave_quad_field<WITH_E, WITH_M, UA0, UA1, 2>(wq[2], d, !pxa, col0, r0, n0, n1, ce, cm, dep);
+    wave_quad_field<WITH_E, WITH_M, UA0, UA1, 3>(wq[3], d, !pxa, col0, r1, n0, n1, ce, cm, dep);
+    if constexpr (WITH_E) {
+        if (!col0) ce.resolve<4>(acc);
+    }
+    if constexpr (WITH_M) cm.resolve<4>(up);
+}
+
+// Adds a half-sweep's up-spin count (5 planes) to the sweep's (6 planes).
+__device__ __forceinline__ void add_up_planes(uint32_t (&acc)[kPlanesM], const uint32_t (&up)[kPlanesHalfM])
+{
+    uint32_t cy = 0u;
+#pragma unroll
+    for (int p = 0; p < kPlanesHalfM; ++p) {
+        const uint32_t x = acc[p];
+        acc[p] = lop3<kXor3>(x, up[p], cy);
+        cy = lop3<kMaj3>(x, up[p], cy);
+    }
+    acc[kPlanesHalfM] ^= cy;
 }
 
 // Unsatisfied-bond totals of the warp's two slots: each half-warp sums its
@@ -580,10 +628,25 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
 
     uint32_t *gS = a.spins + (size_t)unit * NT * N;
     const uint32_t *gJ = a.bonds + (size_t)g * 3 * N;
-    for (int w = tid; w < NT * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(S)[w] = __ldcg(reinterpret_cast<const uint4 *>(gS) + w);
-    for (int w = tid; w < 3 * N / 4; w += nthr)
-        reinterpret_cast<uint4 *>(Js)[w] = reinterpret_cast<const uint4 *>(gJ)[w];
+    constexpr int SN = F ? 3 * N / 2 : N;               // words of a slot's lattice in shared memory
+    if constexpr (F) {
+        // [c0][c1] of each slot; c0' is written by the first colour-0 half-sweep
+        for (int w = tid; w < NT * N / 4; w += nthr)
+            reinterpret_cast<uint4 *>(S)[(w / (N / 4)) * (SN / 4) + w % (N / 4)] =
+                __ldcg(reinterpret_cast<const uint4 *>(gS) + w);
+        // [c0][c1][c0'] of each bond direction
+        for (int w = tid; w < 3 * N / 4; w += nthr) {
+            const uint4 v = reinterpret_cast<const uint4 *>(gJ)[w];
+            const int dir = w / (N / 4), o = w % (N / 4);
+            reinterpret_cast<uint4 *>(Js)[dir * (SN / 4) + o] = v;
+            if (o < N / 8) reinterpret_cast<uint4 *>(Js)[dir * (SN / 4) + N / 4 + o] = v;
+        }
+    } else {
+        for (int w = tid; w < NT * N / 4; w += nthr)
+            reinterpret_cast<uint4 *>(S)[w] = __ldcg(reinterpret_cast<const uint4 *>(gS) + w);
+        for (int w = tid; w < 3 * N / 4; w += nthr)
+            reinterpret_cast<uint4 *>(Js)[w] = reinterpret_cast<const uint4 *>(gJ)[w];
+    }
     const uint32_t *swt = a.swapt;
     if (swap_in_smem) {
         uint32_t *Tsw = base + lay.tsw;
@@ -620,7 +683,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
         t1 = 0ull - (uint64_t)a.metro[ls * 3 + 1];
         t2 = 0ull - (uint64_t)a.metro[ls * 3 + 2];
     }
-    uint32_t *mine = S + (size_t)ls * N;
+    uint32_t *mine = S + (size_t)ls * SN;
     WaveQuad wq[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) wq[j] = wave_quad_setup(mine, Js, quad_row<L>(j >> 1, li + 16 * (j & 1)), gr, a.rk);
@@ -676,17 +739,26 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
 #pragma unroll
         for (int p = 0; p < PLM; ++p) accM[p] = 0;
         if constexpr (F) {
-            UpAcc cm;
-            cm.clear();
+            // one body for both colours (kept a loop: two copies overflow the instruction cache)
             if (needE) {
-                if (act) wave_half_field<0, false, true, UA0, UA1>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, cm);
-                __syncwarp();
-                if (act) wave_half_field<1, true, true, UA0, UA1>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, cm);
-                cm.resolve<8>(accM);
+#pragma unroll 1
+                for (int col = 0; col < 2; ++col) {
+                    uint32_t up[kPlanesHalfM] = {};
+                    if (act)
+                        wave_half_field<true, true, UA0, UA1>(wq, col, (uint32_t)s, col ? tag1 : tag0, a.rk, n0, n1,
+                                                              acc, up);
+                    add_up_planes(accM, up);
+                    __syncwarp();
+                }
             } else {
-                if (act) wave_half_field<0, false, false, UA0, UA1>(wq, (uint32_t)s, tag0, a.rk, n0, n1, acc, cm);
-                __syncwarp();
-                if (act) wave_half_field<1, false, false, UA0, UA1>(wq, (uint32_t)s, tag1, a.rk, n0, n1, acc, cm);
+#pragma unroll 1
+                for (int col = 0; col < 2; ++col) {
+                    uint32_t up[kPlanesHalfM] = {};
+                    if (act)
+                        wave_half_field<false, false, UA0, UA1>(wq, col, (uint32_t)s, col ? tag1 : tag0, a.rk, n0,
+                                                                n1, acc, up);
+                    __syncwarp();
+                }
             }
         } else {
             if (act) wave_half<0, false, PL>(wq, (uint32_t)s, tag0, a.rk, t0, t1, t2, acc);
@@ -743,8 +815,8 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
                         curM = MB;
                     }
                 }
-                uint4 *pa = reinterpret_cast<uint4 *>(S + (size_t)(2 * k) * N);
-                uint4 *pb = reinterpret_cast<uint4 *>(S + (size_t)(2 * k + 1) * N);
+                uint4 *pa = reinterpret_cast<uint4 *>(S + (size_t)(2 * k) * SN);
+                uint4 *pb = reinterpret_cast<uint4 *>(S + (size_t)(2 * k + 1) * SN);
                 uint4 xb[N / 128];                      // slot 2k+1 after pair 2k (the carry)
 #pragma unroll
                 for (int j = 0; j < N / 128; ++j) {
@@ -774,7 +846,7 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
                             curM = e2M;
                         }
                     }
-                    uint4 *pc = reinterpret_cast<uint4 *>(S + (size_t)(2 * k + 2) * N);
+                    uint4 *pc = reinterpret_cast<uint4 *>(S + (size_t)(2 * k + 2) * SN);
 #pragma unroll
                     for (int j = 0; j < N / 128; ++j) {
                         const uint4 x = xb[j], y = pc[lane + 32 * j];
@@ -872,9 +944,16 @@ __device__ __forceinline__ void unit_wave_body(uint32_t *const base, const Sweep
     }
     // this warp's slots are final (no later pass step touches them)
     const int nslot = hasB ? 2 : 1;
-    for (int w = lane; w < nslot * N / 4; w += 32)
-        reinterpret_cast<uint4 *>(gS + (size_t)(2 * k) * N)[w] =
-            reinterpret_cast<const uint4 *>(S + (size_t)(2 * k) * N)[w];
+    if constexpr (F) {
+        for (int i = 0; i < nslot; ++i)
+            for (int w = lane; w < N / 4; w += 32)
+                reinterpret_cast<uint4 *>(gS + (size_t)(2 * k + i) * N)[w] =
+                    reinterpret_cast<const uint4 *>(S + (size_t)(2 * k + i) * SN)[w];
+    } else {
+        for (int w = lane; w < nslot * N / 4; w += 32)
+            reinterpret_cast<uint4 *>(gS + (size_t)(2 * k) * N)[w] =
+                reinterpret_cast<const uint4 *>(S + (size_t)(2 * k) * N)[w];
+    }
     if constexpr (MEAS == 2) {
         // every warp of both copies is done: the histogram is complete and no
         // read of this CTA's shared memory is pending
