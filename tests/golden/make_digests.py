@@ -12,6 +12,9 @@ chunk of sweeps, SHA-256 digests of the little-endian arrays
   swap_log    [P][C][NT-1]   uint32  accepted-pair masks of the chunk's passes
   energy_log  [n][NT][C][32] int32   energies after every sweep of the chunk
 
+(for the temperature-packed workload, realization r = bit 0 of group r: spins
+[NT][C][N] uint8, energies [NT][C] int32, swap_log [P][C] uint32 with bit p =
+pair p)
 and, for the L=8 workload, the overlap histogram [NT][N+1] (uint64) and the
 energy sums [NT] of the measurement after every sweep of the second half.
 The paper prints no worked example: these are not paper values, they freeze the
@@ -87,6 +90,10 @@ def workload_table() -> dict:
         t[f"batch_L{inst.L}"] = dict(inst=inst, sweeps=W.BATCH_SWEEPS, swap_every=W.BATCH_SWAP_EVERY,
                                      chunk=W.BATCH_SWEEPS, groups=[0, inst.G - 1], energy_log=True,
                                      measure=None)
+    # temperature-packed form: realization r is bit 0 of word-group r of the
+    # realization-packed oracle run (group_base = r); sampled realizations
+    t["tpack"] = dict(inst=W.TPACK, sweeps=W.TPACK_SWEEPS, swap_every=W.TPACK_SWAP_EVERY, chunk=500,
+                      groups=spread(W.TPACK.G, 4), energy_log=False, measure=None, tpack=True)
     taken = 0
     for r, req in enumerate(W.served_trace()):
         inst = req["inst"]
@@ -106,11 +113,17 @@ def run_job(name: str, g: int, parts: str) -> str:
 
     w = workload_table()[name]
     inst: W.Instance = w["inst"]
-    inp = W.draw_inputs(inst)
+    tp = w.get("tpack", False)
+    if tp:
+        inp = W.draw_tp_inputs(inst)
+        bonds, spins = W.tp_as_groups(inp["bonds"], inp["spins"], inst.NT)
+    else:
+        inp = W.draw_inputs(inst)
+        bonds, spins = inp["bonds"], inp["spins"]
     metro = oracle.metro_table(inp["betas"])
     swapt = oracle.swap_table_trimmed(inp["betas"], inst.N)
-    sim = oracle.OracleSim(inst.L, 1, inst.NT, inst.C, inst.seed, inp["bonds"][g:g + 1],
-                           inp["spins"][g:g + 1], metro, swapt, group_base=g)
+    sim = oracle.OracleSim(inst.L, 1, inst.NT, inst.C, inst.seed, bonds[g:g + 1], spins[g:g + 1], metro,
+                           swapt, group_base=g)
     qh = es = None
     mf = me = 0
     if w["measure"] is not None:
@@ -142,11 +155,22 @@ def run_job(name: str, g: int, parts: str) -> str:
                         esum=es, measure_from=mf, measure_every=me)
         done += n
         sl = out["swap_log"][:, 0]
-        rec = {"end_sweep": done,
-               "spins": digest(sim.spins()[0]),
-               "energies": digest(sim.energies()[0]),
-               "swap_log": digest(sl),
-               "swap_accepts": int(sum(bin(int(x)).count("1") for x in sl.ravel()))}
+        if tp:
+            # realization g alone (bit 0): spins [NT][C][N] uint8, energies [NT][C],
+            # accepted pairs per pass and copy as one word (bit p = pair p)
+            sl = (sl & np.uint32(1)).astype(np.uint64)
+            sl = (sl << np.arange(inst.NT - 1, dtype=np.uint64)).sum(axis=-1).astype(np.uint32)
+            rec = {"end_sweep": done,
+                   "spins": digest((sim.spins()[0] & np.uint32(1)).astype(np.uint8)),
+                   "energies": digest(np.ascontiguousarray(sim.energies()[0][:, :, 0])),
+                   "swap_log": digest(sl),
+                   "swap_accepts": int(sum(bin(int(x)).count("1") for x in sl.ravel()))}
+        else:
+            rec = {"end_sweep": done,
+                   "spins": digest(sim.spins()[0]),
+                   "energies": digest(sim.energies()[0]),
+                   "swap_log": digest(sl),
+                   "swap_accepts": int(sum(bin(int(x)).count("1") for x in sl.ravel()))}
         if w["energy_log"]:
             rec["energy_log"] = digest(out["energy_log"][:, 0])
         chunks.append(rec)
@@ -181,8 +205,8 @@ def merge(parts: str, names: list[str]) -> dict:
         m = min(len(r["chunks"]) for r in recs.values())
         complete = all(r.get("complete", True) for r in recs.values())
         inst = w["inst"]
-        inp = W.draw_inputs(inst)
-        ent = {"inst": inst_dict(inst), "sweeps": recs[w["groups"][0]]["chunks"][m - 1]["end_sweep"],
+        inp = W.draw_tp_inputs(inst) if w.get("tpack") else W.draw_inputs(inst)
+        ent = {"inst": inst_dict(inst), "tpack": bool(w.get("tpack", False)), "sweeps": recs[w["groups"][0]]["chunks"][m - 1]["end_sweep"],
                "planned_sweeps": w["sweeps"], "swap_every": w["swap_every"],
                "chunk": w["chunk"], "energy_log": w["energy_log"],
                "measure": list(w["measure"]) if (w["measure"] and complete) else None,

@@ -190,3 +190,39 @@ def test_served_trace_requests():
         out = srv.wait(t)
         check_final(ent, out["spins"], out["energies"])
     srv.close()
+
+
+def test_temperature_packed_form_over_its_whole_run():
+    """The temperature-packed workload (76 realizations, 32 temperatures x 2
+    copies, L = 16) over its whole run in chunks with swap logs: realization r
+    is bit 0 of word-group r of the oracle run with group_base = r, so its slot
+    bits, energies and accepted pairs match the oracle's digests."""
+    ent = golden("tpack")
+    inst = instance(ent)
+    inp = W.draw_tp_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    assert digest(metro) == ent["metro_table"] and digest(swapt) == ent["swap_table"]
+    tp = ea.TPEnsemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
+    shifts = np.arange(inst.NT, dtype=np.uint32)[:, None, None]
+    done = k = 0
+    while done < ent["sweeps"]:
+        n = min(ent["chunk"], ent["sweeps"] - done)
+        out = tp.sweep(n, ent["swap_every"], swap_log=True)
+        done += n
+        torch.cuda.synchronize()
+        sp, en = tp.read()
+        sp = sp.cpu().numpy().view(np.uint32)                   # [R][C][N], bit t = slot t
+        en = en.cpu().numpy()                                    # [R][NT][C]
+        sl = out["swap_log"].cpu().numpy().view(np.uint32)      # [passes][R][C], bit p = pair p
+        for g, rec in ent["groups"].items():
+            want = rec["chunks"][k]
+            assert want["end_sweep"] == done
+            r = int(g)
+            bits = ((sp[r][None, :, :] >> shifts) & np.uint32(1)).astype(np.uint8)   # [NT][C][N]
+            assert digest(bits) == want["spins"], f"slot bits of realization {r} after sweep {done}"
+            assert digest(np.ascontiguousarray(en[r])) == want["energies"], \
+                f"energies of realization {r} after sweep {done}"
+            assert digest(np.ascontiguousarray(sl[:, r])) == want["swap_log"], \
+                f"accepted pairs of realization {r}, sweeps {done - n}..{done}"
+        k += 1
+    tp.close()
