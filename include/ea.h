@@ -498,6 +498,25 @@ int ea_tp_set_split(ea_tp *tp, uint32_t k);
 /* Synchronises the context's stream and frees its device memory. */
 void ea_tp_destroy(ea_tp *tp);
 
+/* A temperature-packed request to the server (see ea_submit_tp). */
+typedef struct {
+    uint32_t n_sweeps, swap_every;   /* as ea_tp_sweep */
+    uint32_t *spins_out;       /* HOST [R][C][W][N] final words (ea_tp_read's layout), or NULL */
+    int32_t *energies_out;     /* HOST [R][NT][C] final energies by slot, or NULL */
+} ea_tp_request;
+/* Queues a temperature-packed request (Sec. 3.2's word layout, the ea_tp_*
+ * context above) on the server: cfg's host inputs are copied, the request is
+ * admitted by device memory like any other, and each round advances it on the
+ * server's compute stream behind the round's batched launches (one launch, or
+ * the slot groups and their merge, per round).  Its result is exactly what
+ * ea_tp_create + ea_tp_sweep(n_sweeps, swap_every) + ea_tp_read give alone.
+ * Shape errors return at once (EA_EINVAL / EA_EUNSUPPORTED); table errors and
+ * a request larger than the whole budget finish the ticket.  Creating and
+ * destroying such a context allocates and frees with cudaMalloc / cudaFree,
+ * which synchronise the device: rounds that admit or finish one do not overlap
+ * the next round. */
+int ea_submit_tp(ea_server *server, const ea_tp_config *cfg, const ea_tp_request *req, uint64_t *ticket);
+
 /* Static description of an error code. */
 const char *ea_strerror(int code);
 

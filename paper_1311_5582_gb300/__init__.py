@@ -66,6 +66,11 @@ class _TpConfig(ctypes.Structure):
                 ("real_base", ctypes.c_uint32)]
 
 
+class _TpRequest(ctypes.Structure):
+    _fields_ = [("n_sweeps", ctypes.c_uint32), ("swap_every", ctypes.c_uint32),
+                ("spins_out", ctypes.c_void_p), ("energies_out", ctypes.c_void_p)]
+
+
 class _ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
@@ -98,7 +103,7 @@ EXPORTS = ["ea_build_tables", "ea_build_tables_field", "ea_supported_L", "ea_cre
            "ea_batch_set_plan", "ea_batch_set_width", "ea_batch_set_wait_limit", "ea_batch_inject_stall",
            "ea_batch_set_segment", "ea_batch_sweep",
            "ea_batch_sweep_each", "ea_batch_sync", "ea_batch_autotune", "ea_batch_launch_count", "ea_batch_destroy",
-           "ea_server_create", "ea_submit", "ea_submit_field", "ea_poll", "ea_server_stats_get",
+           "ea_server_create", "ea_submit", "ea_submit_field", "ea_submit_tp", "ea_poll", "ea_server_stats_get",
            "ea_server_destroy",
            "ea_run",
            "ea_pt_swap_static", "ea_tp_create", "ea_tp_sweep", "ea_tp_read", "ea_tp_info",
@@ -170,6 +175,8 @@ def load_library(path: str | None = None):
     lib.ea_server_create.argtypes = [ctypes.POINTER(_ServerOpts), ctypes.POINTER(vp)]
     lib.ea_submit.argtypes = [vp, ctypes.POINTER(_Config), ctypes.POINTER(_Request),
                               ctypes.POINTER(u64)]
+    lib.ea_submit_tp.argtypes = [vp, ctypes.POINTER(_TpConfig), ctypes.POINTER(_TpRequest),
+                                 ctypes.POINTER(u64)]
     lib.ea_poll.argtypes = [vp, u64, u32]
     lib.ea_server_stats_get.argtypes = [vp, ctypes.POINTER(_ServerStats)]
     lib.ea_server_destroy.argtypes = [vp]
@@ -576,6 +583,32 @@ class Server:
             fld = _Field(int(h_num), int(h_den), mf.ctypes.data)
             _check(self.lib.ea_submit_field(self.s, ctypes.byref(cfg), ctypes.byref(fld), ctypes.byref(req),
                                             ctypes.byref(t)), "ea_submit_field")
+        self._out[t.value] = out
+        return t.value
+
+    def submit_tp(self, L, R, NT, C, seed, bonds, spins, metro, swapt, n_sweeps, swap_every,
+                  want_spins=True, want_energies=True, real_base=0) -> int:
+        """A temperature-packed request (ea_submit_tp; inputs as TPEnsemble).  Its
+        outputs: "spins" [R][C][N] ([R][C][W][N] for NT > 32) uint32 words, bit t =
+        slot t, and "energies" [R][NT][C] int32."""
+        N = int(L) ** 3
+        W = max(1, -(-int(NT) // 32))
+        b = np.ascontiguousarray(bonds, np.uint8)
+        sp = np.ascontiguousarray(spins, np.uint32)
+        m = np.ascontiguousarray(metro, np.uint32)
+        w = np.ascontiguousarray(swapt, np.uint32)
+        shape = (R, C, N) if W == 1 else (R, C, W, N)
+        if b.shape != (R, 3, N) or sp.shape != shape or m.shape != (NT, 3):
+            raise ValueError("submit_tp: bonds [R][3][N] uint8, spins [R][C](W)[N], metro [NT][3]")
+        swap_len = w.shape[1] if w.ndim == 2 else 0
+        cfg = _TpConfig(int(L), int(R), int(NT), int(C), int(seed), b.ctypes.data, sp.ctypes.data,
+                        m.ctypes.data, w.ctypes.data if w.size else None, swap_len, int(real_base))
+        out = {"spins": np.zeros(shape, np.uint32) if want_spins else None,
+               "energies": np.zeros((R, NT, C), np.int32) if want_energies else None}
+        req = _TpRequest(int(n_sweeps), int(swap_every), _ptr(out["spins"]), _ptr(out["energies"]))
+        t = ctypes.c_uint64(0)
+        _check(self.lib.ea_submit_tp(self.s, ctypes.byref(cfg), ctypes.byref(req), ctypes.byref(t)),
+               "ea_submit_tp")
         self._out[t.value] = out
         return t.value
 

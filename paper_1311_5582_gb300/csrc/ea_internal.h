@@ -183,4 +183,9 @@ int create_ctx(const ea_config *cfg, cudaStream_t stream, cudaMemPool_t pool, ea
 void destroy_ctx(ea_ctx *c, cudaStream_t st);
 // Device bytes create_ctx allocates for cfg, the import staging included.
 size_t ctx_device_bytes(const ea_config *cfg);
+// Temperature-packed contexts in the server: the stream their later work runs
+// on, and the most device bytes ea_tp_create and ea_tp_sweep allocate for cfg
+// (slot-group slices at eight groups a word included).
+void tp_set_stream(ea_tp *t, cudaStream_t st);
+size_t tp_device_bytes(const ea_tp_config *cfg);
 }  // namespace ea

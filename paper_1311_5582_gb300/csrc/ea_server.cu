@@ -63,6 +63,12 @@ struct Request {
     size_t bytes = 0;                             // device bytes while resident
     Clock::time_point t_submit;
     ea_ctx *ctx = nullptr;
+    bool tp = false;                              // temperature-packed (ea_submit_tp): tcfg, tctx
+    ea_tp_config tcfg{};                          // points into the copies (bonds in tbonds)
+    std::vector<uint8_t> tbonds;
+    ea_tp *tctx = nullptr;
+    double flips_per_sweep = 0.0;                 // flip attempts of one sweep
+    uint64_t units = 0;                           // CTAs of one launch ((group or realization) x copy)
     uint32_t left = 0;                            // sweeps not yet launched
     uint64_t words = 0;                           // site-words of one sweep (N * NT * C * G)
     uint32_t waited = 0;                          // consecutive rounds left out
@@ -128,7 +134,7 @@ void finish(ea_server *s, Request &r, int status)
     if (status == EA_OK) {
         s->completed += 1;
         s->lat_ms.push_back(ms_between(r.t_submit, now));
-        s->flips += (double)r.words * 32.0 * r.n_sweeps;
+        s->flips += r.flips_per_sweep * r.n_sweeps;
         s->last_done_s = ms_between(s->t0, now) * 1e-3;
     } else {
         s->failed += 1;
@@ -159,7 +165,11 @@ void admit(ea_server *s)
             continue;
         }
         ea_ctx *ctx = nullptr;
-        const int rc = ea::create_ctx(&r->cfg, s->admit, s->pool, &ctx, r->has_fld ? &r->fld : nullptr);
+        ea_tp *tctx = nullptr;
+        // a temperature-packed context is created (cudaMalloc) and filled on the
+        // admission stream, which ea_tp_create synchronises before it returns
+        const int rc = r->tp ? ea_tp_create(&r->tcfg, s->admit, &tctx)
+                             : ea::create_ctx(&r->cfg, s->admit, s->pool, &ctx, r->has_fld ? &r->fld : nullptr);
         if (rc == EA_ENOMEM && !s->live.empty()) {
             // the budget was optimistic: retry once resident requests finish
             std::lock_guard<std::mutex> lk(s->mu);
@@ -170,12 +180,18 @@ void admit(ea_server *s)
             finish(s, *r, rc);
             continue;
         }
-        ctx->stream = s->compute;              // all later work of this context
-        r->ctx = ctx;
+        if (r->tp) {
+            ea::tp_set_stream(tctx, s->compute);  // all later work of this context
+            r->tctx = tctx;
+        } else {
+            ctx->stream = s->compute;
+            r->ctx = ctx;
+        }
         r->left = r->n_sweeps;
         // the host copies of the inputs are no longer needed
         std::vector<uint32_t>().swap(r->bonds);
         std::vector<uint32_t>().swap(r->spins0);
+        std::vector<uint8_t>().swap(r->tbonds);
         s->used += r->bytes;
         s->peak = std::max(s->peak, s->used);
         s->live.push_back(std::move(r));
@@ -189,10 +205,34 @@ void admit(ea_server *s)
     s->n_live = s->live.size();
 }
 
+// Frees a request's context (stream-ordered on the compute stream for pooled
+// contexts; a temperature-packed one synchronises it and frees with cudaFree).
+void release_request(ea_server *s, Request &r)
+{
+    if (r.ctx) ea::destroy_ctx(r.ctx, s->compute);
+    if (r.tctx) ea_tp_destroy(r.tctx);
+    r.ctx = nullptr;
+    r.tctx = nullptr;
+}
+
 // Enqueues on the compute stream, behind the round that finishes request r,
 // the export of its final energies and spins into pool scratch.
 void enqueue_export(ea_server *s, Request &r)
 {
+    if (r.tp) {
+        const ea_tp_config &t = r.tcfg;
+        const size_t W = (t.n_temps + 31) / 32, N = (size_t)t.L * t.L * t.L;
+        const size_t nsp = (size_t)t.n_real * t.n_copies * W * N, nen = (size_t)t.n_real * t.n_temps * t.n_copies;
+        cudaError_t e = cudaSuccess;
+        if (r.spins_out)
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.d_spins), nsp * 4, s->pool, s->compute);
+        if (e == cudaSuccess && r.energies_out)
+            e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r.d_energies), nen * 4, s->pool, s->compute);
+        int rc = EA_OK;
+        if (e == cudaSuccess) rc = ea_tp_read(r.tctx, r.d_spins, r.d_energies);
+        r.status = e != cudaSuccess ? (e == cudaErrorMemoryAllocation ? EA_ENOMEM : EA_ECUDA) : rc;
+        return;
+    }
     ea_ctx *c = r.ctx;
     const size_t nsp = (size_t)c->G * c->NT * c->C * c->N, nen = (size_t)c->G * c->NT * c->C * ea::kLanes;
     cudaError_t e = cudaSuccess;
@@ -224,9 +264,22 @@ void deliver(ea_server *s, Round &rd)
     std::vector<int> status(rd.finishing.size(), EA_OK);
     for (size_t j = 0; j < rd.finishing.size(); ++j) {
         Request &r = *rd.finishing[j];
-        ea_ctx *c = r.ctx;
         int st = es != cudaSuccess ? EA_ECUDA : r.status;
         cudaError_t e = cudaSuccess;
+        if (r.tp) {
+            const ea_tp_config &t = r.tcfg;
+            const size_t W = (t.n_temps + 31) / 32, N = (size_t)t.L * t.L * t.L;
+            if (st == EA_OK && r.spins_out)
+                e = cudaMemcpyAsync(r.spins_out, r.d_spins, (size_t)t.n_real * t.n_copies * W * N * 4,
+                                    cudaMemcpyDeviceToHost, s->copy);
+            if (st == EA_OK && e == cudaSuccess && r.energies_out)
+                e = cudaMemcpyAsync(r.energies_out, r.d_energies, (size_t)t.n_real * t.n_temps * t.n_copies * 4,
+                                    cudaMemcpyDeviceToHost, s->copy);
+            if (e != cudaSuccess) st = EA_ECUDA;
+            status[j] = st;
+            continue;
+        }
+        ea_ctx *c = r.ctx;
         if (st == EA_OK && r.energies_out)
             e = cudaMemcpyAsync(r.energies_out, r.d_energies, (size_t)c->G * c->NT * c->C * ea::kLanes * 4,
                                 cudaMemcpyDeviceToHost, s->copy);
@@ -248,8 +301,7 @@ void deliver(ea_server *s, Round &rd)
         r.d_spins = nullptr;
         r.d_energies = nullptr;
         r.d_mags = nullptr;
-        ea::destroy_ctx(r.ctx, s->compute);      // after every round already queued
-        r.ctx = nullptr;
+        release_request(s, r);                    // after every round already queued
         s->used -= r.bytes;
         finish(s, r, ec != cudaSuccess ? EA_ECUDA : status[j]);
     }
@@ -284,7 +336,7 @@ void run_round(ea_server *s, uint64_t k)
         if (units >= 2ull * (uint64_t)s->sms && words > 0.0) break;
         in_round[order[j]] = 1;
         words += (double)r.words;
-        units += (uint64_t)r.ctx->G * r.ctx->C;
+        units += r.units;
     }
     const double qd = s->round_ms * s->rate / (words > 0 ? words : 1.0);
     const uint32_t q = (uint32_t)std::max(1.0, std::min(qd, 1048576.0));
@@ -298,19 +350,25 @@ void run_round(ea_server *s, uint64_t k)
     std::vector<uint32_t> nsw_all(n);
     for (size_t i = 0; i < n && rc == EA_OK; ++i) {
         Request &r = *s->live[i];
-        const int kd = r.field ? 1 : 0;
-        rc = ea_batch_add(kd ? bf : b, r.ctx);
         nsw_all[i] = in_round[i] ? std::min(q, r.left) : 0u;
-        nsw[kd].push_back(nsw_all[i]);
-        kev[kd].push_back(r.swap_every);
         r.waited = in_round[i] ? 0u : r.waited + 1u;
         const double w = (double)nsw_all[i] * (double)r.words;
         work += w;
+        if (r.tp) continue;                       // launched on its own below
+        const int kd = r.field ? 1 : 0;
+        rc = ea_batch_add(kd ? bf : b, r.ctx);
+        nsw[kd].push_back(nsw_all[i]);
+        kev[kd].push_back(r.swap_every);
         kind_work[kd] += w;
     }
     cudaEventRecord(rd.start, s->compute);
     if (rc == EA_OK && kind_work[0] > 0.0) rc = ea_batch_sweep_each(b, nsw[0].data(), kev[0].data());
     if (rc == EA_OK && kind_work[1] > 0.0) rc = ea_batch_sweep_each(bf, nsw[1].data(), kev[1].data());
+    // temperature-packed requests: their own launches, behind the batches
+    for (size_t i = 0; i < n && rc == EA_OK; ++i) {
+        Request &r = *s->live[i];
+        if (r.tp && nsw_all[i] > 0) rc = ea_tp_sweep(r.tctx, nsw_all[i], r.swap_every, nullptr, nullptr);
+    }
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->rounds += 1;
@@ -320,8 +378,7 @@ void run_round(ea_server *s, uint64_t k)
         cudaStreamSynchronize(s->compute);
         for (size_t i = 0; i < n; ++i) {
             Request &r = *s->live[i];
-            ea::destroy_ctx(r.ctx, s->compute);
-            r.ctx = nullptr;
+            release_request(s, r);
             s->used -= r.bytes;
             finish(s, r, rc);
         }
@@ -392,16 +449,12 @@ void worker_main(ea_server *s)
             if (r->d_spins) cudaFreeAsync(r->d_spins, s->compute);
             if (r->d_energies) cudaFreeAsync(r->d_energies, s->compute);
             if (r->d_mags) cudaFreeAsync(r->d_mags, s->compute);
-            ea::destroy_ctx(r->ctx, s->compute);
-            r->ctx = nullptr;
+            release_request(s, *r);
         }
         rd.finishing.clear();
         rd.active = false;
     }
-    for (auto &r : s->live) {
-        ea::destroy_ctx(r->ctx, s->compute);
-        r->ctx = nullptr;
-    }
+    for (auto &r : s->live) release_request(s, *r);
     s->live.clear();
     cudaStreamSynchronize(s->compute);
 }
@@ -543,10 +596,68 @@ int ea_submit_field(ea_server *s, const ea_config *cfg, const ea_field *field, c
     r->spins_out = req->spins_out;
     r->energies_out = req->energies_out;
     r->words = (uint64_t)nsp;
+    r->flips_per_sweep = (double)nsp * 32.0;
+    r->units = (uint64_t)cfg->n_groups * cfg->n_copies;
     // resident state plus the output scratch taken at completion
     const size_t nen = (size_t)cfg->n_groups * cfg->n_temps * cfg->n_copies * ea::kLanes;
     r->bytes = ea::ctx_device_bytes(cfg) + (r->spins_out ? nsp * 4 : 0) + (r->energies_out ? nen * 4 : 0) +
                (r->field ? nen * 4 * (r->mags_out ? 2 : 1) + (size_t)cfg->n_temps * 14 * 8 : 0);
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return EA_ESTATE;
+        r->ticket = s->next_ticket++;
+        *ticket = r->ticket;
+        s->open.insert(r->ticket);
+        s->submitted += 1;
+        if (s->first_submit_s < 0) s->first_submit_s = ms_between(s->t0, r->t_submit) * 1e-3;
+        s->queue.push_back(std::move(r));
+    }
+    s->cv_work.notify_one();
+    return EA_OK;
+}
+
+int ea_submit_tp(ea_server *s, const ea_tp_config *cfg, const ea_tp_request *req, uint64_t *ticket)
+{
+    if (!s || !cfg || !req || !ticket) return EA_EINVAL;
+    if (cfg->L < 4 || (cfg->L & 1u)) return EA_EINVAL;
+    if (!ea::supported_L((int)cfg->L)) return EA_EUNSUPPORTED;
+    if (cfg->n_real == 0 || cfg->n_temps == 0 || cfg->n_temps > 64 || cfg->n_copies < 1 || cfg->n_copies > 2)
+        return EA_EINVAL;
+    if ((uint64_t)cfg->real_base + cfg->n_real > (1ull << 32)) return EA_EINVAL;
+    if (!cfg->bonds || !cfg->spins0 || !cfg->metro) return EA_EINVAL;
+    if (cfg->n_temps > 1 && cfg->swap_len > 0 && !cfg->swapt) return EA_EINVAL;
+    auto r = std::unique_ptr<Request>(new (std::nothrow) Request());
+    if (!r) return EA_ENOMEM;
+    const size_t N = (size_t)cfg->L * cfg->L * cfg->L, W = (cfg->n_temps + 31) / 32;
+    const size_t nsp = (size_t)cfg->n_real * cfg->n_copies * W * N, nbo = (size_t)cfg->n_real * 3 * N;
+    const size_t nen = (size_t)cfg->n_real * cfg->n_temps * cfg->n_copies;
+    const size_t nsw = (size_t)(cfg->n_temps > 1 ? cfg->n_temps - 1 : 0) * cfg->swap_len;
+    try {
+        r->tbonds.assign(cfg->bonds, cfg->bonds + nbo);
+        r->spins0.assign(cfg->spins0, cfg->spins0 + nsp);
+        r->metro.assign(cfg->metro, cfg->metro + (size_t)cfg->n_temps * 3);
+        if (nsw) r->swapt.assign(cfg->swapt, cfg->swapt + nsw);
+    } catch (...) {
+        return EA_ENOMEM;
+    }
+    r->tp = true;
+    r->tcfg = *cfg;
+    r->tcfg.bonds = r->tbonds.data();
+    r->tcfg.spins0 = r->spins0.data();
+    r->tcfg.metro = r->metro.data();
+    r->tcfg.swapt = nsw ? r->swapt.data() : nullptr;
+    r->n_sweeps = req->n_sweeps;
+    r->swap_every = req->swap_every;
+    r->spins_out = req->spins_out;
+    r->energies_out = req->energies_out;
+    // work in units of a realization-packed site-word update (32 flip attempts):
+    // one flip attempt of this form costs about a third of one (one uniform per
+    // attempt instead of one per 32)
+    r->flips_per_sweep = (double)cfg->n_real * cfg->n_copies * N * cfg->n_temps;
+    r->words = (uint64_t)std::ceil(r->flips_per_sweep / 3.0);
+    r->units = (uint64_t)cfg->n_real * cfg->n_copies * W;
+    r->bytes = ea::tp_device_bytes(cfg) + (r->spins_out ? nsp * 4 : 0) + (r->energies_out ? nen * 4 : 0);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);

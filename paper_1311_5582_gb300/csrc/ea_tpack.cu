@@ -899,6 +899,23 @@ extern "C" int ea_tp_info(const ea_tp *t, uint64_t *sweep_index, uint64_t *pass_
     return EA_OK;
 }
 
+namespace ea {
+
+void tp_set_stream(ea_tp *t, cudaStream_t st) { t->stream = st; }
+
+size_t tp_device_bytes(const ea_tp_config *cfg)
+{
+    const size_t N = (size_t)cfg->L * cfg->L * cfg->L, R = cfg->n_real, C = cfg->n_copies;
+    const size_t W = (cfg->n_temps + 31) / 32, NT = cfg->n_temps;
+    const size_t n_spin = R * C * W * N, n_bond = R * 3 * N;
+    const size_t len = NT > 1 ? cfg->swap_len : 0;
+    return n_spin * 4 + n_bond * 4 + (len ? (NT - 1) * len : 1) * 4 + NT * 3 * 8 + R * C * kLanes * W * 4 +
+           (n_spin > n_bond ? n_spin : n_bond) * 4 +       // import staging
+           W * 8 * R * C * N * 4;                           // slot-group slices
+}
+
+}  // namespace ea
+
 extern "C" void ea_tp_destroy(ea_tp *t)
 {
     if (!t) return;

@@ -144,3 +144,77 @@ def test_request_errors():
     st = server.stats()
     assert st["completed"] == 1 and st["failed"] == 1
     server.close()
+
+
+def tp_alone(inst, inp, metro, swapt, n, k):
+    tp = ea.TPEnsemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], metro, swapt)
+    tp.sweep(n, k)
+    torch.cuda.synchronize()
+    sp, en = tp.read()
+    out = sp.cpu().numpy().view(np.uint32), en.cpu().numpy()
+    tp.close()
+    return out
+
+
+def test_temperature_packed_requests_match_alone():
+    """Temperature-packed requests (ea_submit_tp) served together with
+    realization-packed ones, some arriving while others run: each result equals
+    the same temperature-packed ensemble run alone (TPEnsemble), whatever the
+    rounds it was split into; two words per site for NT > 32 included."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    tps = []
+    for j, (L, R, NT, C, n, k) in enumerate([(8, 5, 24, 2, 300, 10), (4, 40, 32, 1, 137, 1),
+                                             (12, 3, 40, 2, 90, 7), (6, 150, 16, 2, 500, 10),
+                                             (16, 2, 33, 1, 45, 5), (10, 9, 1, 2, 60, 3)]):
+        inst = W.Instance(L=L, G=R, NT=NT, C=C, seed=int(rng.integers(1, 2**40)), tmin=0.9, tmax=2.0,
+                          input_seed=int(rng.integers(1, 2**31)))
+        inp = W.draw_tp_inputs(inst)
+        metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+        tps.append((inst, inp, metro, swapt, n, k))
+    packed = [r for r in request_set(6, 78)]
+    srv = ea.Server(round_ms=5)
+    tickets = []
+    for j in range(max(len(tps), len(packed))):
+        if j < len(tps):
+            inst, inp, metro, swapt, n, k = tps[j]
+            tickets.append(("tp", j, srv.submit_tp(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"],
+                                                   inp["spins"], metro, swapt, n, k)))
+        if j < len(packed):
+            r = packed[j]
+            inp, metro, swapt = tables(r["inst"])
+            tickets.append(("packed", j, submit(srv, r["inst"], inp, metro, swapt, r["n"], r["k"])))
+        time.sleep(0.003)
+    for kind, j, t in tickets:
+        out = srv.wait(t)
+        if kind == "tp":
+            sp, en = tp_alone(*tps[j])
+            assert np.array_equal(out["spins"], sp), f"temperature-packed request {j}: spins"
+            assert np.array_equal(out["energies"], en), f"temperature-packed request {j}: energies"
+        else:
+            r = packed[j]
+            inp, metro, swapt = tables(r["inst"])
+            sp, en = alone(r["inst"], inp, metro, swapt, r["n"], r["k"])
+            assert np.array_equal(out["spins"], sp) and np.array_equal(out["energies"], en), f"request {j}"
+    st = srv.stats()
+    assert st["completed"] == len(tickets) and st["failed"] == 0
+    srv.close()
+
+
+def test_temperature_packed_request_errors():
+    srv = ea.Server()
+    inst = W.Instance(L=8, G=2, NT=8, C=2, seed=5, tmin=0.9, tmax=2.0, input_seed=9)
+    inp = W.draw_tp_inputs(inst)
+    metro, swapt = ea.ea_build_tables(inp["betas"], inst.N)
+    with pytest.raises(ea.EAError) as ei:    # odd L is rejected at once
+        srv.submit_tp(7, 2, 8, 2, 5, np.zeros((2, 3, 343), np.uint8), np.zeros((2, 2, 343), np.uint32),
+                      metro, swapt, 10, 1)
+    assert ei.value.code == -1
+    bad = metro.copy()
+    bad[0, 0], bad[0, 1] = bad[0, 1] + 1, bad[0, 0]   # not non-decreasing: fails at admission
+    t = srv.submit_tp(8, 2, 8, 2, 5, inp["bonds"], inp["spins"], bad, swapt, 10, 1)
+    with pytest.raises(ea.EAError) as ei:
+        srv.wait(t)
+    assert ei.value.code == -1
+    st = srv.stats()
+    assert st["failed"] == 1
+    srv.close()
