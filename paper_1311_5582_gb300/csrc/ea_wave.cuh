@@ -160,13 +160,14 @@ __device__ __forceinline__ bool wave_wait(uint64_t *bar, uint32_t parity, volati
     atomicExch(err, 1);
     return false;
 }
-// The same for a barrier the partner CTA of the cluster arrives on.
+// The same for a barrier the partner CTA of the cluster arrives on (the abort
+// flag read every 32nd poll, as for the field-free waits above).
 __device__ __forceinline__ bool wave_wait_cluster(uint64_t *bar, uint32_t parity, volatile uint32_t *abort,
                                                   int *err)
 {
     for (int it = 0; it < kWaveWaitLimit; ++it) {
         if (mbar_try_wait_cluster(bar, parity)) return true;
-        if (*abort != 0u) return false;
+        if ((it & 31) == 31 && *abort != 0u) return false;
     }
     *abort = 1u;
     atomicExch(err, 1);
