@@ -437,6 +437,27 @@ def bench_field(ea, torch, peak_tops, sweeps=200, h=(1, 2)):
     return out
 
 
+def bench_field_plain(ea, torch, sweeps=200, h=(1, 2)):
+    """The headline ensemble in the field h under its default plan (the field
+    wavefront kernel for 0 < |h| < 2): one warm-up call, then one timed call."""
+    wl = workload("scale", sweeps)
+    inst = wl["inst"]
+    inp = W.draw_inputs(inst)
+    mf, sw = ea.ea_build_tables_field(inp["betas"], inst.N, *h)
+    ens = ea.Ensemble(inst.L, inst.G, inst.NT, inst.C, inst.seed, inp["bonds"], inp["spins"], None, sw,
+                      field=(h[0], h[1], mf))
+    ens.sweep(wl["sweeps"], wl["swap_every"])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    ens.sweep(wl["sweeps"], wl["swap_every"])
+    b.record()
+    b.synchronize()
+    plan = ens.plans()[ens.plan]["form"]
+    ens.close()
+    return {"workload": wl["name"] + f", field h = {h[0]}/{h[1]}", "plan": plan,
+            "value": a.elapsed_time(b) / 1e3 / wl["flips"] * 1e12, "unit": UNIT}
+
+
 # Algorithmic integer ops of the temperature-packed form per flip attempt: a
 # quarter Philox4x32-10 call (one uniform per attempt: 10), three threshold
 # tests and three mask-bit ORs, plus the 24-op bit-sliced update of the site
@@ -636,7 +657,15 @@ def main():
                     help="run only the batched mix with default plans (--sweeps sweeps) and print its object")
     ap.add_argument("--tpack-only", action="store_true",
                     help="run only the temperature-packed workload (--sweeps sweeps) and print its object")
+    ap.add_argument("--field-only", action="store_true",
+                    help="run only the headline ensemble in the field h = 1/2 under its default plan "
+                         "(one warm-up and one timed call of --sweeps sweeps) and print its object")
     args = ap.parse_args()
+    if args.field_only:
+        import torch
+        import paper_1311_5582_gb300 as ea
+        print(json.dumps(bench_field_plain(ea, torch, sweeps=args.sweeps or 200)))
+        return 0
     if args.tpack_only:
         import torch
         import paper_1311_5582_gb300 as ea
