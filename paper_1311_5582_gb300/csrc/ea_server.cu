@@ -22,6 +22,10 @@
 //      their memory -- the GPU meanwhile runs the round already queued.
 // Every request's trajectory is the one ea_sweep would give it alone: the
 // batch keeps each member's own counters, tables and swap schedule.
+// Temperature-packed requests (ea_submit_tp) take part in the same rounds
+// with their own launches (ea_tp_sweep) behind the batched ones; their
+// contexts use cudaMalloc / cudaFree, so admitting or finishing one
+// synchronises the device once.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
